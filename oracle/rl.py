@@ -1,0 +1,202 @@
+"""Forward plane-wise multi-view Richardson-Lucy, written out in FP64 numpy.
+
+TEST INFRASTRUCTURE ONLY (see the package docstring): nothing in the
+library imports this module.
+
+What is computed (paper: Supp. Note 1, the multi-view RL update equation;
+Results and Fig. 1a for the plane-wise approximation and reslicing):
+
+    psi^{t+1} = psi^t * prod_{v in V} [ (phi_v / (psi^t * P_v)) (*) P_v^* ]
+
+with P_v^* the flipped PSF of view v (Supp. Note 2 section 1, symbol list).
+Every plane orthogonal to the rotation axis is processed independently with
+one 2D PSF per view.
+
+Readings of points the paper leaves open (each one is listed in the design doc):
+  * all views use the same psi^t (simultaneous product, as printed);
+  * each view's ratio is correlated with its own flipped PSF before the
+    product over views;
+  * division guard: r = phi / max(b, eps);
+  * ZERO boundary = linear convolution cropped to the plane ("same"), which
+    is what padding by the PSF size for the Fourier route implements
+    (Supp. Table 1 caption); CIRCULAR = indices taken modulo the plane size;
+  * odd K only, PSF centre at (R, R) with R = (K-1)/2, and
+    P^*(i, j) = P(K-1-i, K-1-j);
+  * initial estimate = per-plane mean over the pixels of all views (FP64);
+  * rotation axis = the stack's middle axis: a stack [Z][Y][X] becomes
+    planes [Y][Z][X].
+
+Index convention used throughout (i, j in [0, K), di = i-R, dj = j-R):
+    convolve : b(y, x) = sum_ij P[i, j] * img(y - di, x - dj)
+    correlate: c(y, x) = sum_ij P[i, j] * img(y + di, x + dj)
+"""
+
+from __future__ import annotations
+
+import numpy as np
+
+ZERO = "zero"
+CIRCULAR = "circular"
+
+
+def _check_psf(P: np.ndarray) -> int:
+    P = np.asarray(P)
+    if P.ndim != 2 or P.shape[0] != P.shape[1] or P.shape[0] % 2 != 1:
+        raise ValueError("PSF must be K x K with odd K")
+    return (P.shape[0] - 1) // 2
+
+
+def flip_psf(P: np.ndarray) -> np.ndarray:
+    """P^*(i, j) = P(K-1-i, K-1-j): the flipped PSF (Supp. Note 2, sec. 1)."""
+    return np.asarray(P)[::-1, ::-1].copy()
+
+
+def _shifted(img: np.ndarray, sy: int, sx: int, boundary: str) -> np.ndarray:
+    """out(y, x) = img(y + sy, x + sx); zero or wrapped outside the plane."""
+    H, W = img.shape
+    if boundary == CIRCULAR:
+        ys = (np.arange(H) + sy) % H
+        xs = (np.arange(W) + sx) % W
+        return img[np.ix_(ys, xs)]
+    if boundary != ZERO:
+        raise ValueError(f"unknown boundary {boundary!r}")
+    out = np.zeros_like(img)
+    y0, y1 = max(0, -sy), min(H, H - sy)
+    x0, x1 = max(0, -sx), min(W, W - sx)
+    if y0 < y1 and x0 < x1:
+        out[y0:y1, x0:x1] = img[y0 + sy:y1 + sy, x0 + sx:x1 + sx]
+    return out
+
+
+def convolve(img: np.ndarray, P: np.ndarray, boundary: str = ZERO) -> np.ndarray:
+    """Direct "same"-size 2D convolution psi * P by shift-and-add over K^2 taps.
+
+    b(y, x) = sum_{i,j} P[i, j] img(y - (i-R), x - (j-R)).
+    """
+    R = _check_psf(P)
+    img = np.asarray(img, dtype=np.float64)
+    P = np.asarray(P, dtype=np.float64)
+    out = np.zeros_like(img)
+    K = P.shape[0]
+    for i in range(K):
+        for j in range(K):
+            if P[i, j] != 0.0:
+                out += P[i, j] * _shifted(img, -(i - R), -(j - R), boundary)
+    return out
+
+
+def correlate(img: np.ndarray, P: np.ndarray, boundary: str = ZERO) -> np.ndarray:
+    """Direct "same"-size correlation with P, i.e. convolution with P^*.
+
+    c(y, x) = sum_{i,j} P[i, j] img(y + (i-R), x + (j-R)).
+    """
+    R = _check_psf(P)
+    img = np.asarray(img, dtype=np.float64)
+    P = np.asarray(P, dtype=np.float64)
+    out = np.zeros_like(img)
+    K = P.shape[0]
+    for i in range(K):
+        for j in range(K):
+            if P[i, j] != 0.0:
+                out += P[i, j] * _shifted(img, i - R, j - R, boundary)
+    return out
+
+
+def _fft_conv(img: np.ndarray, P: np.ndarray, boundary: str) -> np.ndarray:
+    """Convolution in the Fourier domain (Supp. Note 2, sec. 4).
+
+    ZERO: the plane is padded by the PSF size so that the cyclic product of
+    spectra equals the linear convolution (Supp. Table 1 caption), then the
+    "same" window is cropped.  CIRCULAR: the PSF is wrapped onto the plane
+    grid with its centre at the origin.
+    """
+    R = _check_psf(P)
+    img = np.asarray(img, dtype=np.float64)
+    P = np.asarray(P, dtype=np.float64)
+    H, W = img.shape
+    K = P.shape[0]
+    if boundary == ZERO:
+        Hp, Wp = H + K - 1, W + K - 1
+        F = np.fft.rfft2(img, s=(Hp, Wp)) * np.fft.rfft2(P, s=(Hp, Wp))
+        full = np.fft.irfft2(F, s=(Hp, Wp))
+        return full[R:R + H, R:R + W].copy()
+    if boundary == CIRCULAR:
+        ker = np.zeros((H, W))
+        for i in range(K):
+            for j in range(K):
+                ker[(i - R) % H, (j - R) % W] += P[i, j]
+        F = np.fft.rfft2(img) * np.fft.rfft2(ker)
+        return np.fft.irfft2(F, s=(H, W))
+    raise ValueError(f"unknown boundary {boundary!r}")
+
+
+def convolve_fft(img, P, boundary=ZERO):
+    """Fourier-route psi * P; equal to :func:`convolve` up to rounding."""
+    return _fft_conv(img, P, boundary)
+
+
+def correlate_fft(img, P, boundary=ZERO):
+    """Fourier-route correlation = convolution with the flipped PSF."""
+    return _fft_conv(img, flip_psf(P), boundary)
+
+
+def init_mean(phi: np.ndarray) -> np.ndarray:
+    """Uniform initial estimate: per-plane mean of all views' pixels, FP64.
+
+    phi: [V][P][H][W] -> [P] (one scalar per plane).
+    """
+    phi = np.asarray(phi, dtype=np.float64)
+    return phi.mean(axis=(0, 2, 3))
+
+
+def rl_step(psi, phi_planes, psfs, boundary=ZERO, eps=1e-6, route="direct"):
+    """One MV-RL update of one plane (Supp. Note 1, update equation).
+
+    psi: [H][W]; phi_planes: [V][H][W]; psfs: [V][K][K].  Every view's
+    ratio uses the same psi (simultaneous product).
+    """
+    conv = convolve if route == "direct" else convolve_fft
+    corr = correlate if route == "direct" else correlate_fft
+    psi = np.asarray(psi, dtype=np.float64)
+    update = np.ones_like(psi)
+    for v in range(len(psfs)):
+        blur = conv(psi, psfs[v], boundary)
+        ratio = np.asarray(phi_planes[v], dtype=np.float64) / np.maximum(blur, eps)
+        update *= corr(ratio, psfs[v], boundary)
+    return psi * update
+
+
+def rl_planes(phi, psfs, iters, boundary=ZERO, eps=1e-6, psi0=None,
+              route="direct", planes=None):
+    """Plane-wise MV-RL over a stack of planes.
+
+    phi:  [V][P][H][W] data (any real dtype; used as FP64)
+    psfs: [V][K][K]
+    psi0: None -> per-plane mean initial estimate; else [P][H][W]
+    planes: optional iterable of plane indices to compute (others skipped;
+            the result then holds only those planes, in that order)
+    Returns the estimate after ``iters`` updates, FP64 [n][H][W].
+    """
+    phi = np.asarray(phi)
+    V, P, H, W = phi.shape
+    psfs = np.asarray(psfs, dtype=np.float64)
+    if psfs.shape[0] != V:
+        raise ValueError("one PSF per view")
+    idx = list(range(P)) if planes is None else list(planes)
+    means = None if psi0 is not None else init_mean(phi[:, idx])
+    out = np.empty((len(idx), H, W))
+    for n, p in enumerate(idx):
+        if psi0 is None:
+            psi = np.full((H, W), means[n])
+        else:
+            psi = np.asarray(psi0[p], dtype=np.float64).copy()
+        for _ in range(iters):
+            psi = rl_step(psi, phi[:, p], psfs, boundary, eps, route)
+        out[n] = psi
+    return out
+
+
+def reslice(stack: np.ndarray) -> np.ndarray:
+    """Reslice a registered view stack into planes orthogonal to the
+    rotation axis (Abstract; Fig. 1a).  [Z][Y][X] -> [Y][Z][X]."""
+    return np.ascontiguousarray(np.transpose(np.asarray(stack), (1, 0, 2)))
