@@ -1,0 +1,400 @@
+#!/usr/bin/env python
+"""Throughput of plane-wise multi-view Richardson-Lucy on GB300.
+
+One step = the whole hot path over one synthetic volume: reslice both view
+stacks into planes on the GPU, start every plane from its mean, run 10
+MV-RL iterations over all 512 planes.  Workload (one per GPU, weak scaling):
+2 views of 512^3 uint16 Gaussian-blob stacks (density 1e-4 per voxel,
+Poisson noise), 31x31 Gaussian PSFs sigma (1.5, 8) px, the second view
+turned by 90 degrees, zero boundary, eps 1e-6.
+
+Prints one JSON line (rank 0).  `value` counts voxel-view-iterations per
+second over all GPUs (planes x pixels x iterations x views / time); inputs
+are device-resident and larger than L2 (1 GiB of stacks and planes per
+step).  `e2e` is the same metric through mvd_run_host with pinned host
+buffers, copies included.  `--impl reference` times the FP64 CPU oracle on
+a sample of the same workload instead.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import multiprocessing as mp
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "voxel-iterations/s per view for MV-RL vs plain per-plane path; % HBM roofline"
+UNIT = "voxel-view-iterations/s"
+
+WORKLOADS = {
+    "volume512": dict(Z=512, Y=512, X=512, K=31, sigma_axial=8.0, sigma_lateral=1.5, angles=(0.0, 90.0),
+                      density=1e-4, iters=10, seed=0,
+                      label="2 views, 512^3 uint16 stacks resliced on the GPU to 512 planes of 512x512, "
+                            "31x31 PSFs sigma (1.5, 8) px turned by 90 degrees, 10 iterations"),
+    "volume128": dict(Z=128, Y=128, X=128, K=31, sigma_axial=8.0, sigma_lateral=1.5, angles=(0.0, 90.0),
+                      density=1e-4, iters=10, seed=0,
+                      label="2 views, 128^3 uint16 (quick check)"),
+}
+
+# Measured peaks on the GB300s (MEASURED_PEAKS.json): STREAM-style copy.
+HBM_PEAK_GBS = 6767.4
+# FP32 CUDA-core peak from unit counts and the maximum SM clock:
+# 152 SMs x 128 FP32 lanes x 2 flop x 2.070 GHz.
+ALU_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
+# dram__bytes_read.sum + dram__bytes_write.sum per launch from one ncu capture,
+# scaled to the full workload (None until measured for the current kernels).
+NCU_TRAFFIC_PER_LAUNCH = {"blur_ratio": None, "correlate_update": None}
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    hbm = HBM_PEAK_GBS
+    src = "fallback"
+    try:
+        with open(path) as f:
+            hbm = float(json.load(f)["hbm_gbs"])
+            src = "measured"
+    except Exception:
+        pass
+    return hbm, src
+
+
+# ----------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.file = None
+
+    def start(self):
+        try:
+            self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200",
+                 "-i", str(self.index)], stdout=self.file, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.file.flush()
+        with open(self.file.name) as f:
+            rows = [r.strip().split(", ") for r in f if r.strip()]
+        os.unlink(self.file.name)
+        sm, smax, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            if len(r) < 9:
+                continue
+            try:
+                sm.append(float(r[1]))
+                smax = max(smax, float(r[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, r[5:9]):
+                if v.strip().lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ----------------------------------------------------------------- oracle (CPU)
+def _oracle_plane(args):
+    os.environ.setdefault("OMP_NUM_THREADS", "1")
+    import numpy as np
+    import oracle
+    phi, psfs, iters = args
+    t0 = time.perf_counter()
+    oracle.rl_planes(phi[:, None].astype(np.float64), psfs, iters, boundary="zero", eps=1e-6, route="fft")
+    return time.perf_counter() - t0
+
+
+def oracle_sample(pool, planes_np, psfs, iters):
+    """Oracle over the sampled planes [V][S][H][W], one plane per worker."""
+    t0 = time.perf_counter()
+    pool.map(_oracle_plane, [(planes_np[:, s], psfs, iters) for s in range(planes_np.shape[1])])
+    return time.perf_counter() - t0
+
+
+def n_workers():
+    try:
+        n = len(os.sched_getaffinity(0))
+    except Exception:
+        n = os.cpu_count() or 1
+    return max(1, min(n, 16))
+
+
+# ----------------------------------------------------------------- helpers
+def dist_setup(n_gpus):
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if torch.cuda.is_available():
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend)
+    elif torch.cuda.is_available():
+        torch.cuda.set_device(0)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def reduce_max(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], device="cuda" if torch.cuda.is_available() else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def make_inputs(wl, seed, device):
+    from paper_1503_07998_gb300 import synth
+    return synth.volume_stacks(wl["Z"], wl["Y"], wl["X"], wl["K"], wl["sigma_axial"], wl["sigma_lateral"],
+                               wl["angles"], wl["density"], seed=seed, device=device)
+
+
+def kernel_roofline(prof, name, units_per_launch, bytes_per_unit, flops_per_unit, hbm_peak):
+    total_ms, n = prof.get(name, (0.0, 0))
+    if not n:
+        return None
+    t = total_ms / n / 1e3
+    gbs = units_per_launch * bytes_per_unit / t / 1e9
+    tfl = units_per_launch * flops_per_unit / t / 1e12
+    return {"avg_ms": total_ms / n, "launches": n, "hbm_gbs": gbs, "hbm_frac": gbs / hbm_peak,
+            "tflops": tfl, "alu_frac": tfl / ALU_PEAK_TFLOPS,
+            "bytes_per_unit": bytes_per_unit, "flops_per_unit": flops_per_unit,
+            "units_per_launch": units_per_launch}
+
+
+# ----------------------------------------------------------------- arms
+def run_reference(args, wl):
+    world, rank, _ = dist_setup(args.gpus)
+    if rank != 0:
+        return 0
+    import numpy as np
+    import torch
+    S = n_workers()
+    ctx = mp.get_context("spawn")
+    pool = ctx.Pool(S)
+    dev = "cuda:0" if torch.cuda.is_available() else "cpu"
+    stacks, psfs = make_inputs(wl, wl["seed"], dev)
+    V = stacks.shape[0]
+    idx = np.linspace(0, wl["Y"] - 1, S).round().astype(int)
+    planes = stacks[:, :, idx, :].permute(0, 2, 1, 3).contiguous().cpu().to(torch.int32).numpy()
+    del stacks
+    for _ in range(args.warmup):
+        oracle_sample(pool, planes, psfs, wl["iters"])
+    times = [oracle_sample(pool, planes, psfs, wl["iters"]) for _ in range(args.steps)]
+    pool.close()
+    t = sum(times) / len(times)
+    units = S * wl["Z"] * wl["X"] * wl["iters"] * V
+    value = units / t
+    sample = f"{S} planes of the workload (one per process), FP64 FFT route, {wl['iters']} iterations"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": wl["label"], "sample": sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": S, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def run_mvd(args, wl):
+    import numpy as np
+    pool = None
+    S = n_workers()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if not args.no_cpu and world == 1:
+        pool = mp.get_context("spawn").Pool(S)     # before any GPU work
+    import torch
+    world, rank, local = dist_setup(args.gpus)
+    from paper_1503_07998_gb300 import mvd
+    dev = torch.device("cuda", torch.cuda.current_device())
+    stream = torch.cuda.current_stream(dev)
+    stacks, psfs = make_inputs(wl, wl["seed"] + rank, dev)
+    V, Z, Y, X = stacks.shape
+    K, iters = wl["K"], wl["iters"]
+    ctx = mvd.mvd_create(V, psfs, K, Z, X, iters, "zero", 1e-6)
+    info = mvd.mvd_get_info(ctx)
+    planes = torch.empty((V, Y, Z, X), dtype=stacks.dtype, device=dev)
+    est = torch.empty((Y, Z, X), dtype=torch.float32, device=dev)
+
+    def step():
+        mvd.mvd_reslice(ctx, stacks, planes)
+        mvd.mvd_deconvolve_planes(ctx, planes, est, init_mean=True)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    barrier(world)
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    mvd.mvd_profile_enable(ctx, True)
+    n0 = mvd.mvd_launch_count()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    barrier(world)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        step()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    ms = ev0.elapsed_time(ev1)
+    launches = mvd.mvd_launch_count() - n0
+    prof = mvd.mvd_profile_read(ctx)
+    mvd.mvd_profile_enable(ctx, False)
+    clk = clocks.stop()
+    ms_max = reduce_max(ms, world)
+    units_per_step = Y * Z * X * iters * V
+    value = units_per_step * world * args.steps / (ms_max / 1e3)
+
+    # roofline of the dominant kernel
+    hbm_peak, hbm_src = _peaks()
+    vi_per_launch = Y * Z * X
+    # 2K flop per output of each 1D pass, two passes per SVD term
+    flops_a = 4 * K * info.blur_terms            # one blur per distinct PSF
+    flops_b = 4 * K * sum(info.rank[:V])         # one correlation per view
+    es = 2 if stacks.dtype == torch.uint16 else 4
+    kr = {
+        "blur_ratio": kernel_roofline(prof, "blur_ratio", vi_per_launch, 4 + (es + 4) * V, flops_a, hbm_peak),
+        "correlate_update": kernel_roofline(prof, "correlate_update", vi_per_launch, 4 * V + 8, flops_b, hbm_peak),
+        "reslice": kernel_roofline(prof, "reslice", Y * Z * X * V, 2 * es, 0, hbm_peak),
+    }
+    dom = max((k for k in kr if kr[k]), key=lambda k: kr[k]["avg_ms"] * kr[k]["launches"])
+    d = kr[dom]
+    if d["alu_frac"] >= d["hbm_frac"]:
+        roof = {"bound": "alu", "achieved": d["tflops"], "peak": ALU_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": d["alu_frac"], "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz"}
+    else:
+        roof = {"bound": "hbm", "achieved": d["hbm_gbs"], "peak": hbm_peak, "unit": "GB/s",
+                "frac": d["hbm_frac"], "peak_source": hbm_src}
+    roof.update({"kernel": dom, "traffic": NCU_TRAFFIC_PER_LAUNCH.get(dom),
+                 "hbm_gbs": d["hbm_gbs"], "hbm_frac": d["hbm_frac"], "avg_launch_ms": d["avg_ms"]})
+
+    # plain per-plane path on a slice of the planes (same context and factors)
+    plain = None
+    if not args.no_plain:
+        sub = min(Y, 32)
+        mvd.mvd_set_algo(ctx, "plain")
+        e2 = est[:sub].contiguous()
+        p2 = planes[:, :sub].contiguous()
+        mvd.mvd_deconvolve_planes(ctx, p2, e2)
+        torch.cuda.synchronize()
+        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        mvd.mvd_deconvolve_planes(ctx, p2, e2)
+        a1.record(stream)
+        torch.cuda.synchronize()
+        pms = a0.elapsed_time(a1)
+        mvd.mvd_set_algo(ctx, "fused")
+        fused_ms = sum(v[0] for k, v in prof.items() if k in ("blur_ratio", "correlate_update", "plane_means"))
+        fused_ms_per_plane = fused_ms / args.steps / Y
+        plain_val = sub * Z * X * iters * V / (pms / 1e3)
+        plain = {"value": plain_val, "unit": UNIT, "planes": sub,
+                 "speedup_of_fused": (pms / sub) / fused_ms_per_plane}
+
+    # end to end through host buffers (pinned)
+    e2e = None
+    if not args.no_e2e:
+        host_in = stacks.cpu().pin_memory()
+        host_out = torch.empty((Y, Z, X), dtype=torch.float32).pin_memory()
+        mvd.mvd_run_host(ctx, host_in, host_out)
+        torch.cuda.synchronize()
+        barrier(world)
+        ne = max(1, min(args.steps, 5))
+        t0 = time.perf_counter()
+        for _ in range(ne):
+            mvd.mvd_run_host(ctx, host_in, host_out)
+        torch.cuda.synchronize()
+        te = reduce_max((time.perf_counter() - t0) / ne, world)
+        e2e = {"value": units_per_step * world / te, "unit": UNIT,
+               "h2d_bytes_per_step": int(host_in.numel() * host_in.element_size()),
+               "d2h_bytes_per_step": int(host_out.numel() * host_out.element_size()),
+               "ms_per_step": te * 1e3}
+
+    cpu = None
+    if pool is not None and rank == 0:
+        idx = np.linspace(0, Y - 1, S).round().astype(int)
+        sample_planes = planes[:, idx].cpu().to(torch.int32).numpy()
+        t = oracle_sample(pool, sample_planes, psfs, iters)
+        pool.close()
+        cpu = {"value": S * Z * X * iters * V / t, "unit": UNIT, "cores": S, "kind": "oracle",
+               "sample": f"{S} of the {Y} planes (one per process), FP64 FFT route, {iters} iterations"}
+
+    ctx.close()
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": wl["label"], "views": V, "volume": [Z, Y, X], "psf": K, "iters": iters,
+                           "planes_per_gpu": Y, "data_dtype": "u16",
+                           "l2": "inputs larger than L2: 512 MiB of stacks + 512 MiB of planes per step",
+                           "parallelism": f"{world} GPU(s), one independent volume per GPU, no collective"},
+                "voxel_iterations_per_s": value / V,
+                "roofline": roof, "kernels": kr, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": int(launches), "clocks": clk, "plain_per_plane": plain,
+                "paper_context": "GTX TITAN Black, 2 views, 1024^3 padded, 10 it: 21.1 s = 1.02e9 voxel-view-it/s "
+                                 "(Supp. Table 1); another machine, not the target"}
+        print(json.dumps(line))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="mvd", choices=["mvd", "reference"])
+    ap.add_argument("--workload", default="volume512", choices=sorted(WORKLOADS))
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-plain", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        print("note: at least 3 warm-up steps are used", file=sys.stderr)
+        args.warmup = 3
+    wl = WORKLOADS[args.workload]
+    if args.impl == "reference":
+        return run_reference(args, wl)
+    return run_mvd(args, wl)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,198 @@
+/*
+ * mvd.h -- C ABI of a GB300 (sm_103a) library for plane-wise multi-view
+ * Richardson-Lucy (MV-RL) deconvolution.
+ *
+ * The method (Schmid & Huisken, "Real-time multi-view deconvolution"):
+ *   - every registered view stack is resliced into planes orthogonal to the
+ *     rotation axis (Abstract; Fig. 1a);
+ *   - every plane is deconvolved independently with one 2D PSF per view
+ *     (Results: the 3D transfer function is approximated by a 2D PSF);
+ *   - one iteration is the multi-view RL update of Supp. Note 1:
+ *         psi <- psi * prod_v [ (phi_v / (psi * P_v)) (*) P_v^* ]
+ *     with P_v^* the flipped PSF (Supp. Note 2, sec. 1).
+ *
+ * Conventions used by every entry point
+ *   - Pointers named *_dev are device pointers on the device that was current
+ *     when the context was created; pointers named *_host are host pointers.
+ *     All buffers passed in are owned by the caller; the library never frees
+ *     or keeps them after the call returns.
+ *   - Layouts are dense, row-major, the last index contiguous:
+ *       stack   [V][Z][Y][X]   registered view stacks (z-slices of Y x X)
+ *       planes  [V][P][H][W]   resliced data, P = Y planes of H = Z rows and
+ *                              W = X columns
+ *       estimate [P][H][W]     FP32
+ *   - PSFs are K x K, K odd, centre (R, R) with R = (K-1)/2, row index along
+ *     the plane's rows.  Convolution: b(y,x) = sum_ij P[i][j] psi(y-i+R, x-j+R).
+ *   - Device work is asynchronous on the given stream (a cudaStream_t; NULL is
+ *     the legacy default stream), like the paper's workflow (Supp. Note 2,
+ *     sec. 3).  Argument errors are found before anything is enqueued.
+ *   - Every function returns a status; nothing is thrown across the ABI.
+ *     mvd_last_error() gives a human-readable detail for the calling thread.
+ *   - A context may be used from one host thread at a time.
+ */
+#ifndef MVD_H
+#define MVD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mvd_ctx mvd_ctx;
+
+typedef enum {
+    MVD_OK = 0,
+    MVD_ERR_ARG = 1,          /* an argument is invalid (see mvd_last_error) */
+    MVD_ERR_CUDA = 2,         /* a CUDA call or kernel launch failed         */
+    MVD_ERR_NOMEM = 3,        /* a device or host allocation failed           */
+    MVD_ERR_TIMEOUT = 4,      /* a bounded device-side wait ran out           */
+    MVD_ERR_STATE = 5,        /* the call is not valid in this state          */
+    MVD_ERR_UNSUPPORTED = 6   /* the selected route cannot take these sizes   */
+} mvd_status;
+
+typedef enum {
+    /* Outside the plane the estimate and the ratio are zero: the linear
+     * convolution cropped to the plane, which is what padding each plane by
+     * the PSF size for Fourier convolution implements (Supp. Table 1). */
+    MVD_BOUNDARY_ZERO = 0,
+    /* Plane indices are taken modulo H and W (needs K <= min(H, W)). */
+    MVD_BOUNDARY_CIRCULAR = 1
+} mvd_boundary;
+
+typedef enum {
+    MVD_U16 = 0,   /* camera data, uint16 (Supp. Note 1 memory table) */
+    MVD_F32 = 1
+} mvd_dtype;
+
+typedef enum {
+    /* Fused tiled path: per iteration one kernel blurs the estimate with
+     * every view's PSF and forms the ratios, a second correlates, multiplies
+     * the views' corrections and updates the estimate, for all planes in one
+     * launch.  PSFs are used through an exact FP64 SVD factorisation
+     * P = sum_q s_q u_q w_q^T truncated only below FP32 resolution. */
+    MVD_ALGO_FUSED = 0,
+    /* Plain per-plane path: one plane at a time, one kernel per step
+     * (vertical pass, horizontal pass, ratio, ... , update), same factors.
+     * Kept as the comparison baseline. */
+    MVD_ALGO_PLAIN = 1,
+    /* Plain per-plane path with K x K direct convolutions (no factorisation). */
+    MVD_ALGO_DIRECT = 2
+} mvd_algo;
+
+/* Summary of what a context decided; filled by mvd_get_info. */
+typedef struct {
+    int views;
+    int psf_size;
+    int plane_h, plane_w;
+    int iters;
+    int boundary;
+    int algo;                   /* mvd_algo in use                          */
+    int rank[16];               /* SVD terms kept per view (first 16 views) */
+    int blur_groups;            /* number of distinct PSFs among the views  */
+    int blur_terms;             /* SVD terms summed over distinct PSFs      */
+    int tile_h, tile_w;         /* fused path output tile                   */
+    size_t workspace_bytes;     /* device scratch currently held            */
+} mvd_info;
+
+/* Create a context for `views` views with K x K PSFs psfs_host[V][K][K]
+ * (FP32, host memory, copied), planes of plane_h x plane_w pixels, `iters`
+ * RL iterations, the given boundary and division guard eps
+ * (ratio = phi / max(blur, eps)).
+ *
+ * Errors (MVD_ERR_ARG): views < 1 or > 64, K even or < 1, plane sizes < 1,
+ * iters < 0, eps <= 0 or not finite, a PSF entry negative or not finite, a
+ * PSF with sum <= 0, CIRCULAR with K > min(plane_h, plane_w).
+ * The context binds to the current CUDA device. */
+mvd_status mvd_create(mvd_ctx **out, int views, const float *psfs_host, int psf_size,
+                      int plane_h, int plane_w, int iters, mvd_boundary boundary, float eps);
+
+/* Release the context and every device buffer it owns.  NULL is accepted. */
+mvd_status mvd_destroy(mvd_ctx *ctx);
+
+/* Select the route (default MVD_ALGO_FUSED).  MVD_ERR_UNSUPPORTED if the
+ * fused path cannot take this PSF size (it takes K <= 47). */
+mvd_status mvd_set_algo(mvd_ctx *ctx, mvd_algo algo);
+
+/* Relative Frobenius tolerance below which trailing SVD terms of a PSF are
+ * dropped (default 3e-7, below the FP32 rounding of the PSF's entries).
+ * 0 keeps every non-zero term. */
+mvd_status mvd_set_rank_tolerance(mvd_ctx *ctx, double tol);
+
+mvd_status mvd_get_info(const mvd_ctx *ctx, mvd_info *info);
+
+/* Reslicing (Abstract; Fig. 1a): stacks_dev [V][Z][Y][X] of dtype dt ->
+ * planes_dev [V][Y][Z][X], i.e. plane y holds rows z and columns x.  The
+ * rotation axis is the stacks' middle axis Y.  Buffers must not overlap.
+ * Sizes are independent of the context's plane shape. */
+mvd_status mvd_reslice(mvd_ctx *ctx, const void *stacks_dev, mvd_dtype dt, int views,
+                       int nz, int ny, int nx, void *planes_dev, void *stream);
+
+/* Run the context's `iters` MV-RL iterations (Supp. Note 1) on n_planes
+ * independent planes.
+ *   data_dev     [V][n_planes][H][W] of dtype dt (H, W = the context's plane)
+ *   estimate_dev [n_planes][H][W] FP32.  If init_mean != 0 it is ignored on
+ *                entry and every plane starts from the mean of that plane's
+ *                pixels over all views (computed in FP64); else it holds the
+ *                initial estimate.  On return (stream order) it holds the
+ *                result.  It must not overlap data_dev.
+ * The context keeps device scratch sized for the largest n_planes seen
+ * (one estimate copy plus V ratio planes per plane). */
+mvd_status mvd_deconvolve_planes(mvd_ctx *ctx, const void *data_dev, mvd_dtype dt,
+                                 float *estimate_dev, int n_planes, int init_mean,
+                                 void *stream);
+
+/* End-to-end call on host buffers: stacks_host [V][Z][Y][X] (dt) ->
+ * out_host [Y][Z][X] FP32 (Z = H, X = W of the context), i.e. copy to the
+ * device, reslice, deconvolve from the per-plane mean and copy back.  Planes
+ * move in chunks of `chunk_planes` (0 = automatic) so that copies in both
+ * directions overlap the iterations of other chunks (the paper's interleaved
+ * workflow, Supp. Note 2 sec. 3, with device memory instead of disk).  Host
+ * buffers should be page-locked for full copy speed.  Returns when out_host
+ * is complete. */
+mvd_status mvd_run_host(mvd_ctx *ctx, const void *stacks_host, mvd_dtype dt,
+                        int nz, int ny, int nx, float *out_host, int chunk_planes,
+                        void *stream);
+
+/* Per-kernel device time of this context's launches, taken with CUDA events
+ * recorded on the launching stream around every kernel.  Enabling (on != 0)
+ * or disabling clears what was collected.  mvd_profile_read waits for the
+ * recorded events, then fills up to `capacity` entries (one per kernel
+ * name) and sets *count to the number of names. */
+typedef struct {
+    char name[32];
+    double total_ms;
+    uint64_t launches;
+} mvd_kernel_stat;
+
+mvd_status mvd_profile_enable(mvd_ctx *ctx, int on);
+mvd_status mvd_profile_read(mvd_ctx *ctx, mvd_kernel_stat *out, int capacity, int *count);
+
+/* Host-only: the separable factorisation the library uses for the PSFs of
+ * psfs_host [V][K][K] (FP64 one-sided Jacobi SVD, terms dropped below
+ * rank_tol relative Frobenius norm).  rank_out[V] receives the terms kept
+ * per view; taps_out (capacity `taps_capacity` floats, V*K*4*K suffices)
+ * receives, per kept term in view order, four K-vectors: the vertical factor
+ * (singular value folded in) reversed, the horizontal factor reversed, the
+ * vertical factor and the horizontal factor, so that
+ *     P[i][j] = sum_q u_q[i] * w_q[j]   with u_q = block 2, w_q = block 3.
+ * Views with bitwise-identical PSFs share the first such view's terms, which
+ * are stored once.  Needs no GPU. */
+mvd_status mvd_psf_factors(const float *psfs_host, int views, int psf_size, double rank_tol,
+                           int *rank_out, float *taps_out, int taps_capacity);
+
+const char *mvd_status_string(mvd_status s);
+
+/* Detail of the last error raised on the calling thread ("" if none). */
+const char *mvd_last_error(void);
+
+/* Number of kernels this library has launched in this process (all
+ * contexts, all threads); used to count launches inside a timed region. */
+uint64_t mvd_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MVD_H */

@@ -1,0 +1,561 @@
+// C ABI of the library (declared in include/mvd.h): context life cycle,
+// argument checking, workspace, and the sequencing of kernels for one call.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/mvd.h"
+#include "mvd_internal.h"
+
+namespace mvd {
+
+static std::atomic<uint64_t> g_launches{0};
+void count_launch(int n) { g_launches.fetch_add(static_cast<uint64_t>(n), std::memory_order_relaxed); }
+
+}  // namespace mvd
+
+namespace {
+
+thread_local std::string t_last_error;
+
+mvd_status fail(mvd_status s, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    std::vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    t_last_error = buf;
+    return s;
+}
+
+mvd_status cuda_fail(cudaError_t e, const char *what) {
+    return fail(MVD_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+struct DeviceGuard {
+    int prev = -1, want;
+    explicit DeviceGuard(int d) : want(d) {
+        cudaGetDevice(&prev);
+        if (prev != want) cudaSetDevice(want);
+    }
+    ~DeviceGuard() {
+        if (prev >= 0 && prev != want) cudaSetDevice(prev);
+    }
+};
+
+// Device buffer that only grows.
+struct DevBuf {
+    void *ptr = nullptr;
+    size_t bytes = 0;
+    cudaError_t ensure(size_t want) {
+        if (want <= bytes) return cudaSuccess;
+        if (ptr) {
+            cudaFree(ptr);
+            ptr = nullptr;
+            bytes = 0;
+        }
+        cudaError_t e = cudaMalloc(&ptr, want);
+        if (e == cudaSuccess) bytes = want;
+        return e;
+    }
+    void release() {
+        if (ptr) cudaFree(ptr);
+        ptr = nullptr;
+        bytes = 0;
+    }
+    template <typename T>
+    T *as() const { return static_cast<T *>(ptr); }
+};
+
+constexpr double kDefaultRankTol = 3e-7;
+
+// CUDA-event timing of every launch of a context (mvd_profile_*): an event is
+// recorded before each launch, labelled with the kernel that follows it, and
+// one after the last; the time between consecutive events is the labelled
+// kernel's device time.
+struct Profiler {
+    bool on = false;
+    std::vector<cudaEvent_t> pool, all;
+    std::vector<std::pair<cudaEvent_t, int>> marks;
+    std::vector<std::string> names;
+    std::vector<double> ms;
+    std::vector<uint64_t> count;
+    int label(const char *name) {
+        for (size_t i = 0; i < names.size(); ++i)
+            if (names[i] == name) return static_cast<int>(i);
+        names.emplace_back(name);
+        ms.push_back(0.0);
+        count.push_back(0);
+        return static_cast<int>(names.size() - 1);
+    }
+    void mark(cudaStream_t s, const char *name) {
+        if (!on) return;
+        cudaEvent_t e;
+        if (pool.empty()) {
+            if (cudaEventCreate(&e) != cudaSuccess) return;
+            all.push_back(e);
+        } else {
+            e = pool.back();
+            pool.pop_back();
+        }
+        cudaEventRecord(e, s);
+        marks.emplace_back(e, name ? label(name) : -1);
+    }
+    void end(cudaStream_t s) { mark(s, nullptr); }
+    void resolve() {
+        if (!marks.empty()) cudaEventSynchronize(marks.back().first);
+        for (size_t i = 0; i + 1 < marks.size(); ++i) {
+            if (marks[i].second < 0) continue;
+            float t = 0;
+            if (cudaEventElapsedTime(&t, marks[i].first, marks[i + 1].first) == cudaSuccess) {
+                ms[marks[i].second] += t;
+                count[marks[i].second] += 1;
+            }
+        }
+        for (auto &m : marks) pool.push_back(m.first);
+        marks.clear();
+    }
+    void reset() {
+        resolve();
+        names.clear();
+        ms.clear();
+        count.clear();
+    }
+    void destroy() {
+        for (auto e : all) cudaEventDestroy(e);
+        all.clear();
+        pool.clear();
+        marks.clear();
+    }
+};
+
+}  // namespace
+
+struct mvd_ctx {
+    int device = 0;
+    int V = 0, K = 0, H = 0, W = 0, iters = 0;
+    mvd_boundary boundary = MVD_BOUNDARY_ZERO;
+    float eps = 1e-6f;
+    mvd_algo algo = MVD_ALGO_FUSED;
+    double rank_tol = kDefaultRankTol;
+    std::vector<float> psfs;
+    mvd::FactorTable ft;
+    DevBuf taps, psf_dev, means, ratio, plain;
+    // end-to-end pipeline
+    DevBuf run_stack[2], run_planes, run_est[2];
+    cudaStream_t copy_in = nullptr, copy_out = nullptr;
+    Profiler prof;
+};
+
+namespace {
+
+mvd_status upload_factors(mvd_ctx *c) {
+    const int cap = mvd::max_terms(c->V, c->K) * 4 * c->K;
+    std::vector<float> taps(static_cast<size_t>(cap));
+    char msg[256] = {0};
+    if (!mvd::factorise_psfs(c->psfs.data(), c->V, c->K, c->rank_tol, c->ft, taps.data(), cap, msg, sizeof msg))
+        return fail(MVD_ERR_ARG, "PSF factorisation failed: %s", msg);
+    const size_t bytes = static_cast<size_t>(c->ft.total_terms) * 4 * c->K * sizeof(float);
+    cudaError_t e = c->taps.ensure(bytes);
+    if (e != cudaSuccess) return fail(MVD_ERR_NOMEM, "taps: %s", cudaGetErrorString(e));
+    e = cudaMemcpy(c->taps.ptr, taps.data(), bytes, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(e, "upload taps");
+    return MVD_OK;
+}
+
+mvd::FusedArgs fused_args(const mvd_ctx *c, const void *data, mvd_dtype dt, float *est, int P) {
+    mvd::FusedArgs a{};
+    a.psi_in = est;
+    a.means = c->means.as<float>();
+    a.psi_out = est;
+    a.phi = data;
+    a.phi_u16 = dt == MVD_U16;
+    a.ratio = c->ratio.as<float>();
+    a.taps = c->taps.as<float>();
+    a.ft = c->ft;
+    a.H = c->H;
+    a.W = c->W;
+    a.P = P;
+    a.circular = c->boundary == MVD_BOUNDARY_CIRCULAR;
+    a.eps = c->eps;
+    return a;
+}
+
+mvd_status run_fused(mvd_ctx *c, const void *data, mvd_dtype dt, float *est, int P, int init_mean,
+                     cudaStream_t s) {
+    const size_t plane_px = static_cast<size_t>(c->H) * c->W;
+    cudaError_t e = c->ratio.ensure(static_cast<size_t>(c->V) * P * plane_px * sizeof(float));
+    if (e != cudaSuccess) return fail(MVD_ERR_NOMEM, "ratio workspace: %s", cudaGetErrorString(e));
+    mvd::FusedArgs a = fused_args(c, data, dt, est, P);
+    if (c->iters == 0 && init_mean) {
+        for (int p = 0; p < P; ++p) {
+            e = mvd::plain_fill(est + p * plane_px, a.means, p, plane_px, s);
+            if (e != cudaSuccess) return cuda_fail(e, "fill");
+        }
+        return MVD_OK;
+    }
+    for (int t = 0; t < c->iters; ++t) {
+        a.psi_in = (t == 0 && init_mean) ? nullptr : est;
+        c->prof.mark(s, "blur_ratio");
+        e = mvd::launch_fused_blur_ratio(a, s);
+        if (e != cudaSuccess) return cuda_fail(e, "blur/ratio kernel");
+        c->prof.mark(s, "correlate_update");
+        e = mvd::launch_fused_correlate_update(a, s);
+        if (e != cudaSuccess) return cuda_fail(e, "correlate/update kernel");
+    }
+    c->prof.end(s);
+    return MVD_OK;
+}
+
+mvd_status run_plain(mvd_ctx *c, const void *data, mvd_dtype dt, float *est, int P, int init_mean,
+                     int direct, cudaStream_t s) {
+    const size_t n = static_cast<size_t>(c->H) * c->W;
+    cudaError_t e = c->plain.ensure(4 * n * sizeof(float));
+    if (e != cudaSuccess) return fail(MVD_ERR_NOMEM, "plain workspace: %s", cudaGetErrorString(e));
+    if (direct && !c->psf_dev.ptr) {
+        e = c->psf_dev.ensure(c->psfs.size() * sizeof(float));
+        if (e != cudaSuccess) return fail(MVD_ERR_NOMEM, "psf copy: %s", cudaGetErrorString(e));
+        e = cudaMemcpy(c->psf_dev.ptr, c->psfs.data(), c->psfs.size() * sizeof(float), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) return cuda_fail(e, "upload psfs");
+    }
+    float *b = c->plain.as<float>(), *tmp = b + n, *cv = b + 2 * n, *prod = b + 3 * n;
+    mvd::PlainArgs a{};
+    a.taps = c->taps.as<float>();
+    a.psf_dev = c->psf_dev.as<float>();
+    a.ft = c->ft;
+    a.H = c->H;
+    a.W = c->W;
+    a.circular = c->boundary == MVD_BOUNDARY_CIRCULAR;
+    a.eps = c->eps;
+    const int u16 = dt == MVD_U16;
+    const size_t esz = u16 ? 2 : 4;
+    for (int p = 0; p < P; ++p) {
+        float *psi = est + p * n;
+        if (init_mean) {
+            e = mvd::plain_fill(psi, c->means.as<float>(), p, n, s);
+            if (e != cudaSuccess) return cuda_fail(e, "fill");
+        }
+        for (int t = 0; t < c->iters; ++t) {
+            c->prof.mark(s, direct ? "direct_iteration" : "plain_iteration");
+            for (int v = 0; v < c->V; ++v) {
+                const char *phi = static_cast<const char *>(data) + (static_cast<size_t>(v) * P + p) * n * esz;
+                if ((e = mvd::plain_convolve(a, v, 0, direct, psi, tmp, b, s)) != cudaSuccess) return cuda_fail(e, "blur");
+                if ((e = mvd::plain_ratio(phi, u16, b, b, n, c->eps, s)) != cudaSuccess) return cuda_fail(e, "ratio");
+                if ((e = mvd::plain_convolve(a, v, 1, direct, b, tmp, cv, s)) != cudaSuccess) return cuda_fail(e, "correlate");
+                if ((e = mvd::plain_multiply(prod, cv, n, v == 0, s)) != cudaSuccess) return cuda_fail(e, "product");
+            }
+            if ((e = mvd::plain_update(psi, prod, n, s)) != cudaSuccess) return cuda_fail(e, "update");
+        }
+    }
+    c->prof.end(s);
+    return MVD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *mvd_status_string(mvd_status s) {
+    switch (s) {
+        case MVD_OK: return "ok";
+        case MVD_ERR_ARG: return "invalid argument";
+        case MVD_ERR_CUDA: return "CUDA error";
+        case MVD_ERR_NOMEM: return "out of memory";
+        case MVD_ERR_TIMEOUT: return "device-side wait timed out";
+        case MVD_ERR_STATE: return "invalid state";
+        case MVD_ERR_UNSUPPORTED: return "unsupported by the selected route";
+    }
+    return "unknown status";
+}
+
+const char *mvd_last_error(void) { return t_last_error.c_str(); }
+
+mvd_status mvd_profile_enable(mvd_ctx *c, int on) {
+    if (!c) return fail(MVD_ERR_ARG, "ctx is NULL");
+    DeviceGuard g(c->device);
+    c->prof.reset();
+    c->prof.on = on != 0;
+    return MVD_OK;
+}
+
+mvd_status mvd_profile_read(mvd_ctx *c, mvd_kernel_stat *out, int capacity, int *count) {
+    if (!c || !count || (capacity > 0 && !out)) return fail(MVD_ERR_ARG, "NULL argument");
+    DeviceGuard g(c->device);
+    c->prof.resolve();
+    const int n = static_cast<int>(c->prof.names.size());
+    for (int i = 0; i < n && i < capacity; ++i) {
+        std::memset(&out[i], 0, sizeof out[i]);
+        std::snprintf(out[i].name, sizeof out[i].name, "%s", c->prof.names[i].c_str());
+        out[i].total_ms = c->prof.ms[i];
+        out[i].launches = c->prof.count[i];
+    }
+    *count = n;
+    return MVD_OK;
+}
+
+mvd_status mvd_psf_factors(const float *psfs, int views, int K, double tol, int *rank_out, float *taps_out,
+                           int cap) {
+    t_last_error.clear();
+    if (!psfs || !rank_out || !taps_out) return fail(MVD_ERR_ARG, "NULL argument");
+    if (views < 1 || views > mvd::kMaxViews || K < 1 || K % 2 == 0) return fail(MVD_ERR_ARG, "bad sizes");
+    if (!(tol >= 0.0)) return fail(MVD_ERR_ARG, "tolerance must be >= 0");
+    mvd::FactorTable ft;
+    char msg[256] = {0};
+    if (!mvd::factorise_psfs(psfs, views, K, tol, ft, taps_out, cap, msg, sizeof msg))
+        return fail(MVD_ERR_ARG, "%s", msg);
+    for (int v = 0; v < views; ++v) rank_out[v] = ft.rank[v];
+    return MVD_OK;
+}
+
+uint64_t mvd_launch_count(void) { return mvd::g_launches.load(std::memory_order_relaxed); }
+
+mvd_status mvd_create(mvd_ctx **out, int views, const float *psfs_host, int psf_size, int plane_h, int plane_w,
+                      int iters, mvd_boundary boundary, float eps) {
+    t_last_error.clear();
+    if (!out) return fail(MVD_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (views < 1 || views > mvd::kMaxViews) return fail(MVD_ERR_ARG, "views must be in [1, %d]", mvd::kMaxViews);
+    if (!psfs_host) return fail(MVD_ERR_ARG, "psfs is NULL");
+    if (psf_size < 1 || psf_size % 2 == 0) return fail(MVD_ERR_ARG, "PSF size must be odd and >= 1 (got %d)", psf_size);
+    if (plane_h < 1 || plane_w < 1) return fail(MVD_ERR_ARG, "plane size must be positive");
+    if (iters < 0) return fail(MVD_ERR_ARG, "iters must be >= 0");
+    if (!(eps > 0.0f) || !std::isfinite(eps)) return fail(MVD_ERR_ARG, "eps must be positive and finite");
+    if (boundary != MVD_BOUNDARY_ZERO && boundary != MVD_BOUNDARY_CIRCULAR) return fail(MVD_ERR_ARG, "unknown boundary");
+    if (boundary == MVD_BOUNDARY_CIRCULAR && (psf_size > plane_h || psf_size > plane_w))
+        return fail(MVD_ERR_ARG, "circular boundary needs K <= min(H, W)");
+    const size_t KK = static_cast<size_t>(psf_size) * psf_size;
+    for (int v = 0; v < views; ++v) {
+        double sum = 0;
+        for (size_t i = 0; i < KK; ++i) {
+            const float x = psfs_host[v * KK + i];
+            if (!std::isfinite(x)) return fail(MVD_ERR_ARG, "PSF %d has a non-finite entry", v);
+            if (x < 0) return fail(MVD_ERR_ARG, "PSF %d has a negative entry", v);
+            sum += x;
+        }
+        if (!(sum > 0)) return fail(MVD_ERR_ARG, "PSF %d sums to zero", v);
+    }
+    auto *c = new (std::nothrow) mvd_ctx();
+    if (!c) return fail(MVD_ERR_NOMEM, "context");
+    cudaError_t e = cudaGetDevice(&c->device);
+    if (e != cudaSuccess) {
+        delete c;
+        return cuda_fail(e, "cudaGetDevice");
+    }
+    c->V = views;
+    c->K = psf_size;
+    c->H = plane_h;
+    c->W = plane_w;
+    c->iters = iters;
+    c->boundary = boundary;
+    c->eps = eps;
+    c->algo = mvd::fused_supported(psf_size) ? MVD_ALGO_FUSED : MVD_ALGO_PLAIN;
+    c->psfs.assign(psfs_host, psfs_host + views * KK);
+    mvd_status s = upload_factors(c);
+    if (s != MVD_OK) {
+        mvd_destroy(c);
+        return s;
+    }
+    *out = c;
+    return MVD_OK;
+}
+
+mvd_status mvd_destroy(mvd_ctx *c) {
+    if (!c) return MVD_OK;
+    DeviceGuard g(c->device);
+    c->taps.release();
+    c->psf_dev.release();
+    c->means.release();
+    c->ratio.release();
+    c->plain.release();
+    for (auto &b : c->run_stack) b.release();
+    for (auto &b : c->run_est) b.release();
+    c->run_planes.release();
+    c->prof.destroy();
+    if (c->copy_in) cudaStreamDestroy(c->copy_in);
+    if (c->copy_out) cudaStreamDestroy(c->copy_out);
+    delete c;
+    return MVD_OK;
+}
+
+mvd_status mvd_set_algo(mvd_ctx *c, mvd_algo algo) {
+    if (!c) return fail(MVD_ERR_ARG, "ctx is NULL");
+    if (algo != MVD_ALGO_FUSED && algo != MVD_ALGO_PLAIN && algo != MVD_ALGO_DIRECT)
+        return fail(MVD_ERR_ARG, "unknown algo %d", static_cast<int>(algo));
+    if (algo == MVD_ALGO_FUSED && !mvd::fused_supported(c->K))
+        return fail(MVD_ERR_UNSUPPORTED, "fused path takes K <= %d (got %d)", mvd::kFusedMaxK, c->K);
+    c->algo = algo;
+    return MVD_OK;
+}
+
+mvd_status mvd_set_rank_tolerance(mvd_ctx *c, double tol) {
+    if (!c) return fail(MVD_ERR_ARG, "ctx is NULL");
+    if (!(tol >= 0.0) || !std::isfinite(tol)) return fail(MVD_ERR_ARG, "tolerance must be >= 0");
+    DeviceGuard g(c->device);
+    c->rank_tol = tol;
+    return upload_factors(c);
+}
+
+mvd_status mvd_get_info(const mvd_ctx *c, mvd_info *info) {
+    if (!c || !info) return fail(MVD_ERR_ARG, "NULL argument");
+    std::memset(info, 0, sizeof *info);
+    info->views = c->V;
+    info->psf_size = c->K;
+    info->plane_h = c->H;
+    info->plane_w = c->W;
+    info->iters = c->iters;
+    info->boundary = c->boundary;
+    info->algo = c->algo;
+    for (int v = 0; v < c->V && v < 16; ++v) info->rank[v] = c->ft.rank[v];
+    info->blur_groups = c->ft.n_groups;
+    info->blur_terms = c->ft.total_terms;
+    mvd::fused_tile_shape(c->K, &info->tile_h, &info->tile_w);
+    info->workspace_bytes = c->taps.bytes + c->psf_dev.bytes + c->means.bytes + c->ratio.bytes + c->plain.bytes +
+                            c->run_stack[0].bytes + c->run_stack[1].bytes + c->run_planes.bytes +
+                            c->run_est[0].bytes + c->run_est[1].bytes;
+    return MVD_OK;
+}
+
+mvd_status mvd_reslice(mvd_ctx *c, const void *stacks, mvd_dtype dt, int views, int nz, int ny, int nx,
+                       void *planes, void *stream) {
+    t_last_error.clear();
+    if (!c) return fail(MVD_ERR_ARG, "ctx is NULL");
+    if (!stacks || !planes) return fail(MVD_ERR_ARG, "NULL buffer");
+    if (dt != MVD_U16 && dt != MVD_F32) return fail(MVD_ERR_ARG, "unknown dtype");
+    if (views < 1 || nz < 0 || ny < 0 || nx < 0) return fail(MVD_ERR_ARG, "bad sizes");
+    if (static_cast<long long>(nz) * ny * nx == 0) return MVD_OK;
+    const size_t es = dt == MVD_U16 ? 2 : 4;
+    const char *a = static_cast<const char *>(stacks), *b = static_cast<const char *>(planes);
+    const size_t bytes = static_cast<size_t>(views) * nz * ny * nx * es;
+    if (a < b + bytes && b < a + bytes) return fail(MVD_ERR_ARG, "stacks and planes overlap");
+    DeviceGuard g(c->device);
+    c->prof.mark(static_cast<cudaStream_t>(stream), "reslice");
+    cudaError_t e = mvd::launch_reslice(stacks, planes, static_cast<int>(es), views, nz, ny, nx,
+                                        static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(e, "reslice kernel");
+    c->prof.end(static_cast<cudaStream_t>(stream));
+    return MVD_OK;
+}
+
+mvd_status mvd_deconvolve_planes(mvd_ctx *c, const void *data, mvd_dtype dt, float *est, int n_planes, int init_mean,
+                                 void *stream) {
+    t_last_error.clear();
+    if (!c) return fail(MVD_ERR_ARG, "ctx is NULL");
+    if (dt != MVD_U16 && dt != MVD_F32) return fail(MVD_ERR_ARG, "unknown dtype");
+    if (n_planes < 0) return fail(MVD_ERR_ARG, "n_planes must be >= 0");
+    if (n_planes == 0) return MVD_OK;
+    if (!data || !est) return fail(MVD_ERR_ARG, "NULL buffer");
+    if (n_planes > 65535) return fail(MVD_ERR_ARG, "at most 65535 planes per call");
+    const size_t n = static_cast<size_t>(c->H) * c->W;
+    const size_t es = dt == MVD_U16 ? 2 : 4;
+    const char *d0 = static_cast<const char *>(data), *e0 = reinterpret_cast<const char *>(est);
+    const size_t dbytes = static_cast<size_t>(c->V) * n_planes * n * es, ebytes = n_planes * n * sizeof(float);
+    if (d0 < e0 + ebytes && e0 < d0 + dbytes) return fail(MVD_ERR_ARG, "data and estimate overlap");
+    DeviceGuard g(c->device);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaError_t e;
+    if (init_mean) {
+        if ((e = c->means.ensure(static_cast<size_t>(n_planes) * sizeof(float))) != cudaSuccess)
+            return fail(MVD_ERR_NOMEM, "means: %s", cudaGetErrorString(e));
+        c->prof.mark(s, "plane_means");
+        if ((e = mvd::launch_plane_means(data, dt == MVD_U16, c->V, n_planes, c->H, c->W, c->means.as<float>(), s)) !=
+            cudaSuccess)
+            return cuda_fail(e, "plane means kernel");
+        c->prof.end(s);
+    }
+    if (c->algo == MVD_ALGO_FUSED) return run_fused(c, data, dt, est, n_planes, init_mean, s);
+    return run_plain(c, data, dt, est, n_planes, init_mean, c->algo == MVD_ALGO_DIRECT, s);
+}
+
+mvd_status mvd_run_host(mvd_ctx *c, const void *stacks_host, mvd_dtype dt, int nz, int ny, int nx, float *out_host,
+                        int chunk_planes, void *stream) {
+    t_last_error.clear();
+    if (!c) return fail(MVD_ERR_ARG, "ctx is NULL");
+    if (!stacks_host || !out_host) return fail(MVD_ERR_ARG, "NULL buffer");
+    if (dt != MVD_U16 && dt != MVD_F32) return fail(MVD_ERR_ARG, "unknown dtype");
+    if (nz != c->H || nx != c->W) return fail(MVD_ERR_ARG, "stack (nz, nx) must equal the context's plane (H, W)");
+    if (ny < 1) return fail(MVD_ERR_ARG, "ny must be >= 1");
+    if (chunk_planes < 0) return fail(MVD_ERR_ARG, "chunk_planes must be >= 0");
+    DeviceGuard g(c->device);
+    const size_t es = dt == MVD_U16 ? 2 : 4;
+    const size_t plane_px = static_cast<size_t>(nz) * nx;
+    int cp = chunk_planes;
+    if (cp == 0) {
+        // about 64 MiB of input per chunk, at least 4 chunks when there are enough planes
+        const size_t per_plane = c->V * plane_px * es;
+        cp = static_cast<int>(std::max<size_t>(1, (64u << 20) / per_plane));
+        cp = std::min(cp, std::max(1, (ny + 3) / 4));
+    }
+    cp = std::min(cp, ny);
+    cudaError_t e;
+    for (int i = 0; i < 2; ++i) {
+        if ((e = c->run_stack[i].ensure(c->V * plane_px * cp * es)) != cudaSuccess ||
+            (e = c->run_est[i].ensure(plane_px * cp * sizeof(float))) != cudaSuccess)
+            return fail(MVD_ERR_NOMEM, "pipeline buffers: %s", cudaGetErrorString(e));
+    }
+    if ((e = c->run_planes.ensure(c->V * plane_px * cp * es)) != cudaSuccess)
+        return fail(MVD_ERR_NOMEM, "pipeline buffers: %s", cudaGetErrorString(e));
+    if (!c->copy_in && (e = cudaStreamCreateWithFlags(&c->copy_in, cudaStreamNonBlocking)) != cudaSuccess)
+        return cuda_fail(e, "stream");
+    if (!c->copy_out && (e = cudaStreamCreateWithFlags(&c->copy_out, cudaStreamNonBlocking)) != cudaSuccess)
+        return cuda_fail(e, "stream");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int nchunks = (ny + cp - 1) / cp;
+    std::vector<cudaEvent_t> ev(4 * static_cast<size_t>(nchunks), nullptr);
+    auto evt = [&](int kind, int i) -> cudaEvent_t & { return ev[4 * static_cast<size_t>(i) + kind]; };
+    enum { kH2D = 0, kResliced = 1, kComputed = 2, kD2H = 3 };
+    mvd_status st = MVD_OK;
+    for (auto &x : ev) {
+        if ((e = cudaEventCreateWithFlags(&x, cudaEventDisableTiming)) != cudaSuccess) {
+            st = cuda_fail(e, "event");
+            break;
+        }
+    }
+    const char *src = static_cast<const char *>(stacks_host);
+    for (int i = 0; i < nchunks && st == MVD_OK; ++i) {
+        const int y0 = i * cp, yn = std::min(cp, ny - y0), slot = i % 2;
+        // H2D into the stack slot once the reslice of chunk i-2 has consumed it
+        if (i >= 2) cudaStreamWaitEvent(c->copy_in, evt(kResliced, i - 2), 0);
+        char *dst = c->run_stack[slot].as<char>();
+        for (int v = 0; v < c->V && st == MVD_OK; ++v) {
+            e = cudaMemcpy2DAsync(dst + static_cast<size_t>(v) * nz * yn * nx * es, yn * nx * es,
+                                  src + (static_cast<size_t>(v) * nz * ny + y0) * nx * es, static_cast<size_t>(ny) * nx * es,
+                                  yn * nx * es, nz, cudaMemcpyHostToDevice, c->copy_in);
+            if (e != cudaSuccess) st = cuda_fail(e, "H2D copy");
+        }
+        if (st != MVD_OK) break;
+        cudaEventRecord(evt(kH2D, i), c->copy_in);
+        // reslice + deconvolve on the caller's stream
+        cudaStreamWaitEvent(s, evt(kH2D, i), 0);
+        if (i >= 2) cudaStreamWaitEvent(s, evt(kD2H, i - 2), 0);
+        if ((st = mvd_reslice(c, dst, dt, c->V, nz, yn, nx, c->run_planes.ptr, s)) != MVD_OK) break;
+        cudaEventRecord(evt(kResliced, i), s);
+        float *est = c->run_est[slot].as<float>();
+        if ((st = mvd_deconvolve_planes(c, c->run_planes.ptr, dt, est, yn, 1, s)) != MVD_OK) break;
+        cudaEventRecord(evt(kComputed, i), s);
+        // D2H: planes y0 .. y0+yn are contiguous in the [Y][Z][X] output
+        cudaStreamWaitEvent(c->copy_out, evt(kComputed, i), 0);
+        e = cudaMemcpyAsync(out_host + static_cast<size_t>(y0) * plane_px, est, yn * plane_px * sizeof(float),
+                            cudaMemcpyDeviceToHost, c->copy_out);
+        if (e != cudaSuccess) st = cuda_fail(e, "D2H copy");
+        cudaEventRecord(evt(kD2H, i), c->copy_out);
+    }
+    cudaError_t e1 = cudaStreamSynchronize(c->copy_in);
+    cudaError_t e2 = cudaStreamSynchronize(s);
+    cudaError_t e3 = cudaStreamSynchronize(c->copy_out);
+    for (auto &x : ev)
+        if (x) cudaEventDestroy(x);
+    if (st != MVD_OK) return st;
+    if (e1 != cudaSuccess) return cuda_fail(e1, "copy stream");
+    if (e2 != cudaSuccess) return cuda_fail(e2, "compute stream");
+    if (e3 != cudaSuccess) return cuda_fail(e3, "copy stream");
+    return MVD_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,265 @@
+// The two kernels of one fused MV-RL iteration (Supp. Note 1 update
+// equation), for all planes of a batch in one launch each:
+//
+//   blur_ratio        r_v = phi_v / max(psi * P_v, eps)   for every view v
+//   correlate_update  psi <- psi * prod_v (r_v (*) P_v^*)
+//
+// A CTA owns a TY x 128 output tile of one plane.  Kernel A reads the psi
+// tile (with a halo of R) once for all views; views whose PSFs are identical
+// share one blur.  Kernel B reads each view's ratio tile with its halo,
+// keeps the running product of the views' corrections in registers and
+// updates psi in place: each CTA reads and writes only its own output
+// pixels, and kernel A of the next iteration starts after kernel B ends in
+// stream order.
+//
+// HBM traffic per voxel-iteration (uint16 data): kernel A reads psi (4 B) and
+// phi_v (2V B) and writes r_v (4V B); kernel B reads r_v (4V B) and psi (4 B)
+// and writes psi (4 B): 12 + 10V bytes.  Halo re-reads hit L2.
+#include <cuda_runtime.h>
+#include <cstdint>
+
+#include "fused_common.cuh"
+
+namespace mvd {
+namespace fused {
+
+namespace {
+
+__device__ __forceinline__ void load16_phi(const void *phi, int u16, long long off, bool vec, int n,
+                                           float (&out)[kNC]) {
+    if (u16) {
+        const uint16_t *p = static_cast<const uint16_t *>(phi) + off;
+        if (vec) {
+            const uint4 a = __ldg(reinterpret_cast<const uint4 *>(p));
+            const uint4 b = __ldg(reinterpret_cast<const uint4 *>(p) + 1);
+            const unsigned w[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                out[2 * k] = static_cast<float>(w[k] & 0xffffu);
+                out[2 * k + 1] = static_cast<float>(w[k] >> 16);
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < kNC; ++j) out[j] = j < n ? static_cast<float>(p[j]) : 0.0f;
+        }
+    } else {
+        const float *p = static_cast<const float *>(phi) + off;
+        if (vec) {
+#pragma unroll
+            for (int q = 0; q < kNC / 4; ++q) {
+                const float4 a = __ldg(reinterpret_cast<const float4 *>(p) + q);
+                out[4 * q + 0] = a.x;
+                out[4 * q + 1] = a.y;
+                out[4 * q + 2] = a.z;
+                out[4 * q + 3] = a.w;
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < kNC; ++j) out[j] = j < n ? __ldg(p + j) : 0.0f;
+        }
+    }
+}
+
+__device__ __forceinline__ void store16(float *dst, bool vec, int n, const float (&v)[kNC]) {
+    if (vec) {
+#pragma unroll
+        for (int q = 0; q < kNC / 4; ++q)
+            reinterpret_cast<float4 *>(dst)[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+    } else {
+#pragma unroll
+        for (int j = 0; j < kNC; ++j)
+            if (j < n) dst[j] = v[j];
+    }
+}
+
+template <int K>
+__global__ void __launch_bounds__(kThreads, Geo<K>::MIN_BLOCKS)
+blur_ratio_kernel(const __grid_constant__ FusedArgs a, const int vec_ok) {
+    using G = Geo<K>;
+    extern __shared__ float4 smem4[];
+    float *tile = reinterpret_cast<float *>(smem4);
+    float *stage = tile + G::IN_H * G::IN_LD;
+
+    const int p = blockIdx.z;
+    const int y0 = blockIdx.y * G::TY;
+    const int x0 = blockIdx.x * G::TX;
+    const long long plane_px = static_cast<long long>(a.H) * a.W;
+    const float *psi = a.psi_in ? a.psi_in + p * plane_px : nullptr;
+    const float fill = a.psi_in ? 0.0f : __ldg(a.means + p);
+    load_tile<K>(tile, psi, fill, y0, x0, a.H, a.W, a.circular);
+    __syncthreads();
+
+    for (int g = 0; g < a.ft.n_groups; ++g) {
+        const int lead = a.ft.group_leader[g];
+        float acc[G::H_PER_THREAD][kNC];
+#pragma unroll
+        for (int h = 0; h < G::H_PER_THREAD; ++h)
+#pragma unroll
+            for (int j = 0; j < kNC; ++j) acc[h][j] = 0.0f;
+        for (int q = 0; q < a.ft.rank[lead]; ++q) {
+            const float *tq = a.taps + static_cast<long long>(a.ft.tap_off[lead] + q) * 4 * K;
+            vertical_pass<K>(tile, stage, tq);
+            __syncthreads();
+            horizontal_pass<K>(stage, tq + K, acc);
+            __syncthreads();
+        }
+        for (int v = 0; v < a.ft.views; ++v) {
+            if (a.ft.group[v] != g) continue;
+            const long long vplane = (static_cast<long long>(v) * a.P + p) * plane_px;
+#pragma unroll
+            for (int h = 0; h < G::H_PER_THREAD; ++h) {
+                int y, x;
+                item_origin<K>(h, y0, x0, y, x);
+                if (y >= a.H || x >= a.W) continue;
+                const int n = min(kNC, a.W - x);
+                const bool vec = vec_ok && n == kNC;
+                const long long off = vplane + static_cast<long long>(y) * a.W + x;
+                float phi[kNC];
+                load16_phi(a.phi, a.phi_u16, off, vec, n, phi);
+                float r[kNC];
+#pragma unroll
+                for (int j = 0; j < kNC; ++j) r[j] = __fdividef(phi[j], fmaxf(acc[h][j], a.eps));
+                store16(a.ratio + off, vec, n, r);
+            }
+        }
+    }
+}
+
+template <int K>
+__global__ void __launch_bounds__(kThreads, Geo<K>::MIN_BLOCKS)
+correlate_update_kernel(const __grid_constant__ FusedArgs a, const int vec_ok) {
+    using G = Geo<K>;
+    extern __shared__ float4 smem4[];
+    float *tile = reinterpret_cast<float *>(smem4);
+    float *stage = tile + G::IN_H * G::IN_LD;
+
+    const int p = blockIdx.z;
+    const int y0 = blockIdx.y * G::TY;
+    const int x0 = blockIdx.x * G::TX;
+    const long long plane_px = static_cast<long long>(a.H) * a.W;
+
+    float prod[G::H_PER_THREAD][kNC];
+#pragma unroll
+    for (int h = 0; h < G::H_PER_THREAD; ++h)
+#pragma unroll
+        for (int j = 0; j < kNC; ++j) prod[h][j] = 1.0f;
+
+    for (int v = 0; v < a.ft.views; ++v) {
+        const float *rsrc = a.ratio + (static_cast<long long>(v) * a.P + p) * plane_px;
+        load_tile<K>(tile, rsrc, 0.0f, y0, x0, a.H, a.W, a.circular);
+        __syncthreads();
+        float c[G::H_PER_THREAD][kNC];
+#pragma unroll
+        for (int h = 0; h < G::H_PER_THREAD; ++h)
+#pragma unroll
+            for (int j = 0; j < kNC; ++j) c[h][j] = 0.0f;
+        for (int q = 0; q < a.ft.rank[v]; ++q) {
+            const float *tq = a.taps + static_cast<long long>(a.ft.tap_off[v] + q) * 4 * K;
+            vertical_pass<K>(tile, stage, tq + 2 * K);
+            __syncthreads();
+            horizontal_pass<K>(stage, tq + 3 * K, c);
+            __syncthreads();
+        }
+#pragma unroll
+        for (int h = 0; h < G::H_PER_THREAD; ++h)
+#pragma unroll
+            for (int j = 0; j < kNC; ++j) prod[h][j] *= c[h][j];
+    }
+
+    const float mean = a.psi_in ? 0.0f : __ldg(a.means + p);
+#pragma unroll
+    for (int h = 0; h < G::H_PER_THREAD; ++h) {
+        int y, x;
+        item_origin<K>(h, y0, x0, y, x);
+        if (y >= a.H || x >= a.W) continue;
+        const int n = min(kNC, a.W - x);
+        const bool vec = vec_ok && n == kNC;
+        const long long off = p * plane_px + static_cast<long long>(y) * a.W + x;
+        float old[kNC];
+        if (a.psi_in) {
+            load16_phi(a.psi_in, 0, off, vec, n, old);
+        } else {
+#pragma unroll
+            for (int j = 0; j < kNC; ++j) old[j] = mean;
+        }
+        float out[kNC];
+#pragma unroll
+        for (int j = 0; j < kNC; ++j) out[j] = old[j] * prod[h][j];
+        store16(a.psi_out + off, vec, n, out);
+    }
+}
+
+template <int K>
+cudaError_t launch_pair(const FusedArgs &a, int which, cudaStream_t s) {
+    using G = Geo<K>;
+    // the shared-memory opt-in is per function and device
+    static unsigned long long attr_set = 0;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const unsigned long long bit = 1ull << (dev & 63);
+    if (!(attr_set & bit)) {
+        cudaError_t e = cudaFuncSetAttribute(blur_ratio_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             G::SMEM_BYTES);
+        if (e != cudaSuccess) return e;
+        e = cudaFuncSetAttribute(correlate_update_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 G::SMEM_BYTES);
+        if (e != cudaSuccess) return e;
+        attr_set |= bit;
+    }
+    const dim3 grid((a.W + G::TX - 1) / G::TX, (a.H + G::TY - 1) / G::TY, a.P);
+    const bool aligned = (reinterpret_cast<uintptr_t>(a.phi) % 16 == 0) &&
+                         (reinterpret_cast<uintptr_t>(a.ratio) % 16 == 0) &&
+                         (reinterpret_cast<uintptr_t>(a.psi_out) % 16 == 0) &&
+                         (a.psi_in == nullptr || reinterpret_cast<uintptr_t>(a.psi_in) % 16 == 0);
+    const int vec_ok = aligned && (a.W % 16 == 0);
+    if (which == 0)
+        blur_ratio_kernel<K><<<grid, kThreads, G::SMEM_BYTES, s>>>(a, vec_ok);
+    else
+        correlate_update_kernel<K><<<grid, kThreads, G::SMEM_BYTES, s>>>(a, vec_ok);
+    count_launch();
+    return cudaGetLastError();
+}
+
+#define MVD_FUSED_CASES(X) \
+    X(1) X(3) X(5) X(7) X(9) X(11) X(13) X(15) X(17) X(19) X(21) X(23) X(25) X(27) X(29) X(31) \
+    X(33) X(35) X(37) X(39) X(41) X(43) X(45) X(47)
+
+cudaError_t dispatch(const FusedArgs &a, int which, cudaStream_t s) {
+    switch (a.ft.K) {
+#define MVD_CASE(k) \
+    case k:         \
+        return launch_pair<k>(a, which, s);
+        MVD_FUSED_CASES(MVD_CASE)
+#undef MVD_CASE
+        default:
+            return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace
+
+}  // namespace fused
+
+bool fused_supported(int K) { return K >= 1 && K <= kFusedMaxK && (K % 2) == 1; }
+
+void fused_tile_shape(int K, int *tile_h, int *tile_w) {
+    switch (K) {
+#define MVD_CASE(k)                       \
+    case k:                               \
+        *tile_h = fused::Geo<k>::TY;      \
+        *tile_w = fused::Geo<k>::TX;      \
+        return;
+        MVD_FUSED_CASES(MVD_CASE)
+#undef MVD_CASE
+        default:
+            *tile_h = *tile_w = 0;
+    }
+}
+
+cudaError_t launch_fused_blur_ratio(const FusedArgs &a, cudaStream_t s) { return fused::dispatch(a, 0, s); }
+
+cudaError_t launch_fused_correlate_update(const FusedArgs &a, cudaStream_t s) {
+    return fused::dispatch(a, 1, s);
+}
+
+}  // namespace mvd

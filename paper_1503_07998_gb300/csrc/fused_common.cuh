@@ -1,0 +1,161 @@
+// Tile machinery shared by the two kernels of one fused MV-RL iteration
+// (Supp. Note 1 update equation):
+//   kernel A  blur psi with every view's PSF, ratio phi_v / max(blur, eps)
+//   kernel B  correlate every ratio with its flipped PSF, multiply the views'
+//             corrections and update psi.
+// Each 2D convolution is a sum over SVD terms of a vertical 1D pass (from the
+// halo'd input tile in shared memory into a staging tile) followed by a
+// horizontal 1D pass (from the staging tile into registers).
+//
+// Both passes are written in correlation form out[i] = sum_m t[m] in[i+m]
+// (the host reverses the factors for the blur).  Every thread keeps a
+// register block of 16 outputs so that each shared-memory value it loads
+// feeds up to K FMAs:
+//   vertical:   item = (column, block of 16 rows); lanes run along columns, so
+//               the 4-byte loads of a warp hit 32 distinct banks;
+//   horizontal: item = (row, group of 16 columns); lanes run along rows and
+//               the staging tile's row pitch is an odd multiple of 4 floats,
+//               so every 8-lane phase of a 16-byte load hits 8 distinct
+//               4-bank groups.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+
+#include "mvd_internal.h"
+
+namespace mvd {
+namespace fused {
+
+constexpr int kThreads = 256;
+constexpr int kNR = 16;      // rows per vertical item
+constexpr int kNC = 16;      // columns per horizontal item
+constexpr int kTX = 128;     // output tile width
+
+__host__ __device__ constexpr int round_up(int a, int b) { return (a + b - 1) / b * b; }
+
+// Row pitch >= w with pitch/4 odd (see the bank argument above).
+__host__ __device__ constexpr int odd_quad_pitch(int w) {
+    return ((round_up(w, 4) / 4) % 2 == 1) ? round_up(w, 4) : round_up(w, 4) + 4;
+}
+
+template <int K>
+struct Geo {
+    static constexpr int R = (K - 1) / 2;
+    static constexpr int TX = kTX;
+    static constexpr int IN_W = TX + 2 * R;                  // columns of the input tile
+    static constexpr int IN_LD = round_up(IN_W, 4);
+    static constexpr int HL = round_up(kNC + 2 * R, 4);       // horizontal load width
+    static constexpr int VB_LD = odd_quad_pitch((TX / kNC - 1) * kNC + HL);
+    static constexpr int smem_floats(int ty) { return (ty + 2 * R) * IN_LD + ty * VB_LD; }
+    // 64-row tiles while two CTAs still fit on an SM, else 32.
+    static constexpr int TY = (smem_floats(64) * 4 <= 112 * 1024) ? 64 : 32;
+    static constexpr int IN_H = TY + 2 * R;
+    static constexpr int SMEM_BYTES = smem_floats(TY) * 4;
+    static constexpr int V_ITEMS = IN_W * (TY / kNR);
+    static constexpr int H_ITEMS = TY * (TX / kNC);
+    static constexpr int H_PER_THREAD = H_ITEMS / kThreads;
+    static_assert(H_ITEMS % kThreads == 0, "horizontal items must tile the CTA");
+    static constexpr int MIN_BLOCKS = (SMEM_BYTES <= 112 * 1024) ? 2 : 1;
+};
+
+// Load the (IN_H x IN_W) halo'd tile of one plane whose output origin is
+// (y0, x0) into shared memory.  src == nullptr means a constant plane of
+// value `fill` (iteration 0 from the per-plane mean).  ZERO boundary: zero
+// outside the plane; CIRCULAR: indices modulo the plane size.
+template <int K>
+__device__ __forceinline__ void load_tile(float *__restrict__ tile, const float *__restrict__ src,
+                                          float fill, int y0, int x0, int H, int W, int circular) {
+    using G = Geo<K>;
+    constexpr int N = G::IN_H * G::IN_W;
+    for (int idx = threadIdx.x; idx < N; idx += kThreads) {
+        const int r = idx / G::IN_W;
+        const int c = idx - r * G::IN_W;
+        int gy = y0 - G::R + r;
+        int gx = x0 - G::R + c;
+        float v = 0.0f;
+        if (circular) {
+            gy %= H; if (gy < 0) gy += H;
+            gx %= W; if (gx < 0) gx += W;
+            v = src ? __ldg(src + static_cast<long long>(gy) * W + gx) : fill;
+        } else if (gy >= 0 && gy < H && gx >= 0 && gx < W) {
+            v = src ? __ldg(src + static_cast<long long>(gy) * W + gx) : fill;
+        }
+        tile[r * G::IN_LD + c] = v;
+    }
+}
+
+// Vertical pass: stage[i][c] = sum_m t[m] * tile[i + m][c] for the TY output
+// rows and all IN_W columns.
+template <int K>
+__device__ __forceinline__ void vertical_pass(const float *__restrict__ tile, float *__restrict__ stage,
+                                              const float *__restrict__ taps_g) {
+    using G = Geo<K>;
+    float t[K];
+#pragma unroll
+    for (int m = 0; m < K; ++m) t[m] = __ldg(taps_g + m);
+    for (int it = threadIdx.x; it < G::V_ITEMS; it += kThreads) {
+        const int rb = it / G::IN_W;
+        const int c = it - rb * G::IN_W;
+        const float *col = tile + rb * kNR * G::IN_LD + c;
+        float acc[kNR];
+#pragma unroll
+        for (int i = 0; i < kNR; ++i) acc[i] = 0.0f;
+#pragma unroll
+        for (int m = 0; m < kNR + K - 1; ++m) {
+            const float x = col[m * G::IN_LD];
+#pragma unroll
+            for (int i = 0; i < kNR; ++i) {
+                const int j = m - i;
+                if (j >= 0 && j < K) acc[i] = fmaf(t[j], x, acc[i]);
+            }
+        }
+        float *dst = stage + rb * kNR * G::VB_LD + c;
+#pragma unroll
+        for (int i = 0; i < kNR; ++i) dst[i * G::VB_LD] = acc[i];
+    }
+}
+
+// Horizontal pass for this thread's items: acc[h][j] += sum_m t[m] * stage[row][16g + j + m].
+template <int K>
+__device__ __forceinline__ void horizontal_pass(const float *__restrict__ stage,
+                                                const float *__restrict__ taps_g,
+                                                float (&acc)[Geo<K>::H_PER_THREAD][kNC]) {
+    using G = Geo<K>;
+    float t[K];
+#pragma unroll
+    for (int m = 0; m < K; ++m) t[m] = __ldg(taps_g + m);
+#pragma unroll
+    for (int h = 0; h < G::H_PER_THREAD; ++h) {
+        const int it = threadIdx.x + h * kThreads;
+        const int row = it % G::TY;
+        const int g = it / G::TY;
+        const float4 *src = reinterpret_cast<const float4 *>(stage + row * G::VB_LD + g * kNC);
+        float in[G::HL];
+#pragma unroll
+        for (int q = 0; q < G::HL / 4; ++q) {
+            const float4 v = src[q];
+            in[4 * q + 0] = v.x;
+            in[4 * q + 1] = v.y;
+            in[4 * q + 2] = v.z;
+            in[4 * q + 3] = v.w;
+        }
+#pragma unroll
+        for (int j = 0; j < kNC; ++j) {
+#pragma unroll
+            for (int m = 0; m < K; ++m) acc[h][j] = fmaf(t[m], in[j + m], acc[h][j]);
+        }
+    }
+}
+
+// Output coordinates of horizontal item h of this thread.
+template <int K>
+__device__ __forceinline__ void item_origin(int h, int y0, int x0, int &y, int &x) {
+    using G = Geo<K>;
+    const int it = threadIdx.x + h * kThreads;
+    y = y0 + it % G::TY;
+    x = x0 + (it / G::TY) * kNC;
+}
+
+}  // namespace fused
+}  // namespace mvd

@@ -1,0 +1,88 @@
+// Internal declarations shared by the host side of the library and the CUDA
+// translation units.  Nothing here is part of the public ABI (include/mvd.h).
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace mvd {
+
+constexpr int kMaxViews = 64;
+constexpr int kFusedMaxK = 47;   // largest PSF side with a fused-kernel instance
+
+// Launch accounting (mvd_launch_count).
+void count_launch(int n = 1);
+
+// Per-view separable factorisation of the PSFs, laid out on the device as
+//   taps[(tap_off[v] + q) * 4 * K + {0: blur vertical, 1: blur horizontal,
+//                                    2: corr vertical, 3: corr horizontal}*K + m]
+// Each pass computes out[i] = sum_m t[m] * in[i + m] over a window that starts
+// R rows/columns before the output; the blur taps are reversed factors, the
+// correlation taps the factors as they are.  The singular value is folded
+// into the vertical factor.
+struct FactorTable {
+    int K = 0;
+    int views = 0;
+    int rank[kMaxViews] = {};
+    int tap_off[kMaxViews] = {};     // in units of terms
+    int group[kMaxViews] = {};       // blur group (views with identical PSFs)
+    int n_groups = 0;
+    int group_leader[kMaxViews] = {};
+    int total_terms = 0;
+};
+
+// Host-side PSF analysis (factor.cpp).  psfs: [V][K][K] FP32.  Fills `ft` and
+// the host tap array (total_terms * 4 * K floats).  Returns false with a
+// message when the factorisation fails.
+bool factorise_psfs(const float *psfs, int views, int K, double rank_tol,
+                    FactorTable &ft, float *taps_out, int taps_capacity, char *msg, size_t msg_len);
+int max_terms(int views, int K);
+
+// ---- kernel launchers (return cudaGetLastError after the launch) ---------
+
+// stacks [V][Z][Y][X] -> planes [V][Y][Z][X]
+cudaError_t launch_reslice(const void *src, void *dst, int elem_bytes, int views,
+                           int nz, int ny, int nx, cudaStream_t s);
+
+// means[p] = (sum over views and pixels of plane p) / (V*H*W), FP64 sum.
+cudaError_t launch_plane_means(const void *data, int u16, int views, int planes, int H,
+                               int W, float *means, cudaStream_t s);
+
+struct FusedArgs {
+    const float *psi_in;     // [P][H][W], or nullptr -> use means (iteration 0)
+    const float *means;      // [P]
+    float *psi_out;          // [P][H][W]
+    const void *phi;         // [V][P][H][W]
+    int phi_u16;
+    float *ratio;            // [V][P][H][W] scratch
+    const float *taps;       // device factor taps (see FactorTable)
+    FactorTable ft;
+    int H, W, P;
+    int circular;
+    float eps;
+};
+
+bool fused_supported(int K);
+void fused_tile_shape(int K, int *tile_h, int *tile_w);
+cudaError_t launch_fused_blur_ratio(const FusedArgs &a, cudaStream_t s);
+cudaError_t launch_fused_correlate_update(const FusedArgs &a, cudaStream_t s);
+
+// Plain per-plane path (one plane, one step per launch).
+struct PlainArgs {
+    const float *taps;       // device factor taps
+    const float *psf_dev;    // [V][K][K] raw PSFs (direct route)
+    FactorTable ft;
+    int H, W, circular;
+    float eps;
+};
+// out = conv/corr of `in` (one plane) with view v's PSF. `direct` uses K^2 taps.
+cudaError_t plain_convolve(const PlainArgs &a, int v, int correlate, int direct,
+                           const float *in, float *tmp, float *out, cudaStream_t s);
+cudaError_t plain_fill(float *dst, const float *means, int plane, size_t n, cudaStream_t s);
+cudaError_t plain_ratio(const void *phi, int u16, const float *blur, float *ratio, size_t n,
+                        float eps, cudaStream_t s);
+cudaError_t plain_multiply(float *acc, const float *c, size_t n, int first, cudaStream_t s);
+cudaError_t plain_update(float *psi, const float *prod, size_t n, cudaStream_t s);
+
+}  // namespace mvd

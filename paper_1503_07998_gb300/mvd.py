@@ -1,0 +1,274 @@
+"""Python binding of the C ABI in ``include/mvd.h`` (ctypes).
+
+Argument marshalling only: every step of the method runs in the CUDA kernels
+of ``_lib/libmvd.so``.  Functions keep the C names; device buffers are torch
+CUDA tensors (their ``data_ptr()`` is passed), host buffers numpy arrays or
+CPU tensors, and the stream defaults to torch's current stream on the
+tensor's device.  Loading fails loudly when the library has not been built:
+there is no CPU fallback.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+from dataclasses import dataclass
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_lib", "libmvd.so")
+HEADER = os.path.join(os.path.dirname(HERE), "include", "mvd.h")
+
+MVD_OK, MVD_ERR_ARG, MVD_ERR_CUDA, MVD_ERR_NOMEM, MVD_ERR_TIMEOUT, MVD_ERR_STATE, MVD_ERR_UNSUPPORTED = range(7)
+BOUNDARY = {"zero": 0, "circular": 1}
+DTYPE = {"u16": 0, "f32": 1}
+ALGO = {"fused": 0, "plain": 1, "direct": 2}
+
+
+class MvdError(RuntimeError):
+    def __init__(self, status: int, where: str, detail: str):
+        self.status = status
+        super().__init__(f"{where}: status {status} ({detail})")
+
+
+class _KernelStat(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 32), ("total_ms", ctypes.c_double), ("launches", ctypes.c_uint64)]
+
+
+class _Info(ctypes.Structure):
+    _fields_ = [
+        ("views", ctypes.c_int), ("psf_size", ctypes.c_int),
+        ("plane_h", ctypes.c_int), ("plane_w", ctypes.c_int),
+        ("iters", ctypes.c_int), ("boundary", ctypes.c_int), ("algo", ctypes.c_int),
+        ("rank", ctypes.c_int * 16), ("blur_groups", ctypes.c_int), ("blur_terms", ctypes.c_int),
+        ("tile_h", ctypes.c_int), ("tile_w", ctypes.c_int),
+        ("workspace_bytes", ctypes.c_size_t),
+    ]
+
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    """Load the in-tree library (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: build it with `python -m paper_1503_07998_gb300.build`")
+    L = ctypes.CDLL(LIB_PATH)
+    vp, i, f, d = ctypes.c_void_p, ctypes.c_int, ctypes.c_float, ctypes.c_double
+    L.mvd_create.argtypes = [ctypes.POINTER(vp), i, vp, i, i, i, i, i, f]
+    L.mvd_destroy.argtypes = [vp]
+    L.mvd_set_algo.argtypes = [vp, i]
+    L.mvd_set_rank_tolerance.argtypes = [vp, d]
+    L.mvd_get_info.argtypes = [vp, ctypes.POINTER(_Info)]
+    L.mvd_reslice.argtypes = [vp, vp, i, i, i, i, i, vp, vp]
+    L.mvd_deconvolve_planes.argtypes = [vp, vp, i, vp, i, i, vp]
+    L.mvd_run_host.argtypes = [vp, vp, i, i, i, i, vp, i, vp]
+    L.mvd_psf_factors.argtypes = [vp, i, i, d, vp, vp, i]
+    L.mvd_profile_enable.argtypes = [vp, i]
+    L.mvd_profile_read.argtypes = [vp, ctypes.POINTER(_KernelStat), i, ctypes.POINTER(i)]
+    L.mvd_status_string.argtypes = [i]
+    L.mvd_status_string.restype = ctypes.c_char_p
+    L.mvd_last_error.argtypes = []
+    L.mvd_last_error.restype = ctypes.c_char_p
+    L.mvd_launch_count.argtypes = []
+    L.mvd_launch_count.restype = ctypes.c_uint64
+    for name in ("mvd_create", "mvd_destroy", "mvd_set_algo", "mvd_set_rank_tolerance", "mvd_get_info",
+                 "mvd_reslice", "mvd_deconvolve_planes", "mvd_run_host", "mvd_psf_factors",
+                 "mvd_profile_enable", "mvd_profile_read"):
+        getattr(L, name).restype = ctypes.c_int
+    _lib = L
+    return L
+
+
+def header_functions() -> list[str]:
+    """Names of the functions declared in include/mvd.h."""
+    with open(HEADER) as fh:
+        text = re.sub(r"/\*.*?\*/", "", fh.read(), flags=re.S)
+    return sorted(set(re.findall(r"\b(mvd_[a-z0-9_]+)\s*\(", text)))
+
+
+def _check(status: int, where: str) -> None:
+    if status != MVD_OK:
+        L = lib()
+        detail = L.mvd_last_error().decode() or L.mvd_status_string(status).decode()
+        raise MvdError(status, where, detail)
+
+
+def _stream_of(t, stream):
+    if stream is not None:
+        return ctypes.c_void_p(int(stream))
+    import torch
+    return ctypes.c_void_p(torch.cuda.current_stream(t.device).cuda_stream)
+
+
+def _dtype_code(t) -> int:
+    import torch
+    if t.dtype == torch.uint16:
+        return DTYPE["u16"]
+    if t.dtype == torch.float32:
+        return DTYPE["f32"]
+    raise TypeError(f"data must be uint16 or float32, got {t.dtype}")
+
+
+def _require_cuda(*ts):
+    for t in ts:
+        if not t.is_cuda or not t.is_contiguous():
+            raise ValueError("device buffers must be contiguous CUDA tensors")
+
+
+@dataclass
+class Info:
+    views: int
+    psf_size: int
+    plane_h: int
+    plane_w: int
+    iters: int
+    boundary: int
+    algo: int
+    rank: list
+    blur_groups: int
+    blur_terms: int
+    tile_h: int
+    tile_w: int
+    workspace_bytes: int
+
+
+class Context:
+    """Owns an ``mvd_ctx``; created by :func:`mvd_create`."""
+
+    def __init__(self, handle: int, views: int, K: int, H: int, W: int, iters: int):
+        self.handle = ctypes.c_void_p(handle)
+        self.views, self.K, self.H, self.W, self.iters = views, K, H, W, iters
+
+    def close(self):
+        if self.handle and self.handle.value:
+            _check(lib().mvd_destroy(self.handle), "mvd_destroy")
+            self.handle = ctypes.c_void_p(0)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+def mvd_create(views: int, psfs, psf_size: int, plane_h: int, plane_w: int, iters: int,
+               boundary: str = "zero", eps: float = 1e-6) -> Context:
+    p = np.ascontiguousarray(np.asarray(psfs, dtype=np.float32))
+    if p.size != views * psf_size * psf_size:
+        raise ValueError("psfs must hold views * K * K values")
+    h = ctypes.c_void_p()
+    _check(lib().mvd_create(ctypes.byref(h), int(views), p.ctypes.data_as(ctypes.c_void_p), int(psf_size),
+                            int(plane_h), int(plane_w), int(iters), BOUNDARY[boundary], float(eps)), "mvd_create")
+    return Context(h.value, views, psf_size, plane_h, plane_w, iters)
+
+
+def mvd_destroy(ctx: Context) -> None:
+    ctx.close()
+
+
+def mvd_set_algo(ctx: Context, algo: str) -> None:
+    _check(lib().mvd_set_algo(ctx.handle, ALGO[algo]), "mvd_set_algo")
+
+
+def mvd_set_rank_tolerance(ctx: Context, tol: float) -> None:
+    _check(lib().mvd_set_rank_tolerance(ctx.handle, float(tol)), "mvd_set_rank_tolerance")
+
+
+def mvd_get_info(ctx: Context) -> Info:
+    inf = _Info()
+    _check(lib().mvd_get_info(ctx.handle, ctypes.byref(inf)), "mvd_get_info")
+    return Info(inf.views, inf.psf_size, inf.plane_h, inf.plane_w, inf.iters, inf.boundary, inf.algo,
+                list(inf.rank)[:min(16, inf.views)], inf.blur_groups, inf.blur_terms, inf.tile_h, inf.tile_w,
+                int(inf.workspace_bytes))
+
+
+def mvd_reslice(ctx: Context, stacks, planes, stream=None) -> None:
+    """stacks [V][Z][Y][X] -> planes [V][Y][Z][X] (CUDA tensors, same dtype)."""
+    _require_cuda(stacks, planes)
+    V, Z, Y, X = stacks.shape
+    if tuple(planes.shape) != (V, Y, Z, X) or planes.dtype != stacks.dtype:
+        raise ValueError("planes must be [V][Y][Z][X] of the stacks' dtype")
+    _check(lib().mvd_reslice(ctx.handle, ctypes.c_void_p(stacks.data_ptr()), _dtype_code(stacks), V, Z, Y, X,
+                             ctypes.c_void_p(planes.data_ptr()), _stream_of(stacks, stream)), "mvd_reslice")
+
+
+def mvd_deconvolve_planes(ctx: Context, data, estimate, init_mean: bool = True, stream=None) -> None:
+    """data [V][P][H][W] (uint16/float32), estimate [P][H][W] float32, in place."""
+    import torch
+    _require_cuda(data, estimate)
+    V, P, H, W = data.shape
+    if V != ctx.views or (H, W) != (ctx.H, ctx.W):
+        raise ValueError("data shape does not match the context")
+    if tuple(estimate.shape) != (P, H, W) or estimate.dtype != torch.float32:
+        raise ValueError("estimate must be float32 [P][H][W]")
+    _check(lib().mvd_deconvolve_planes(ctx.handle, ctypes.c_void_p(data.data_ptr()), _dtype_code(data),
+                                       ctypes.c_void_p(estimate.data_ptr()), P, int(bool(init_mean)),
+                                       _stream_of(data, stream)), "mvd_deconvolve_planes")
+
+
+def mvd_run_host(ctx: Context, stacks_host, out_host, chunk_planes: int = 0, stream=None) -> None:
+    """Host stacks [V][Z][Y][X] -> host result [Y][Z][X] float32 (torch CPU tensors,
+    ideally pinned)."""
+    import torch
+    if stacks_host.is_cuda or out_host.is_cuda:
+        raise ValueError("mvd_run_host takes host tensors")
+    V, Z, Y, X = stacks_host.shape
+    if tuple(out_host.shape) != (Y, Z, X) or out_host.dtype != torch.float32:
+        raise ValueError("out must be float32 [Y][Z][X]")
+    if not (stacks_host.is_contiguous() and out_host.is_contiguous()):
+        raise ValueError("host buffers must be contiguous")
+    if stream is None:
+        stream = torch.cuda.current_stream().cuda_stream
+    _check(lib().mvd_run_host(ctx.handle, ctypes.c_void_p(stacks_host.data_ptr()), _dtype_code(stacks_host),
+                              Z, Y, X, ctypes.c_void_p(out_host.data_ptr()), int(chunk_planes),
+                              ctypes.c_void_p(int(stream))), "mvd_run_host")
+
+
+def mvd_psf_factors(psfs, rank_tol: float = 3e-7):
+    """Host-only factorisation: returns (ranks [V], taps [terms][4][K])."""
+    p = np.ascontiguousarray(np.asarray(psfs, dtype=np.float32))
+    V, K, _ = p.shape
+    cap = V * K * 4 * K
+    taps = np.zeros(cap, dtype=np.float32)
+    ranks = np.zeros(V, dtype=np.int32)
+    _check(lib().mvd_psf_factors(p.ctypes.data_as(ctypes.c_void_p), V, K, float(rank_tol),
+                                 ranks.ctypes.data_as(ctypes.c_void_p), taps.ctypes.data_as(ctypes.c_void_p), cap),
+           "mvd_psf_factors")
+    return ranks, taps.reshape(-1, 4, K)
+
+
+def mvd_profile_enable(ctx: Context, on: bool = True) -> None:
+    _check(lib().mvd_profile_enable(ctx.handle, int(bool(on))), "mvd_profile_enable")
+
+
+def mvd_profile_read(ctx: Context) -> dict:
+    """{kernel name: (total_ms, launches)} since profiling was enabled."""
+    cap = 32
+    arr = (_KernelStat * cap)()
+    n = ctypes.c_int(0)
+    _check(lib().mvd_profile_read(ctx.handle, arr, cap, ctypes.byref(n)), "mvd_profile_read")
+    return {arr[k].name.decode(): (arr[k].total_ms, int(arr[k].launches)) for k in range(min(n.value, cap))}
+
+
+def mvd_launch_count() -> int:
+    return int(lib().mvd_launch_count())
+
+
+def mvd_status_string(status: int) -> str:
+    return lib().mvd_status_string(int(status)).decode()
+
+
+def mvd_last_error() -> str:
+    return lib().mvd_last_error().decode()

@@ -1,0 +1,118 @@
+"""Host-side checks of the C ABI that need no GPU: the library loads, exports
+every function that include/mvd.h declares, rejects bad arguments before any
+device work, and factorises PSFs the way the kernels expect."""
+
+import ctypes
+
+import numpy as np
+import pytest
+
+from paper_1503_07998_gb300 import build as B
+from paper_1503_07998_gb300 import mvd, synth
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    B.build()
+    return mvd.lib()
+
+
+def test_exports_every_header_function():
+    names = mvd.header_functions()
+    assert "mvd_create" in names and "mvd_deconvolve_planes" in names and "mvd_reslice" in names
+    missing = [n for n in names if not hasattr(mvd.lib(), n)]
+    assert not missing, missing
+
+
+def test_status_strings():
+    assert mvd.mvd_status_string(0) == "ok"
+    assert "argument" in mvd.mvd_status_string(1)
+    assert mvd.mvd_status_string(99) == "unknown status"
+
+
+def _create(views=2, K=5, H=16, W=16, iters=3, boundary=0, eps=1e-6, psfs=None):
+    if psfs is None:
+        psfs = np.full((max(views, 1), max(K, 1), max(K, 1)), 0.1, dtype=np.float32)
+    h = ctypes.c_void_p()
+    st = mvd.lib().mvd_create(ctypes.byref(h), views, psfs.ctypes.data_as(ctypes.c_void_p), K, H, W, iters,
+                              boundary, eps)
+    return st, h
+
+
+@pytest.mark.parametrize("kw", [
+    dict(K=4), dict(K=0), dict(views=0), dict(views=65), dict(H=0), dict(iters=-1),
+    dict(eps=0.0), dict(eps=-1.0), dict(eps=float("inf")), dict(K=17, boundary=1), dict(boundary=7),
+])
+def test_create_rejects_bad_arguments(kw):
+    st, h = _create(**kw)
+    assert st == mvd.MVD_ERR_ARG, (kw, st, mvd.mvd_last_error())
+    assert h.value is None
+    assert mvd.mvd_last_error() != ""
+
+
+@pytest.mark.parametrize("bad", ["negative", "nan", "zero"])
+def test_create_rejects_bad_psfs(bad):
+    p = np.full((2, 3, 3), 0.1, dtype=np.float32)
+    if bad == "negative":
+        p[1, 0, 0] = -0.01
+    elif bad == "nan":
+        p[0, 1, 1] = np.nan
+    else:
+        p[1] = 0
+    st, _ = _create(K=3, psfs=p)
+    assert st == mvd.MVD_ERR_ARG
+
+
+def _reconstruct(taps, ranks, K, views, shared):
+    """Sum of outer products per view from the correlation-order factors."""
+    out, off = [], 0
+    seen = {}
+    for v in range(views):
+        if shared[v] in seen:
+            out.append(out[seen[shared[v]]])
+            continue
+        seen[shared[v]] = v
+        P = np.zeros((K, K))
+        for q in range(ranks[v]):
+            u = taps[off + q, 2].astype(np.float64)
+            w = taps[off + q, 3].astype(np.float64)
+            np.testing.assert_array_equal(taps[off + q, 0], taps[off + q, 2][::-1])
+            np.testing.assert_array_equal(taps[off + q, 1], taps[off + q, 3][::-1])
+            P += np.outer(u, w)
+        off += ranks[v]
+        out.append(P)
+    return out
+
+
+def test_gaussian_psfs_are_rank_one():
+    psfs = np.stack([synth.gaussian_psf(31, 8.0, 1.5, a) for a in (0, 90, 180, 270)])
+    ranks, taps = mvd.mvd_psf_factors(psfs)
+    assert list(ranks) == [1, 1, 1, 1]
+    rec = _reconstruct(taps, ranks, 31, 4, [0, 1, 0, 1])
+    for v in range(4):
+        P = psfs[v].astype(np.float64)
+        assert np.linalg.norm(rec[v] - P) <= 1e-6 * np.linalg.norm(P)
+
+
+def test_general_psf_full_rank_reconstructs():
+    rng = np.random.default_rng(0)
+    psfs = rng.random((2, 9, 9)).astype(np.float32)
+    ranks, taps = mvd.mvd_psf_factors(psfs, rank_tol=0.0)
+    assert list(ranks) == [9, 9]
+    rec = _reconstruct(taps, ranks, 9, 2, [0, 1])
+    for v in range(2):
+        P = psfs[v].astype(np.float64)
+        assert np.linalg.norm(rec[v] - P) <= 1e-6 * np.linalg.norm(P)
+    # the default tolerance keeps every term a random PSF needs
+    r2, t2 = mvd.mvd_psf_factors(psfs)
+    rec2 = _reconstruct(t2, r2, 9, 2, [0, 1])
+    for v in range(2):
+        assert np.linalg.norm(rec2[v] - psfs[v]) <= 1e-6 * np.linalg.norm(psfs[v])
+
+
+def test_rotated_gaussian_needs_several_terms():
+    psfs = synth.gaussian_psf(17, 5.0, 1.2, 30.0)[None]
+    ranks, taps = mvd.mvd_psf_factors(psfs)
+    assert 1 < ranks[0] <= 17
+    rec = _reconstruct(taps, ranks, 17, 1, [0])
+    assert np.linalg.norm(rec[0] - psfs[0]) <= 1e-6 * np.linalg.norm(psfs[0])
