@@ -41,6 +41,10 @@ WORKLOADS = {
                       density=1e-4, iters=10, seed=0,
                       label="2 views, 512^3 uint16 stacks resliced on the GPU to 512 planes of 512x512, "
                             "31x31 PSFs sigma (1.5, 8) px turned by 90 degrees, 10 iterations"),
+    "slab512": dict(Z=512, Y=128, X=512, K=31, sigma_axial=8.0, sigma_lateral=1.5, angles=(0.0, 90.0),
+                    density=1e-4, iters=10, seed=0,
+                    label="2 views, 512x128x512 uint16 slab: 128 planes of 512x512 (profiling case, "
+                          "one quarter of the 512^3 volume)"),
     "volume128": dict(Z=128, Y=128, X=128, K=31, sigma_axial=8.0, sigma_lateral=1.5, angles=(0.0, 90.0),
                       density=1e-4, iters=10, seed=0,
                       label="2 views, 128^3 uint16 (quick check)"),

@@ -81,6 +81,19 @@ typedef enum {
     MVD_ALGO_DIRECT = 2
 } mvd_algo;
 
+typedef enum {
+    /* All views use the same estimate and their corrections are multiplied,
+     * as the update equation of Supp. Note 1 is printed (default). */
+    MVD_ORDER_SIMULTANEOUS = 0,
+    /* The views update the estimate one after another, each with its own
+     * factor of the same equation evaluated at the current estimate (the
+     * sequential scheme of the multi-view RL work the paper builds on, Supp.
+     * Note 2 sec. 1).  The simultaneous product over-corrects when several
+     * views share a PSF (e.g. views 180 degrees apart) and can diverge;
+     * each sequential sub-step is a single-view RL step. */
+    MVD_ORDER_SEQUENTIAL = 1
+} mvd_update_order;
+
 /* Summary of what a context decided; filled by mvd_get_info. */
 typedef struct {
     int views;
@@ -89,6 +102,7 @@ typedef struct {
     int iters;
     int boundary;
     int algo;                   /* mvd_algo in use                          */
+    int order;                  /* mvd_update_order in use                  */
     int rank[16];               /* SVD terms kept per view (first 16 views) */
     int blur_groups;            /* number of distinct PSFs among the views  */
     int blur_terms;             /* SVD terms summed over distinct PSFs      */
@@ -114,6 +128,9 @@ mvd_status mvd_destroy(mvd_ctx *ctx);
 /* Select the route (default MVD_ALGO_FUSED).  MVD_ERR_UNSUPPORTED if the
  * fused path cannot take this PSF size (it takes K <= 47). */
 mvd_status mvd_set_algo(mvd_ctx *ctx, mvd_algo algo);
+
+/* Select how the views combine within one iteration (default simultaneous). */
+mvd_status mvd_set_update_order(mvd_ctx *ctx, mvd_update_order order);
 
 /* Relative Frobenius tolerance below which trailing SVD terms of a PSF are
  * dropped (default 3e-7, below the FP32 rounding of the PSF's entries).

@@ -149,15 +149,30 @@ def init_mean(phi: np.ndarray) -> np.ndarray:
     return phi.mean(axis=(0, 2, 3))
 
 
-def rl_step(psi, phi_planes, psfs, boundary=ZERO, eps=1e-6, route="direct"):
+def rl_step(psi, phi_planes, psfs, boundary=ZERO, eps=1e-6, route="direct",
+            order="simultaneous"):
     """One MV-RL update of one plane (Supp. Note 1, update equation).
 
-    psi: [H][W]; phi_planes: [V][H][W]; psfs: [V][K][K].  Every view's
-    ratio uses the same psi (simultaneous product).
+    psi: [H][W]; phi_planes: [V][H][W]; psfs: [V][K][K].
+
+    order="simultaneous": every view's ratio uses the same psi and the
+    views' corrections are multiplied, as the equation is printed.
+    order="sequential": the views update psi one after another, each with
+    the single-view factor of the same equation evaluated at the current
+    psi (the sequential scheme of the multi-view RL literature the paper
+    builds on, Supp. Note 2 sec. 1).
     """
     conv = convolve if route == "direct" else convolve_fft
     corr = correlate if route == "direct" else correlate_fft
     psi = np.asarray(psi, dtype=np.float64)
+    if order == "sequential":
+        for v in range(len(psfs)):
+            blur = conv(psi, psfs[v], boundary)
+            ratio = np.asarray(phi_planes[v], dtype=np.float64) / np.maximum(blur, eps)
+            psi = psi * corr(ratio, psfs[v], boundary)
+        return psi
+    if order != "simultaneous":
+        raise ValueError(f"unknown update order {order!r}")
     update = np.ones_like(psi)
     for v in range(len(psfs)):
         blur = conv(psi, psfs[v], boundary)
@@ -167,7 +182,7 @@ def rl_step(psi, phi_planes, psfs, boundary=ZERO, eps=1e-6, route="direct"):
 
 
 def rl_planes(phi, psfs, iters, boundary=ZERO, eps=1e-6, psi0=None,
-              route="direct", planes=None):
+              route="direct", planes=None, order="simultaneous"):
     """Plane-wise MV-RL over a stack of planes.
 
     phi:  [V][P][H][W] data (any real dtype; used as FP64)
@@ -175,6 +190,7 @@ def rl_planes(phi, psfs, iters, boundary=ZERO, eps=1e-6, psi0=None,
     psi0: None -> per-plane mean initial estimate; else [P][H][W]
     planes: optional iterable of plane indices to compute (others skipped;
             the result then holds only those planes, in that order)
+    order:  "simultaneous" (default, as printed) or "sequential" (see rl_step)
     Returns the estimate after ``iters`` updates, FP64 [n][H][W].
     """
     phi = np.asarray(phi)
@@ -191,7 +207,7 @@ def rl_planes(phi, psfs, iters, boundary=ZERO, eps=1e-6, psi0=None,
         else:
             psi = np.asarray(psi0[p], dtype=np.float64).copy()
         for _ in range(iters):
-            psi = rl_step(psi, phi[:, p], psfs, boundary, eps, route)
+            psi = rl_step(psi, phi[:, p], psfs, boundary, eps, route, order)
         out[n] = psi
     return out
 

@@ -144,6 +144,7 @@ struct mvd_ctx {
     mvd_boundary boundary = MVD_BOUNDARY_ZERO;
     float eps = 1e-6f;
     mvd_algo algo = MVD_ALGO_FUSED;
+    mvd_update_order order = MVD_ORDER_SIMULTANEOUS;
     double rank_tol = kDefaultRankTol;
     std::vector<float> psfs;
     mvd::FactorTable ft;
@@ -201,14 +202,22 @@ mvd_status run_fused(mvd_ctx *c, const void *data, mvd_dtype dt, float *est, int
         }
         return MVD_OK;
     }
+    // simultaneous: one launch pair over all views; sequential: one per view
+    const int step = c->order == MVD_ORDER_SEQUENTIAL ? 1 : c->V;
+    bool first = init_mean != 0;
     for (int t = 0; t < c->iters; ++t) {
-        a.psi_in = (t == 0 && init_mean) ? nullptr : est;
-        c->prof.mark(s, "blur_ratio");
-        e = mvd::launch_fused_blur_ratio(a, s);
-        if (e != cudaSuccess) return cuda_fail(e, "blur/ratio kernel");
-        c->prof.mark(s, "correlate_update");
-        e = mvd::launch_fused_correlate_update(a, s);
-        if (e != cudaSuccess) return cuda_fail(e, "correlate/update kernel");
+        for (int v0 = 0; v0 < c->V; v0 += step) {
+            a.view_lo = v0;
+            a.view_hi = v0 + step;
+            a.psi_in = first ? nullptr : est;
+            first = false;
+            c->prof.mark(s, "blur_ratio");
+            e = mvd::launch_fused_blur_ratio(a, s);
+            if (e != cudaSuccess) return cuda_fail(e, "blur/ratio kernel");
+            c->prof.mark(s, "correlate_update");
+            e = mvd::launch_fused_correlate_update(a, s);
+            if (e != cudaSuccess) return cuda_fail(e, "correlate/update kernel");
+        }
     }
     c->prof.end(s);
     return MVD_OK;
@@ -236,6 +245,7 @@ mvd_status run_plain(mvd_ctx *c, const void *data, mvd_dtype dt, float *est, int
     a.eps = c->eps;
     const int u16 = dt == MVD_U16;
     const size_t esz = u16 ? 2 : 4;
+    const bool sequential = c->order == MVD_ORDER_SEQUENTIAL;
     for (int p = 0; p < P; ++p) {
         float *psi = est + p * n;
         if (init_mean) {
@@ -249,9 +259,13 @@ mvd_status run_plain(mvd_ctx *c, const void *data, mvd_dtype dt, float *est, int
                 if ((e = mvd::plain_convolve(a, v, 0, direct, psi, tmp, b, s)) != cudaSuccess) return cuda_fail(e, "blur");
                 if ((e = mvd::plain_ratio(phi, u16, b, b, n, c->eps, s)) != cudaSuccess) return cuda_fail(e, "ratio");
                 if ((e = mvd::plain_convolve(a, v, 1, direct, b, tmp, cv, s)) != cudaSuccess) return cuda_fail(e, "correlate");
-                if ((e = mvd::plain_multiply(prod, cv, n, v == 0, s)) != cudaSuccess) return cuda_fail(e, "product");
+                if (sequential) {
+                    if ((e = mvd::plain_update(psi, cv, n, s)) != cudaSuccess) return cuda_fail(e, "update");
+                } else if ((e = mvd::plain_multiply(prod, cv, n, v == 0, s)) != cudaSuccess) {
+                    return cuda_fail(e, "product");
+                }
             }
-            if ((e = mvd::plain_update(psi, prod, n, s)) != cudaSuccess) return cuda_fail(e, "update");
+            if (!sequential && (e = mvd::plain_update(psi, prod, n, s)) != cudaSuccess) return cuda_fail(e, "update");
         }
     }
     c->prof.end(s);
@@ -394,6 +408,14 @@ mvd_status mvd_set_algo(mvd_ctx *c, mvd_algo algo) {
     return MVD_OK;
 }
 
+mvd_status mvd_set_update_order(mvd_ctx *c, mvd_update_order order) {
+    if (!c) return fail(MVD_ERR_ARG, "ctx is NULL");
+    if (order != MVD_ORDER_SIMULTANEOUS && order != MVD_ORDER_SEQUENTIAL)
+        return fail(MVD_ERR_ARG, "unknown update order %d", static_cast<int>(order));
+    c->order = order;
+    return MVD_OK;
+}
+
 mvd_status mvd_set_rank_tolerance(mvd_ctx *c, double tol) {
     if (!c) return fail(MVD_ERR_ARG, "ctx is NULL");
     if (!(tol >= 0.0) || !std::isfinite(tol)) return fail(MVD_ERR_ARG, "tolerance must be >= 0");
@@ -412,6 +434,7 @@ mvd_status mvd_get_info(const mvd_ctx *c, mvd_info *info) {
     info->iters = c->iters;
     info->boundary = c->boundary;
     info->algo = c->algo;
+    info->order = c->order;
     for (int v = 0; v < c->V && v < 16; ++v) info->rank[v] = c->ft.rank[v];
     info->blur_groups = c->ft.n_groups;
     info->blur_terms = c->ft.total_terms;

@@ -90,6 +90,9 @@ blur_ratio_kernel(const __grid_constant__ FusedArgs a, const int vec_ok) {
     __syncthreads();
 
     for (int g = 0; g < a.ft.n_groups; ++g) {
+        bool used = false;
+        for (int v = a.view_lo; v < a.view_hi; ++v) used |= (a.ft.group[v] == g);
+        if (!used) continue;
         const int lead = a.ft.group_leader[g];
         float acc[G::H_PER_THREAD][kNC];
 #pragma unroll
@@ -103,7 +106,7 @@ blur_ratio_kernel(const __grid_constant__ FusedArgs a, const int vec_ok) {
             horizontal_pass<K>(stage, tq + K, acc);
             __syncthreads();
         }
-        for (int v = 0; v < a.ft.views; ++v) {
+        for (int v = a.view_lo; v < a.view_hi; ++v) {
             if (a.ft.group[v] != g) continue;
             const long long vplane = (static_cast<long long>(v) * a.P + p) * plane_px;
 #pragma unroll
@@ -144,7 +147,7 @@ correlate_update_kernel(const __grid_constant__ FusedArgs a, const int vec_ok) {
 #pragma unroll
         for (int j = 0; j < kNC; ++j) prod[h][j] = 1.0f;
 
-    for (int v = 0; v < a.ft.views; ++v) {
+    for (int v = a.view_lo; v < a.view_hi; ++v) {
         const float *rsrc = a.ratio + (static_cast<long long>(v) * a.P + p) * plane_px;
         load_tile<K>(tile, rsrc, 0.0f, y0, x0, a.H, a.W, a.circular);
         __syncthreads();

@@ -61,6 +61,7 @@ struct FusedArgs {
     int H, W, P;
     int circular;
     float eps;
+    int view_lo, view_hi;    // views [lo, hi) take part in this launch
 };
 
 bool fused_supported(int K);

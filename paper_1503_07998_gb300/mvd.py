@@ -25,6 +25,7 @@ MVD_OK, MVD_ERR_ARG, MVD_ERR_CUDA, MVD_ERR_NOMEM, MVD_ERR_TIMEOUT, MVD_ERR_STATE
 BOUNDARY = {"zero": 0, "circular": 1}
 DTYPE = {"u16": 0, "f32": 1}
 ALGO = {"fused": 0, "plain": 1, "direct": 2}
+ORDER = {"simultaneous": 0, "sequential": 1}
 
 
 class MvdError(RuntimeError):
@@ -41,7 +42,7 @@ class _Info(ctypes.Structure):
     _fields_ = [
         ("views", ctypes.c_int), ("psf_size", ctypes.c_int),
         ("plane_h", ctypes.c_int), ("plane_w", ctypes.c_int),
-        ("iters", ctypes.c_int), ("boundary", ctypes.c_int), ("algo", ctypes.c_int),
+        ("iters", ctypes.c_int), ("boundary", ctypes.c_int), ("algo", ctypes.c_int), ("order", ctypes.c_int),
         ("rank", ctypes.c_int * 16), ("blur_groups", ctypes.c_int), ("blur_terms", ctypes.c_int),
         ("tile_h", ctypes.c_int), ("tile_w", ctypes.c_int),
         ("workspace_bytes", ctypes.c_size_t),
@@ -64,6 +65,7 @@ def lib() -> ctypes.CDLL:
     L.mvd_destroy.argtypes = [vp]
     L.mvd_set_algo.argtypes = [vp, i]
     L.mvd_set_rank_tolerance.argtypes = [vp, d]
+    L.mvd_set_update_order.argtypes = [vp, i]
     L.mvd_get_info.argtypes = [vp, ctypes.POINTER(_Info)]
     L.mvd_reslice.argtypes = [vp, vp, i, i, i, i, i, vp, vp]
     L.mvd_deconvolve_planes.argtypes = [vp, vp, i, vp, i, i, vp]
@@ -78,6 +80,7 @@ def lib() -> ctypes.CDLL:
     L.mvd_launch_count.argtypes = []
     L.mvd_launch_count.restype = ctypes.c_uint64
     for name in ("mvd_create", "mvd_destroy", "mvd_set_algo", "mvd_set_rank_tolerance", "mvd_get_info",
+                 "mvd_set_update_order",
                  "mvd_reslice", "mvd_deconvolve_planes", "mvd_run_host", "mvd_psf_factors",
                  "mvd_profile_enable", "mvd_profile_read"):
         getattr(L, name).restype = ctypes.c_int
@@ -130,6 +133,7 @@ class Info:
     iters: int
     boundary: int
     algo: int
+    order: int
     rank: list
     blur_groups: int
     blur_terms: int
@@ -182,6 +186,10 @@ def mvd_set_algo(ctx: Context, algo: str) -> None:
     _check(lib().mvd_set_algo(ctx.handle, ALGO[algo]), "mvd_set_algo")
 
 
+def mvd_set_update_order(ctx: Context, order: str) -> None:
+    _check(lib().mvd_set_update_order(ctx.handle, ORDER[order]), "mvd_set_update_order")
+
+
 def mvd_set_rank_tolerance(ctx: Context, tol: float) -> None:
     _check(lib().mvd_set_rank_tolerance(ctx.handle, float(tol)), "mvd_set_rank_tolerance")
 
@@ -189,7 +197,7 @@ def mvd_set_rank_tolerance(ctx: Context, tol: float) -> None:
 def mvd_get_info(ctx: Context) -> Info:
     inf = _Info()
     _check(lib().mvd_get_info(ctx.handle, ctypes.byref(inf)), "mvd_get_info")
-    return Info(inf.views, inf.psf_size, inf.plane_h, inf.plane_w, inf.iters, inf.boundary, inf.algo,
+    return Info(inf.views, inf.psf_size, inf.plane_h, inf.plane_w, inf.iters, inf.boundary, inf.algo, inf.order,
                 list(inf.rank)[:min(16, inf.views)], inf.blur_groups, inf.blur_terms, inf.tile_h, inf.tile_w,
                 int(inf.workspace_bytes))
 

@@ -32,12 +32,14 @@ def mvd():
     return m
 
 
-def run_gpu(mvd, phi, psfs, iters, boundary="zero", eps=1e-6, algo="fused", psi0=None, rank_tol=None):
+def run_gpu(mvd, phi, psfs, iters, boundary="zero", eps=1e-6, algo="fused", psi0=None, rank_tol=None,
+            order="simultaneous"):
     V, P, H, W = phi.shape
     K = psfs.shape[-1]
     ctx = mvd.mvd_create(V, psfs, K, H, W, iters, boundary, eps)
     try:
         mvd.mvd_set_algo(ctx, algo)
+        mvd.mvd_set_update_order(ctx, order)
         if rank_tol is not None:
             mvd.mvd_set_rank_tolerance(ctx, rank_tol)
         d = torch.from_numpy(np.ascontiguousarray(phi)).to(DEV)
@@ -110,16 +112,28 @@ def test_ragged_tiles_general_psfs(mvd, boundary, K, V, H, W, dtype):
 
 
 @pytest.mark.parametrize("boundary", ["zero", "circular"])
-def test_gaussian_views_uint16_rank_one(mvd, boundary):
-    c = synth.plane_case(seed=3, H=200, W=168, n_planes=3, n_blobs=150, K=31, sigma_axial=8.0,
-                         sigma_lateral=1.5, angles=(0, 90, 180, 270), dtype=np.uint16)
-    info_ctx = mvd.mvd_create(4, c.psfs, 31, 200, 168, 10, boundary, 1e-6)
+@pytest.mark.parametrize("algo", ["fused", "plain"])
+def test_four_views_sequential_order(mvd, boundary, algo):
+    """Views at 0/90/180/270 degrees (two distinct in-plane PSFs, rank one),
+    each view updating the estimate in turn."""
+    c = synth.plane_case(seed=3, H=200, W=168, n_planes=3, n_blobs=40, K=41, sigma_axial=10.0,
+                         sigma_lateral=1.8, angles=(0, 90, 180, 270), dtype=np.uint16)
+    info_ctx = mvd.mvd_create(4, c.psfs, 41, 200, 168, 10, boundary, 1e-6)
     info = mvd.mvd_get_info(info_ctx)
     info_ctx.close()
-    assert info.rank == [1, 1, 1, 1] and info.blur_groups == 2
-    ref = oracle.rl_planes(c.phi, c.psfs, 10, boundary=boundary, eps=1e-6, route="fft")
-    got = run_gpu(mvd, c.phi, c.psfs, 10, boundary)
-    assert_parity(got, ref, what=f"gaussian 4 views {boundary}")
+    assert info.rank == [1, 1, 1, 1] and info.blur_groups == 2 and info.blur_terms == 2
+    ref = oracle.rl_planes(c.phi, c.psfs, 10, boundary=boundary, eps=1e-6, route="fft", order="sequential")
+    got = run_gpu(mvd, c.phi, c.psfs, 10, boundary, algo=algo, order="sequential")
+    assert_parity(got, ref, what=f"4 views sequential {boundary} {algo}")
+
+
+def test_shared_psf_blurred_once_simultaneous(mvd):
+    """Views 180 degrees apart share one PSF: kernel A blurs once for both."""
+    c = synth.plane_case(seed=4, H=130, W=150, n_planes=2, n_blobs=60, K=31, sigma_axial=8.0,
+                         sigma_lateral=1.5, angles=(0, 180), dtype=np.uint16)
+    ref = oracle.rl_planes(c.phi, c.psfs, 3, eps=1e-6, route="fft")
+    got = run_gpu(mvd, c.phi, c.psfs, 3)
+    assert_parity(got, ref, what="shared PSF")
 
 
 def test_given_initial_estimate_and_zero_iterations(mvd):

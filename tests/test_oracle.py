@@ -278,3 +278,23 @@ def test_golden_fixtures_reproduce(name):
                            np.array(case["psf"], dtype=np.float64),
                            case["iters"], boundary=case["boundary"], eps=case["eps"])
     np.testing.assert_allclose(out, np.array(case["expected"]), rtol=1e-13)
+
+
+@pytest.mark.parametrize("boundary", ["zero", "circular"])
+def test_sequential_order_matches_textbook_and_conserves_last_view_flux(boundary):
+    """Sequential order: each view applies a single-view RL step to the
+    current estimate, so after a full iteration sum(psi) = sum(phi_last)."""
+    rng = np.random.default_rng(12)
+    H, W, V, K = 5, 6, 3, 3
+    psfs = rng.random((V, K, K)) + 0.1
+    phi = rng.uniform(1, 20, size=(V, 1, H, W))
+    A = [conv_matrix(psfs[v], H, W, boundary) for v in range(V)]
+    psi = np.full(H * W, phi.mean())
+    for _ in range(3):
+        for v in range(V):
+            psi = psi * (A[v].T @ (phi[v, 0].ravel() / np.maximum(A[v] @ psi, 1e-6)))
+        assert abs(psi.sum() - phi[V - 1].sum()) <= 1e-11 * phi[V - 1].sum()
+    out = oracle.rl_planes(phi, psfs, 3, boundary=boundary, order="sequential")
+    np.testing.assert_allclose(out[0].ravel(), psi, rtol=1e-12)
+    one = oracle.rl_planes(phi[:1], psfs[:1], 3, boundary=boundary, order="sequential")
+    np.testing.assert_allclose(one, oracle.rl_planes(phi[:1], psfs[:1], 3, boundary=boundary), rtol=1e-14)
