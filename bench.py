@@ -216,7 +216,9 @@ def run_reference(args, wl):
     stacks, psfs = make_inputs(wl, wl["seed"], dev)
     V = stacks.shape[0]
     idx = np.linspace(0, wl["Y"] - 1, S).round().astype(int)
-    planes = stacks[:, :, idx, :].permute(0, 2, 1, 3).contiguous().cpu().to(torch.int32).numpy()
+    # plane y of view v is stacks[v, :, y, :]; uint16 CUDA tensors have no
+    # advanced indexing, so planes are copied one by one
+    planes = np.stack([stacks[:, :, int(y), :].cpu().numpy() for y in idx], axis=1)
     del stacks
     for _ in range(args.warmup):
         oracle_sample(pool, planes, psfs, wl["iters"])
@@ -353,7 +355,7 @@ def run_mvd(args, wl):
     cpu = None
     if pool is not None and rank == 0:
         idx = np.linspace(0, Y - 1, S).round().astype(int)
-        sample_planes = planes[:, idx].cpu().to(torch.int32).numpy()
+        sample_planes = np.stack([planes[:, int(y)].cpu().numpy() for y in idx], axis=1)
         t = oracle_sample(pool, sample_planes, psfs, iters)
         pool.close()
         cpu = {"value": S * Z * X * iters * V / t, "unit": UNIT, "cores": S, "kind": "oracle",
