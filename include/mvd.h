@@ -172,6 +172,19 @@ mvd_status mvd_run_host(mvd_ctx *ctx, const void *stacks_host, mvd_dtype dt,
                         int nz, int ny, int nx, float *out_host, int chunk_planes,
                         void *stream);
 
+/* Device-side status of the context's kernels.  Waits for `stream`, then
+ * reads and clears the context's device status word: MVD_ERR_TIMEOUT if a
+ * kernel's bounded wait for a tile copy ran out (the kernel then left its
+ * tile unfinished), MVD_OK otherwise.  Kernels never hang on a lost copy:
+ * every wait spins for at most the context's wait budget. */
+mvd_status mvd_device_status(mvd_ctx *ctx, void *stream);
+
+/* Clock cycles a kernel may wait for one tile copy before it reports
+ * MVD_ERR_TIMEOUT (default 2e9, about one second); 0 restores the default.
+ * A negative value injects the fault: every tile wait reports a timeout once
+ * its copy has landed, so the error path can be tested without a real one. */
+mvd_status mvd_set_wait_budget(mvd_ctx *ctx, long long cycles);
+
 /* Per-kernel device time of this context's launches, taken with CUDA events
  * recorded on the launching stream around every kernel.  Enabling (on != 0)
  * or disabling clears what was collected.  mvd_profile_read waits for the

@@ -153,6 +153,8 @@ struct mvd_ctx {
     DevBuf run_stack[2], run_planes, run_est[2];
     cudaStream_t copy_in = nullptr, copy_out = nullptr;
     Profiler prof;
+    DevBuf status;                       // one int: device status word
+    long long wait_budget = mvd::kDefaultWaitBudget;
 };
 
 namespace {
@@ -186,6 +188,8 @@ mvd::FusedArgs fused_args(const mvd_ctx *c, const void *data, mvd_dtype dt, floa
     a.P = P;
     a.circular = c->boundary == MVD_BOUNDARY_CIRCULAR;
     a.eps = c->eps;
+    a.err = c->status.as<int>();
+    a.wait_budget = c->wait_budget;
     return a;
 }
 
@@ -291,6 +295,28 @@ const char *mvd_status_string(mvd_status s) {
 
 const char *mvd_last_error(void) { return t_last_error.c_str(); }
 
+mvd_status mvd_device_status(mvd_ctx *c, void *stream) {
+    if (!c) return fail(MVD_ERR_ARG, "ctx is NULL");
+    DeviceGuard g(c->device);
+    cudaError_t e = cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(e, "stream");
+    int word = 0;
+    if ((e = cudaMemcpy(&word, c->status.ptr, sizeof word, cudaMemcpyDeviceToHost)) != cudaSuccess)
+        return cuda_fail(e, "status read");
+    if (word != 0) {
+        if ((e = cudaMemset(c->status.ptr, 0, sizeof(int))) != cudaSuccess) return cuda_fail(e, "status clear");
+        if (word & mvd::kDevTimeout) return fail(MVD_ERR_TIMEOUT, "a kernel's wait for a tile copy ran out");
+        return fail(MVD_ERR_CUDA, "device status word %d", word);
+    }
+    return MVD_OK;
+}
+
+mvd_status mvd_set_wait_budget(mvd_ctx *c, long long cycles) {
+    if (!c) return fail(MVD_ERR_ARG, "ctx is NULL");
+    c->wait_budget = cycles == 0 ? mvd::kDefaultWaitBudget : cycles;
+    return MVD_OK;
+}
+
 mvd_status mvd_profile_enable(mvd_ctx *c, int on) {
     if (!c) return fail(MVD_ERR_ARG, "ctx is NULL");
     DeviceGuard g(c->device);
@@ -371,6 +397,10 @@ mvd_status mvd_create(mvd_ctx **out, int views, const float *psfs_host, int psf_
     c->eps = eps;
     c->algo = mvd::fused_supported(psf_size) ? MVD_ALGO_FUSED : MVD_ALGO_PLAIN;
     c->psfs.assign(psfs_host, psfs_host + views * KK);
+    if ((e = c->status.ensure(sizeof(int))) != cudaSuccess || (e = cudaMemset(c->status.ptr, 0, sizeof(int))) != cudaSuccess) {
+        mvd_destroy(c);
+        return fail(MVD_ERR_NOMEM, "status word: %s", cudaGetErrorString(e));
+    }
     mvd_status s = upload_factors(c);
     if (s != MVD_OK) {
         mvd_destroy(c);
@@ -392,6 +422,7 @@ mvd_status mvd_destroy(mvd_ctx *c) {
     for (auto &b : c->run_est) b.release();
     c->run_planes.release();
     c->prof.destroy();
+    c->status.release();
     if (c->copy_in) cudaStreamDestroy(c->copy_in);
     if (c->copy_out) cudaStreamDestroy(c->copy_out);
     delete c;

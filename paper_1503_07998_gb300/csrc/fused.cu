@@ -4,19 +4,27 @@
 //   blur_ratio        r_v = phi_v / max(psi * P_v, eps)   for every view v
 //   correlate_update  psi <- psi * prod_v (r_v (*) P_v^*)
 //
-// A CTA owns a TY x 128 output tile of one plane.  Kernel A reads the psi
-// tile (with a halo of R) once for all views; views whose PSFs are identical
-// share one blur.  Kernel B reads each view's ratio tile with its halo,
-// keeps the running product of the views' corrections in registers and
-// updates psi in place: each CTA reads and writes only its own output
-// pixels, and kernel A of the next iteration starts after kernel B ends in
-// stream order.
+// A CTA owns a TY x 128 output tile of one plane.  Kernel A stages the psi
+// tile (halo R) once for all views; views whose PSFs are identical share
+// one blur.  Kernel B stages each view's ratio tile with its halo, keeps the
+// running product of the views' corrections in registers and updates psi in
+// place: each CTA reads and writes only its own output pixels, and kernel A
+// of the next iteration starts after kernel B ends in stream order.
+//
+// Tiles arrive by TMA (one thread issues a 3D box copy, hardware zero fill
+// outside the plane = the ZERO boundary) whenever the plane rows are 16-byte
+// multiples; the circular boundary, unaligned planes and the constant first
+// estimate use a software load into the same layout.
 //
 // HBM traffic per voxel-iteration (uint16 data): kernel A reads psi (4 B) and
 // phi_v (2V B) and writes r_v (4V B); kernel B reads r_v (4V B) and psi (4 B)
 // and writes psi (4 B): 12 + 10V bytes.  Halo re-reads hit L2.
+#include <cuda.h>
 #include <cuda_runtime.h>
+#include <cudaTypedefs.h>
+
 #include <cstdint>
+#include <cstring>
 
 #include "fused_common.cuh"
 
@@ -24,6 +32,30 @@ namespace mvd {
 namespace fused {
 
 namespace {
+
+constexpr long long kDrainBudget = 4000000000LL;
+
+struct KParams {
+    CUtensorMap map;   // psi (kernel A) or the ratio planes (kernel B); valid if use_tma
+    FusedArgs a;
+    int use_tma;
+    int vec_ok;
+};
+
+// Wait for the tile on `bar`; on an expired budget flag the device status,
+// drain the copy (bounded again) and make the whole CTA leave.  A negative
+// budget makes every wait report a timeout once its copy has landed (fault
+// injection for testing the error path).
+__device__ __forceinline__ bool wait_tile(uint64_t *bar, uint32_t parity, const FusedArgs &a,
+                                          volatile int *abort_flag) {
+    if (a.wait_budget < 0 || !tma::mbar_wait_bounded(bar, parity, a.wait_budget)) {
+        atomicOr(a.err, kDevTimeout);
+        tma::mbar_wait_bounded(bar, parity, kDrainBudget);
+        *abort_flag = 1;
+    }
+    __syncthreads();
+    return *abort_flag == 0;
+}
 
 __device__ __forceinline__ void load16_phi(const void *phi, int u16, long long off, bool vec, int n,
                                            float (&out)[kNC]) {
@@ -74,20 +106,40 @@ __device__ __forceinline__ void store16(float *dst, bool vec, int n, const float
 
 template <int K>
 __global__ void __launch_bounds__(kThreads, Geo<K>::MIN_BLOCKS)
-blur_ratio_kernel(const __grid_constant__ FusedArgs a, const int vec_ok) {
+blur_ratio_kernel(const __grid_constant__ KParams kp) {
     using G = Geo<K>;
-    extern __shared__ float4 smem4[];
-    float *tile = reinterpret_cast<float *>(smem4);
-    float *stage = tile + G::IN_H * G::IN_LD;
+    const FusedArgs &a = kp.a;
+    extern __shared__ __align__(128) unsigned char smem[];
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(smem + 8);
+    float *tile = reinterpret_cast<float *>(smem + kHeaderBytes);
+    float *stage = tile + G::BOX_H * G::BOX_W;
 
     const int p = blockIdx.z;
     const int y0 = blockIdx.y * G::TY;
     const int x0 = blockIdx.x * G::TX;
     const long long plane_px = static_cast<long long>(a.H) * a.W;
-    const float *psi = a.psi_in ? a.psi_in + p * plane_px : nullptr;
-    const float fill = a.psi_in ? 0.0f : __ldg(a.means + p);
-    load_tile<K>(tile, psi, fill, y0, x0, a.H, a.W, a.circular);
+    const bool use_tma = kp.use_tma && a.psi_in != nullptr;
+    if (threadIdx.x == 0) {
+        *abort_flag = 0;
+        if (use_tma) {
+            tma::mbar_init(bar, 1);
+            tma::fence_barrier_init();
+        }
+    }
     __syncthreads();
+    if (use_tma) {
+        if (threadIdx.x == 0) {
+            tma::mbar_arrive_expect_tx(bar, G::TILE_BYTES);
+            tma::load_3d(tile, &kp.map, bar, x0 - G::R4, y0 - G::R, p);
+        }
+        if (!wait_tile(bar, 0, a, abort_flag)) return;
+    } else {
+        const float *psi = a.psi_in ? a.psi_in + p * plane_px : nullptr;
+        const float fill = a.psi_in ? 0.0f : __ldg(a.means + p);
+        load_tile_sw<K>(tile, psi, fill, y0, x0, a.H, a.W, a.circular);
+        __syncthreads();
+    }
 
     for (int g = 0; g < a.ft.n_groups; ++g) {
         bool used = false;
@@ -115,7 +167,7 @@ blur_ratio_kernel(const __grid_constant__ FusedArgs a, const int vec_ok) {
                 item_origin<K>(h, y0, x0, y, x);
                 if (y >= a.H || x >= a.W) continue;
                 const int n = min(kNC, a.W - x);
-                const bool vec = vec_ok && n == kNC;
+                const bool vec = kp.vec_ok && n == kNC;
                 const long long off = vplane + static_cast<long long>(y) * a.W + x;
                 float phi[kNC];
                 load16_phi(a.phi, a.phi_u16, off, vec, n, phi);
@@ -130,16 +182,27 @@ blur_ratio_kernel(const __grid_constant__ FusedArgs a, const int vec_ok) {
 
 template <int K>
 __global__ void __launch_bounds__(kThreads, Geo<K>::MIN_BLOCKS)
-correlate_update_kernel(const __grid_constant__ FusedArgs a, const int vec_ok) {
+correlate_update_kernel(const __grid_constant__ KParams kp) {
     using G = Geo<K>;
-    extern __shared__ float4 smem4[];
-    float *tile = reinterpret_cast<float *>(smem4);
-    float *stage = tile + G::IN_H * G::IN_LD;
+    const FusedArgs &a = kp.a;
+    extern __shared__ __align__(128) unsigned char smem[];
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(smem + 8);
+    float *tile = reinterpret_cast<float *>(smem + kHeaderBytes);
+    float *stage = tile + G::BOX_H * G::BOX_W;
 
     const int p = blockIdx.z;
     const int y0 = blockIdx.y * G::TY;
     const int x0 = blockIdx.x * G::TX;
     const long long plane_px = static_cast<long long>(a.H) * a.W;
+    if (threadIdx.x == 0) {
+        *abort_flag = 0;
+        if (kp.use_tma) {
+            tma::mbar_init(bar, 1);
+            tma::fence_barrier_init();
+        }
+    }
+    __syncthreads();
 
     float prod[G::H_PER_THREAD][kNC];
 #pragma unroll
@@ -147,10 +210,21 @@ correlate_update_kernel(const __grid_constant__ FusedArgs a, const int vec_ok) {
 #pragma unroll
         for (int j = 0; j < kNC; ++j) prod[h][j] = 1.0f;
 
+    uint32_t phase = 0;
     for (int v = a.view_lo; v < a.view_hi; ++v) {
-        const float *rsrc = a.ratio + (static_cast<long long>(v) * a.P + p) * plane_px;
-        load_tile<K>(tile, rsrc, 0.0f, y0, x0, a.H, a.W, a.circular);
-        __syncthreads();
+        if (kp.use_tma) {
+            if (threadIdx.x == 0) {
+                tma::fence_proxy_async_smem();
+                tma::mbar_arrive_expect_tx(bar, G::TILE_BYTES);
+                tma::load_3d(tile, &kp.map, bar, x0 - G::R4, y0 - G::R, v * a.P + p);
+            }
+            if (!wait_tile(bar, phase, a, abort_flag)) return;
+            phase ^= 1u;
+        } else {
+            const float *rsrc = a.ratio + (static_cast<long long>(v) * a.P + p) * plane_px;
+            load_tile_sw<K>(tile, rsrc, 0.0f, y0, x0, a.H, a.W, a.circular);
+            __syncthreads();
+        }
         float c[G::H_PER_THREAD][kNC];
 #pragma unroll
         for (int h = 0; h < G::H_PER_THREAD; ++h)
@@ -176,7 +250,7 @@ correlate_update_kernel(const __grid_constant__ FusedArgs a, const int vec_ok) {
         item_origin<K>(h, y0, x0, y, x);
         if (y >= a.H || x >= a.W) continue;
         const int n = min(kNC, a.W - x);
-        const bool vec = vec_ok && n == kNC;
+        const bool vec = kp.vec_ok && n == kNC;
         const long long off = p * plane_px + static_cast<long long>(y) * a.W + x;
         float old[kNC];
         if (a.psi_in) {
@@ -191,6 +265,38 @@ correlate_update_kernel(const __grid_constant__ FusedArgs a, const int vec_ok) {
         store16(a.psi_out + off, vec, n, out);
     }
 }
+
+// ---- host side ------------------------------------------------------------
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }
+    return fn;
+}
+
+// 3D FP32 tensor [D][H][W] with a (box_w x box_h x 1) box; zero fill outside.
+bool encode_3d(CUtensorMap *m, const void *base, int W, int H, long long D, int box_w, int box_h) {
+    auto fn = encode_fn();
+    if (!fn) return false;
+    cuuint64_t dims[3] = {static_cast<cuuint64_t>(W), static_cast<cuuint64_t>(H), static_cast<cuuint64_t>(D)};
+    cuuint64_t strides[2] = {static_cast<cuuint64_t>(W) * 4, static_cast<cuuint64_t>(W) * H * 4};
+    cuuint32_t box[3] = {static_cast<cuuint32_t>(box_w), static_cast<cuuint32_t>(box_h), 1};
+    cuuint32_t estr[3] = {1, 1, 1};
+    return fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<void *>(base), dims, strides, box, estr,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+inline bool aligned16(const void *p) { return reinterpret_cast<uintptr_t>(p) % 16 == 0; }
 
 template <int K>
 cudaError_t launch_pair(const FusedArgs &a, int which, cudaStream_t s) {
@@ -210,15 +316,23 @@ cudaError_t launch_pair(const FusedArgs &a, int which, cudaStream_t s) {
         attr_set |= bit;
     }
     const dim3 grid((a.W + G::TX - 1) / G::TX, (a.H + G::TY - 1) / G::TY, a.P);
-    const bool aligned = (reinterpret_cast<uintptr_t>(a.phi) % 16 == 0) &&
-                         (reinterpret_cast<uintptr_t>(a.ratio) % 16 == 0) &&
-                         (reinterpret_cast<uintptr_t>(a.psi_out) % 16 == 0) &&
-                         (a.psi_in == nullptr || reinterpret_cast<uintptr_t>(a.psi_in) % 16 == 0);
-    const int vec_ok = aligned && (a.W % 16 == 0);
-    if (which == 0)
-        blur_ratio_kernel<K><<<grid, kThreads, G::SMEM_BYTES, s>>>(a, vec_ok);
-    else
-        correlate_update_kernel<K><<<grid, kThreads, G::SMEM_BYTES, s>>>(a, vec_ok);
+    KParams kp;
+    std::memset(&kp, 0, sizeof kp);
+    kp.a = a;
+    const bool aligned = aligned16(a.phi) && aligned16(a.ratio) && aligned16(a.psi_out) &&
+                         (a.psi_in == nullptr || aligned16(a.psi_in));
+    kp.vec_ok = aligned && (a.W % 16 == 0);
+    const bool tma_ok = !a.circular && (a.W % 4 == 0);
+    if (which == 0) {
+        if (tma_ok && a.psi_in && aligned16(a.psi_in))
+            kp.use_tma = encode_3d(&kp.map, a.psi_in, a.W, a.H, a.P, G::BOX_W, G::BOX_H);
+        blur_ratio_kernel<K><<<grid, kThreads, G::SMEM_BYTES, s>>>(kp);
+    } else {
+        if (tma_ok && aligned16(a.ratio))
+            kp.use_tma = encode_3d(&kp.map, a.ratio, a.W, a.H, static_cast<long long>(a.ft.views) * a.P,
+                                   G::BOX_W, G::BOX_H);
+        correlate_update_kernel<K><<<grid, kThreads, G::SMEM_BYTES, s>>>(kp);
+    }
     count_launch();
     return cudaGetLastError();
 }

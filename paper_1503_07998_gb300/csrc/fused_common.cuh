@@ -17,12 +17,18 @@
 //               the staging tile's row pitch is an odd multiple of 4 floats,
 //               so every 8-lane phase of a 16-byte load hits 8 distinct
 //               4-bank groups.
+//
+// The input tile is the TMA box [BOX_H][BOX_W]: rows y0-R .. y0+TY+R-1 and
+// columns x0-R4 .. x0+TX+R4-1, where R4 = R rounded up to a multiple of 4 so
+// that the box starts on a 16-byte boundary; the vertical pass reads its
+// TX+2R columns from column COL0 = R4-R on.
 #pragma once
 
 #include <cuda_runtime.h>
 #include <cstdint>
 
 #include "mvd_internal.h"
+#include "tma.cuh"
 
 namespace mvd {
 namespace fused {
@@ -31,6 +37,7 @@ constexpr int kThreads = 256;
 constexpr int kNR = 16;      // rows per vertical item
 constexpr int kNC = 16;      // columns per horizontal item
 constexpr int kTX = 128;     // output tile width
+constexpr int kHeaderBytes = 128;   // mbarrier + abort flag, keeps the tile 128-byte aligned
 
 __host__ __device__ constexpr int round_up(int a, int b) { return (a + b - 1) / b * b; }
 
@@ -42,37 +49,43 @@ __host__ __device__ constexpr int odd_quad_pitch(int w) {
 template <int K>
 struct Geo {
     static constexpr int R = (K - 1) / 2;
+    static constexpr int R4 = round_up(R, 4);
     static constexpr int TX = kTX;
-    static constexpr int IN_W = TX + 2 * R;                  // columns of the input tile
-    static constexpr int IN_LD = round_up(IN_W, 4);
+    static constexpr int IN_W = TX + 2 * R;                  // columns the vertical pass computes
+    static constexpr int BOX_W = TX + 2 * R4;                // tile pitch = TMA box width
+    static constexpr int COL0 = R4 - R;
     static constexpr int HL = round_up(kNC + 2 * R, 4);       // horizontal load width
     static constexpr int VB_LD = odd_quad_pitch((TX / kNC - 1) * kNC + HL);
-    static constexpr int smem_floats(int ty) { return (ty + 2 * R) * IN_LD + ty * VB_LD; }
+    static constexpr int smem_bytes(int ty) {
+        return kHeaderBytes + ((ty + 2 * R) * BOX_W + ty * VB_LD) * 4;
+    }
     // 64-row tiles while two CTAs still fit on an SM, else 32.
-    static constexpr int TY = (smem_floats(64) * 4 <= 112 * 1024) ? 64 : 32;
-    static constexpr int IN_H = TY + 2 * R;
-    static constexpr int SMEM_BYTES = smem_floats(TY) * 4;
+    static constexpr int TY = (smem_bytes(64) <= 112 * 1024) ? 64 : 32;
+    static constexpr int BOX_H = TY + 2 * R;
+    static constexpr int SMEM_BYTES = smem_bytes(TY);
+    static constexpr int TILE_BYTES = BOX_H * BOX_W * 4;
     static constexpr int V_ITEMS = IN_W * (TY / kNR);
     static constexpr int H_ITEMS = TY * (TX / kNC);
     static constexpr int H_PER_THREAD = H_ITEMS / kThreads;
     static_assert(H_ITEMS % kThreads == 0, "horizontal items must tile the CTA");
+    static_assert(BOX_W <= 256 && BOX_H <= 256, "TMA box dimensions are at most 256");
     static constexpr int MIN_BLOCKS = (SMEM_BYTES <= 112 * 1024) ? 2 : 1;
 };
 
-// Load the (IN_H x IN_W) halo'd tile of one plane whose output origin is
-// (y0, x0) into shared memory.  src == nullptr means a constant plane of
-// value `fill` (iteration 0 from the per-plane mean).  ZERO boundary: zero
-// outside the plane; CIRCULAR: indices modulo the plane size.
+// Software tile load (circular boundary, unaligned planes): same layout as
+// the TMA box.  src == nullptr means a constant plane of value `fill`
+// (iteration 0 from the per-plane mean).  ZERO: zero outside the plane;
+// CIRCULAR: indices modulo the plane size.
 template <int K>
-__device__ __forceinline__ void load_tile(float *__restrict__ tile, const float *__restrict__ src,
-                                          float fill, int y0, int x0, int H, int W, int circular) {
+__device__ __forceinline__ void load_tile_sw(float *__restrict__ tile, const float *__restrict__ src,
+                                             float fill, int y0, int x0, int H, int W, int circular) {
     using G = Geo<K>;
-    constexpr int N = G::IN_H * G::IN_W;
+    constexpr int N = G::BOX_H * G::BOX_W;
     for (int idx = threadIdx.x; idx < N; idx += kThreads) {
-        const int r = idx / G::IN_W;
-        const int c = idx - r * G::IN_W;
+        const int r = idx / G::BOX_W;
+        const int c = idx - r * G::BOX_W;
         int gy = y0 - G::R + r;
-        int gx = x0 - G::R + c;
+        int gx = x0 - G::R4 + c;
         float v = 0.0f;
         if (circular) {
             gy %= H; if (gy < 0) gy += H;
@@ -81,12 +94,12 @@ __device__ __forceinline__ void load_tile(float *__restrict__ tile, const float 
         } else if (gy >= 0 && gy < H && gx >= 0 && gx < W) {
             v = src ? __ldg(src + static_cast<long long>(gy) * W + gx) : fill;
         }
-        tile[r * G::IN_LD + c] = v;
+        tile[idx] = v;
     }
 }
 
-// Vertical pass: stage[i][c] = sum_m t[m] * tile[i + m][c] for the TY output
-// rows and all IN_W columns.
+// Vertical pass: stage[i][c] = sum_m t[m] * tile[i + m][COL0 + c] for the TY
+// output rows and IN_W columns.
 template <int K>
 __device__ __forceinline__ void vertical_pass(const float *__restrict__ tile, float *__restrict__ stage,
                                               const float *__restrict__ taps_g) {
@@ -97,13 +110,13 @@ __device__ __forceinline__ void vertical_pass(const float *__restrict__ tile, fl
     for (int it = threadIdx.x; it < G::V_ITEMS; it += kThreads) {
         const int rb = it / G::IN_W;
         const int c = it - rb * G::IN_W;
-        const float *col = tile + rb * kNR * G::IN_LD + c;
+        const float *col = tile + rb * kNR * G::BOX_W + G::COL0 + c;
         float acc[kNR];
 #pragma unroll
         for (int i = 0; i < kNR; ++i) acc[i] = 0.0f;
 #pragma unroll
         for (int m = 0; m < kNR + K - 1; ++m) {
-            const float x = col[m * G::IN_LD];
+            const float x = col[m * G::BOX_W];
 #pragma unroll
             for (int i = 0; i < kNR; ++i) {
                 const int j = m - i;

@@ -62,7 +62,12 @@ struct FusedArgs {
     int circular;
     float eps;
     int view_lo, view_hi;    // views [lo, hi) take part in this launch
+    int *err;                // device status word (kDevTimeout set on an expired wait)
+    long long wait_budget;   // clock cycles a tile wait may spin before it reports a timeout
 };
+
+constexpr int kDevTimeout = 1;
+constexpr long long kDefaultWaitBudget = 2000000000LL;   // about one second at 2 GHz
 
 bool fused_supported(int K);
 void fused_tile_shape(int K, int *tile_h, int *tile_w);

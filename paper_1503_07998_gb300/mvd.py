@@ -66,6 +66,8 @@ def lib() -> ctypes.CDLL:
     L.mvd_set_algo.argtypes = [vp, i]
     L.mvd_set_rank_tolerance.argtypes = [vp, d]
     L.mvd_set_update_order.argtypes = [vp, i]
+    L.mvd_device_status.argtypes = [vp, vp]
+    L.mvd_set_wait_budget.argtypes = [vp, ctypes.c_longlong]
     L.mvd_get_info.argtypes = [vp, ctypes.POINTER(_Info)]
     L.mvd_reslice.argtypes = [vp, vp, i, i, i, i, i, vp, vp]
     L.mvd_deconvolve_planes.argtypes = [vp, vp, i, vp, i, i, vp]
@@ -80,7 +82,7 @@ def lib() -> ctypes.CDLL:
     L.mvd_launch_count.argtypes = []
     L.mvd_launch_count.restype = ctypes.c_uint64
     for name in ("mvd_create", "mvd_destroy", "mvd_set_algo", "mvd_set_rank_tolerance", "mvd_get_info",
-                 "mvd_set_update_order",
+                 "mvd_set_update_order", "mvd_device_status", "mvd_set_wait_budget",
                  "mvd_reslice", "mvd_deconvolve_planes", "mvd_run_host", "mvd_psf_factors",
                  "mvd_profile_enable", "mvd_profile_read"):
         getattr(L, name).restype = ctypes.c_int
@@ -188,6 +190,17 @@ def mvd_set_algo(ctx: Context, algo: str) -> None:
 
 def mvd_set_update_order(ctx: Context, order: str) -> None:
     _check(lib().mvd_set_update_order(ctx.handle, ORDER[order]), "mvd_set_update_order")
+
+
+def mvd_device_status(ctx: Context, stream=None) -> None:
+    """Raise MvdError (MVD_ERR_TIMEOUT) if a kernel's bounded wait ran out."""
+    import torch
+    s = torch.cuda.current_stream().cuda_stream if stream is None else int(stream)
+    _check(lib().mvd_device_status(ctx.handle, ctypes.c_void_p(s)), "mvd_device_status")
+
+
+def mvd_set_wait_budget(ctx: Context, cycles: int) -> None:
+    _check(lib().mvd_set_wait_budget(ctx.handle, int(cycles)), "mvd_set_wait_budget")
 
 
 def mvd_set_rank_tolerance(ctx: Context, tol: float) -> None:

@@ -49,6 +49,7 @@ def run_gpu(mvd, phi, psfs, iters, boundary="zero", eps=1e-6, algo="fused", psi0
             est = torch.from_numpy(np.ascontiguousarray(psi0, dtype=np.float32)).to(DEV)
         mvd.mvd_deconvolve_planes(ctx, d, est, init_mean=psi0 is None)
         torch.cuda.synchronize()
+        mvd.mvd_device_status(ctx)
         return est.cpu().numpy()
     finally:
         ctx.close()
