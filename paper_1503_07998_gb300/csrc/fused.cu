@@ -57,6 +57,31 @@ __device__ __forceinline__ bool wait_tile(uint64_t *bar, uint32_t parity, const 
     return *abort_flag == 0;
 }
 
+// Where a kernel finds the factor taps: vertical taps of term tt at
+// base + tt * stride, the horizontal ones `hoff` floats later.
+struct TapSrc {
+    const float *base;
+    int stride;
+    int hoff;
+};
+
+// Copy kinds kind0 and kind0+1 (blur or correlation) of every term into
+// shared memory when they fit; else point into the global table.  The
+// caller synchronises before the taps are read.
+template <int K>
+__device__ __forceinline__ TapSrc stage_taps(float *taps_s, const FusedArgs &a, int kind0) {
+    const int n = a.ft.total_terms * 2 * K;
+    if (n * 4 <= kTapBytes) {
+        for (int i = threadIdx.x; i < n; i += kThreads) {
+            const int tt = i / (2 * K);
+            const int r = i - tt * 2 * K;
+            taps_s[i] = __ldg(a.taps + (tt * 4 + kind0) * K + r);
+        }
+        return {taps_s, 2 * K, K};
+    }
+    return {a.taps + kind0 * K, 4 * K, K};
+}
+
 __device__ __forceinline__ void load16_phi(const void *phi, int u16, long long off, bool vec, int n,
                                            float (&out)[kNC]) {
     if (u16) {
@@ -112,7 +137,8 @@ blur_ratio_kernel(const __grid_constant__ KParams kp) {
     extern __shared__ __align__(128) unsigned char smem[];
     uint64_t *bar = reinterpret_cast<uint64_t *>(smem);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(smem + 8);
-    float *tile = reinterpret_cast<float *>(smem + kHeaderBytes);
+    float *taps_s = reinterpret_cast<float *>(smem + kHeaderBytes);
+    float *tile = reinterpret_cast<float *>(smem + kTileOffset);
     float *stage = tile + G::BOX_H * G::BOX_W;
 
     const int p = blockIdx.z;
@@ -127,6 +153,7 @@ blur_ratio_kernel(const __grid_constant__ KParams kp) {
             tma::fence_barrier_init();
         }
     }
+    const TapSrc ts = stage_taps<K>(taps_s, a, 0);
     __syncthreads();
     if (use_tma) {
         if (threadIdx.x == 0) {
@@ -152,10 +179,10 @@ blur_ratio_kernel(const __grid_constant__ KParams kp) {
 #pragma unroll
             for (int j = 0; j < kNC; ++j) acc[h][j] = 0.0f;
         for (int q = 0; q < a.ft.rank[lead]; ++q) {
-            const float *tq = a.taps + static_cast<long long>(a.ft.tap_off[lead] + q) * 4 * K;
+            const float *tq = ts.base + (a.ft.tap_off[lead] + q) * ts.stride;
             vertical_pass<K>(tile, stage, tq);
             __syncthreads();
-            horizontal_pass<K>(stage, tq + K, acc);
+            horizontal_pass<K>(stage, tq + ts.hoff, acc);
             __syncthreads();
         }
         for (int v = a.view_lo; v < a.view_hi; ++v) {
@@ -188,7 +215,8 @@ correlate_update_kernel(const __grid_constant__ KParams kp) {
     extern __shared__ __align__(128) unsigned char smem[];
     uint64_t *bar = reinterpret_cast<uint64_t *>(smem);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(smem + 8);
-    float *tile = reinterpret_cast<float *>(smem + kHeaderBytes);
+    float *taps_s = reinterpret_cast<float *>(smem + kHeaderBytes);
+    float *tile = reinterpret_cast<float *>(smem + kTileOffset);
     float *stage = tile + G::BOX_H * G::BOX_W;
 
     const int p = blockIdx.z;
@@ -202,6 +230,7 @@ correlate_update_kernel(const __grid_constant__ KParams kp) {
             tma::fence_barrier_init();
         }
     }
+    const TapSrc ts = stage_taps<K>(taps_s, a, 2);
     __syncthreads();
 
     float prod[G::H_PER_THREAD][kNC];
@@ -231,10 +260,10 @@ correlate_update_kernel(const __grid_constant__ KParams kp) {
 #pragma unroll
             for (int j = 0; j < kNC; ++j) c[h][j] = 0.0f;
         for (int q = 0; q < a.ft.rank[v]; ++q) {
-            const float *tq = a.taps + static_cast<long long>(a.ft.tap_off[v] + q) * 4 * K;
-            vertical_pass<K>(tile, stage, tq + 2 * K);
+            const float *tq = ts.base + (a.ft.tap_off[v] + q) * ts.stride;
+            vertical_pass<K>(tile, stage, tq);
             __syncthreads();
-            horizontal_pass<K>(stage, tq + 3 * K, c);
+            horizontal_pass<K>(stage, tq + ts.hoff, c);
             __syncthreads();
         }
 #pragma unroll

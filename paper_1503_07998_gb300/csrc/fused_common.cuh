@@ -37,7 +37,11 @@ constexpr int kThreads = 256;
 constexpr int kNR = 16;      // rows per vertical item
 constexpr int kNC = 16;      // columns per horizontal item
 constexpr int kTX = 128;     // output tile width
-constexpr int kHeaderBytes = 128;   // mbarrier + abort flag, keeps the tile 128-byte aligned
+constexpr int kHeaderBytes = 128;   // mbarrier + abort flag
+constexpr int kTapBytes = 1536;     // the launch's factor taps when they fit (else read from global)
+constexpr int kTileOffset = kHeaderBytes + kTapBytes;   // a multiple of 128 for the TMA destination
+// Two CTAs per SM: 228 KB per SM minus 1 KB reserved per CTA.
+constexpr int kTwoCtaSmem = 113 * 1024;
 
 __host__ __device__ constexpr int round_up(int a, int b) { return (a + b - 1) / b * b; }
 
@@ -57,10 +61,10 @@ struct Geo {
     static constexpr int HL = round_up(kNC + 2 * R, 4);       // horizontal load width
     static constexpr int VB_LD = odd_quad_pitch((TX / kNC - 1) * kNC + HL);
     static constexpr int smem_bytes(int ty) {
-        return kHeaderBytes + ((ty + 2 * R) * BOX_W + ty * VB_LD) * 4;
+        return kTileOffset + ((ty + 2 * R) * BOX_W + ty * VB_LD) * 4;
     }
     // 64-row tiles while two CTAs still fit on an SM, else 32.
-    static constexpr int TY = (smem_bytes(64) <= 112 * 1024) ? 64 : 32;
+    static constexpr int TY = (smem_bytes(64) <= kTwoCtaSmem) ? 64 : 32;
     static constexpr int BOX_H = TY + 2 * R;
     static constexpr int SMEM_BYTES = smem_bytes(TY);
     static constexpr int TILE_BYTES = BOX_H * BOX_W * 4;
@@ -69,7 +73,7 @@ struct Geo {
     static constexpr int H_PER_THREAD = H_ITEMS / kThreads;
     static_assert(H_ITEMS % kThreads == 0, "horizontal items must tile the CTA");
     static_assert(BOX_W <= 256 && BOX_H <= 256, "TMA box dimensions are at most 256");
-    static constexpr int MIN_BLOCKS = (SMEM_BYTES <= 112 * 1024) ? 2 : 1;
+    static constexpr int MIN_BLOCKS = (SMEM_BYTES <= kTwoCtaSmem) ? 2 : 1;
 };
 
 // Software tile load (circular boundary, unaligned planes): same layout as
@@ -102,11 +106,11 @@ __device__ __forceinline__ void load_tile_sw(float *__restrict__ tile, const flo
 // output rows and IN_W columns.
 template <int K>
 __device__ __forceinline__ void vertical_pass(const float *__restrict__ tile, float *__restrict__ stage,
-                                              const float *__restrict__ taps_g) {
+                                              const float *__restrict__ taps_s) {
     using G = Geo<K>;
     float t[K];
 #pragma unroll
-    for (int m = 0; m < K; ++m) t[m] = __ldg(taps_g + m);
+    for (int m = 0; m < K; ++m) t[m] = taps_s[m];
     for (int it = threadIdx.x; it < G::V_ITEMS; it += kThreads) {
         const int rb = it / G::IN_W;
         const int c = it - rb * G::IN_W;
@@ -130,33 +134,37 @@ __device__ __forceinline__ void vertical_pass(const float *__restrict__ tile, fl
 }
 
 // Horizontal pass for this thread's items: acc[h][j] += sum_m t[m] * stage[row][16g + j + m].
+// Inputs stream through registers four at a time (one 16-byte load), each
+// feeding every output it reaches, so only the 16 accumulators, the taps
+// and one quad are live.
 template <int K>
 __device__ __forceinline__ void horizontal_pass(const float *__restrict__ stage,
-                                                const float *__restrict__ taps_g,
+                                                const float *__restrict__ taps_s,
                                                 float (&acc)[Geo<K>::H_PER_THREAD][kNC]) {
     using G = Geo<K>;
+    constexpr int NIN = kNC + K - 1;      // inputs actually used
     float t[K];
 #pragma unroll
-    for (int m = 0; m < K; ++m) t[m] = __ldg(taps_g + m);
+    for (int m = 0; m < K; ++m) t[m] = taps_s[m];
 #pragma unroll
     for (int h = 0; h < G::H_PER_THREAD; ++h) {
         const int it = threadIdx.x + h * kThreads;
         const int row = it % G::TY;
         const int g = it / G::TY;
         const float4 *src = reinterpret_cast<const float4 *>(stage + row * G::VB_LD + g * kNC);
-        float in[G::HL];
 #pragma unroll
-        for (int q = 0; q < G::HL / 4; ++q) {
+        for (int q = 0; q < (NIN + 3) / 4; ++q) {
             const float4 v = src[q];
-            in[4 * q + 0] = v.x;
-            in[4 * q + 1] = v.y;
-            in[4 * q + 2] = v.z;
-            in[4 * q + 3] = v.w;
-        }
+            const float x4[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
-        for (int j = 0; j < kNC; ++j) {
+            for (int e = 0; e < 4; ++e) {
+                const int i = 4 * q + e;          // input index
 #pragma unroll
-            for (int m = 0; m < K; ++m) acc[h][j] = fmaf(t[m], in[j + m], acc[h][j]);
+                for (int j = 0; j < kNC; ++j) {
+                    const int m = i - j;
+                    if (i < NIN && m >= 0 && m < K) acc[h][j] = fmaf(t[m], x4[e], acc[h][j]);
+                }
+            }
         }
     }
 }
