@@ -185,6 +185,36 @@ mvd_status mvd_device_status(mvd_ctx *ctx, void *stream);
  * its copy has landed, so the error path can be tested without a real one. */
 mvd_status mvd_set_wait_budget(mvd_ctx *ctx, long long cycles);
 
+/* Fused deconvolution that allocates no GPU memory.  The paper has no
+ * counterpart; this exists for callers that may not call cudaMalloc, such as
+ * acquisition software deconvolving while a camera records (an allocation can
+ * stall the device and has no latency bound) or a plug-in inside an
+ * application that owns every byte of the GPU's memory.  It takes the
+ * arguments of mvd_create and mvd_deconvolve_planes together, needs no
+ * context, and runs the fused path (simultaneous order, default rank
+ * tolerance) with all its scratch in one library-owned static device array
+ * of 32 MiB (status word, factor taps, per-plane means and the V ratio planes
+ * of every plane).  Every GPU that loads the library holds that array until
+ * the process exits.
+ *   - Limits: views <= 8, K odd and <= 47, and
+ *     256 + V*K*4*K*4 + 4*n_planes + 4*V*n_planes*H*W bytes (each part rounded
+ *     up to 256) must fit in 32 MiB; larger calls fail with MVD_ERR_ARG and a
+ *     message giving the bytes needed (split the planes over several calls).
+ *   - The first call on a device looks up the array's device address with
+ *     cudaGetSymbolAddress; make that first call before any stream capture.
+ *   - Every call shares the one array and reuses what the last call left
+ *     there; calls whose work overlaps on the GPU (other streams, other host
+ *     threads) race.  Serialise them.
+ *   - Device-side wait timeouts are not reported by this call.
+ * data_dev, estimate_dev, init_mean and stream mean what they mean for
+ * mvd_deconvolve_planes; the other arguments what they mean for mvd_create. */
+mvd_status mvd_deconvolve_planes_static(int views, const float *psfs_host, int psf_size,
+                                        int plane_h, int plane_w, int iters,
+                                        mvd_boundary boundary, float eps,
+                                        const void *data_dev, mvd_dtype dt,
+                                        float *estimate_dev, int n_planes, int init_mean,
+                                        void *stream);
+
 /* Per-kernel device time of this context's launches, taken with CUDA events
  * recorded on the launching stream around every kernel.  Enabling (on != 0)
  * or disabling clears what was collected.  mvd_profile_read waits for the

@@ -25,6 +25,12 @@ namespace {
 
 thread_local std::string t_last_error;
 
+}  // namespace
+
+void mvd::set_last_error(const char *msg) { t_last_error = msg ? msg : ""; }
+
+namespace {
+
 mvd_status fail(mvd_status s, const char *fmt, ...) {
     char buf[512];
     va_list ap;

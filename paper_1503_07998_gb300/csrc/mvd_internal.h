@@ -14,6 +14,9 @@ constexpr int kFusedMaxK = 47;   // largest PSF side with a fused-kernel instanc
 // Launch accounting (mvd_launch_count).
 void count_launch(int n = 1);
 
+// Sets the calling thread's mvd_last_error() text.
+void set_last_error(const char *msg);
+
 // Per-view separable factorisation of the PSFs, laid out on the device as
 //   taps[(tap_off[v] + q) * 4 * K + {0: blur vertical, 1: blur horizontal,
 //                                    2: corr vertical, 3: corr horizontal}*K + m]

@@ -67,6 +67,7 @@ def lib() -> ctypes.CDLL:
     L.mvd_set_rank_tolerance.argtypes = [vp, d]
     L.mvd_set_update_order.argtypes = [vp, i]
     L.mvd_device_status.argtypes = [vp, vp]
+    L.mvd_deconvolve_planes_static.argtypes = [i, vp, i, i, i, i, i, f, vp, i, vp, i, i, vp]
     L.mvd_set_wait_budget.argtypes = [vp, ctypes.c_longlong]
     L.mvd_get_info.argtypes = [vp, ctypes.POINTER(_Info)]
     L.mvd_reslice.argtypes = [vp, vp, i, i, i, i, i, vp, vp]
@@ -83,6 +84,7 @@ def lib() -> ctypes.CDLL:
     L.mvd_launch_count.restype = ctypes.c_uint64
     for name in ("mvd_create", "mvd_destroy", "mvd_set_algo", "mvd_set_rank_tolerance", "mvd_get_info",
                  "mvd_set_update_order", "mvd_device_status", "mvd_set_wait_budget",
+                 "mvd_deconvolve_planes_static",
                  "mvd_reslice", "mvd_deconvolve_planes", "mvd_run_host", "mvd_psf_factors",
                  "mvd_profile_enable", "mvd_profile_read"):
         getattr(L, name).restype = ctypes.c_int
@@ -237,6 +239,28 @@ def mvd_deconvolve_planes(ctx: Context, data, estimate, init_mean: bool = True, 
     _check(lib().mvd_deconvolve_planes(ctx.handle, ctypes.c_void_p(data.data_ptr()), _dtype_code(data),
                                        ctypes.c_void_p(estimate.data_ptr()), P, int(bool(init_mean)),
                                        _stream_of(data, stream)), "mvd_deconvolve_planes")
+
+
+def mvd_deconvolve_planes_static(psfs, data, estimate, iters: int, boundary: str = "zero", eps: float = 1e-6,
+                                 init_mean: bool = True, stream=None) -> None:
+    """Context-free fused deconvolution that allocates no GPU memory, for
+    callers that may not call cudaMalloc (see include/mvd.h): its scratch is
+    a 32 MiB static device array shared by all calls, so calls must not
+    overlap on the GPU.  data [V][P][H][W] uint16/float32 and estimate
+    [P][H][W] float32 are CUDA tensors; psfs [V][K][K] is host data."""
+    import torch
+    _require_cuda(data, estimate)
+    V, P, H, W = data.shape
+    p = np.ascontiguousarray(np.asarray(psfs, dtype=np.float32))
+    if p.ndim != 3 or p.shape[0] != V or p.shape[1] != p.shape[2]:
+        raise ValueError("psfs must be [V][K][K]")
+    if tuple(estimate.shape) != (P, H, W) or estimate.dtype != torch.float32:
+        raise ValueError("estimate must be float32 [P][H][W]")
+    _check(lib().mvd_deconvolve_planes_static(V, p.ctypes.data_as(ctypes.c_void_p), p.shape[1], H, W, int(iters),
+                                              BOUNDARY[boundary], float(eps), ctypes.c_void_p(data.data_ptr()),
+                                              _dtype_code(data), ctypes.c_void_p(estimate.data_ptr()), P,
+                                              int(bool(init_mean)), _stream_of(data, stream)),
+           "mvd_deconvolve_planes_static")
 
 
 def mvd_run_host(ctx: Context, stacks_host, out_host, chunk_planes: int = 0, stream=None) -> None:
