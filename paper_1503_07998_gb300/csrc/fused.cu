@@ -4,7 +4,8 @@
 //   blur_ratio        r_v = phi_v / max(psi * P_v, eps)   for every view v
 //   correlate_update  psi <- psi * prod_v (r_v (*) P_v^*)
 //
-// A CTA owns a TY x 128 output tile of one plane.  Kernel A stages the psi
+// A CTA works on TY x 128 output tiles of the planes, one after another
+// (persistent grid, one resident wave).  Kernel A stages the psi
 // tile (halo R) once for all views; views whose PSFs are identical share
 // one blur.  Kernel B stages each view's ratio tile with its halo, keeps the
 // running product of the views' corrections in registers and updates psi in
@@ -129,6 +130,26 @@ __device__ __forceinline__ void store16(float *dst, bool vec, int n, const float
     }
 }
 
+// Tile t of a launch: plane p, output origin (y0, x0); x fastest so that the
+// CTAs working at the same time share halo rows in L2.
+struct TileCoord {
+    int p, y0, x0;
+};
+
+template <int K>
+__device__ __forceinline__ TileCoord tile_coord(int t, int tiles_x, int tiles_y) {
+    using G = Geo<K>;
+    const int per_plane = tiles_x * tiles_y;
+    const int p = t / per_plane;
+    const int r = t - p * per_plane;
+    const int ty = r / tiles_x;
+    return {p, ty * G::TY, (r - ty * tiles_x) * G::TX};
+}
+
+// Persistent: each CTA walks tiles blockIdx.x, blockIdx.x + gridDim.x, ...
+// With TMA, the next tile's psi box is requested right after the last
+// vertical pass of the current tile (the input tile is free from then on),
+// so the copy overlaps the last horizontal pass and the epilogue.
 template <int K>
 __global__ void __launch_bounds__(kThreads, Geo<K>::MIN_BLOCKS)
 blur_ratio_kernel(const __grid_constant__ KParams kp) {
@@ -141,11 +162,20 @@ blur_ratio_kernel(const __grid_constant__ KParams kp) {
     float *tile = reinterpret_cast<float *>(smem + kTileOffset);
     float *stage = tile + G::BOX_H * G::BOX_W;
 
-    const int p = blockIdx.z;
-    const int y0 = blockIdx.y * G::TY;
-    const int x0 = blockIdx.x * G::TX;
+    const int tiles_x = (a.W + G::TX - 1) / G::TX;
+    const int tiles_y = (a.H + G::TY - 1) / G::TY;
+    const int n_tiles = tiles_x * tiles_y * a.P;
     const long long plane_px = static_cast<long long>(a.H) * a.W;
     const bool use_tma = kp.use_tma && a.psi_in != nullptr;
+
+    // vertical passes per tile: one per SVD term of every blur group in use
+    int passes = 0;
+    for (int g = 0; g < a.ft.n_groups; ++g) {
+        bool used = false;
+        for (int v = a.view_lo; v < a.view_hi; ++v) used |= (a.ft.group[v] == g);
+        if (used) passes += a.ft.rank[a.ft.group_leader[g]];
+    }
+
     if (threadIdx.x == 0) {
         *abort_flag = 0;
         if (use_tma) {
@@ -155,58 +185,75 @@ blur_ratio_kernel(const __grid_constant__ KParams kp) {
     }
     const TapSrc ts = stage_taps<K>(taps_s, a, 0);
     __syncthreads();
-    if (use_tma) {
-        if (threadIdx.x == 0) {
-            tma::mbar_arrive_expect_tx(bar, G::TILE_BYTES);
-            tma::load_3d(tile, &kp.map, bar, x0 - G::R4, y0 - G::R, p);
-        }
-        if (!wait_tile(bar, 0, a, abort_flag)) return;
-    } else {
-        const float *psi = a.psi_in ? a.psi_in + p * plane_px : nullptr;
-        const float fill = a.psi_in ? 0.0f : __ldg(a.means + p);
-        load_tile_sw<K>(tile, psi, fill, y0, x0, a.H, a.W, a.circular);
-        __syncthreads();
+    int t = blockIdx.x;
+    if (use_tma && threadIdx.x == 0 && t < n_tiles) {
+        const TileCoord c = tile_coord<K>(t, tiles_x, tiles_y);
+        tma::mbar_arrive_expect_tx(bar, G::TILE_BYTES);
+        tma::load_3d(tile, &kp.map, bar, c.x0 - G::R4, c.y0 - G::R, c.p);
     }
-
-    for (int g = 0; g < a.ft.n_groups; ++g) {
-        bool used = false;
-        for (int v = a.view_lo; v < a.view_hi; ++v) used |= (a.ft.group[v] == g);
-        if (!used) continue;
-        const int lead = a.ft.group_leader[g];
-        float acc[G::H_PER_THREAD][kNC];
-#pragma unroll
-        for (int h = 0; h < G::H_PER_THREAD; ++h)
-#pragma unroll
-            for (int j = 0; j < kNC; ++j) acc[h][j] = 0.0f;
-        for (int q = 0; q < a.ft.rank[lead]; ++q) {
-            const float *tq = ts.base + (a.ft.tap_off[lead] + q) * ts.stride;
-            vertical_pass<K>(tile, stage, tq);
-            __syncthreads();
-            horizontal_pass<K>(stage, tq + ts.hoff, acc);
+    uint32_t phase = 0;
+    for (; t < n_tiles; t += gridDim.x) {
+        const TileCoord tc = tile_coord<K>(t, tiles_x, tiles_y);
+        const int p = tc.p, y0 = tc.y0, x0 = tc.x0;
+        if (use_tma) {
+            if (!wait_tile(bar, phase, a, abort_flag)) return;
+            phase ^= 1u;
+        } else {
+            const float *psi = a.psi_in ? a.psi_in + p * plane_px : nullptr;
+            const float fill = a.psi_in ? 0.0f : __ldg(a.means + p);
+            load_tile_sw<K>(tile, psi, fill, y0, x0, a.H, a.W, a.circular);
             __syncthreads();
         }
-        for (int v = a.view_lo; v < a.view_hi; ++v) {
-            if (a.ft.group[v] != g) continue;
-            const long long vplane = (static_cast<long long>(v) * a.P + p) * plane_px;
+        const int t_next = t + gridDim.x;
+        int left = passes;
+        for (int g = 0; g < a.ft.n_groups; ++g) {
+            bool used = false;
+            for (int v = a.view_lo; v < a.view_hi; ++v) used |= (a.ft.group[v] == g);
+            if (!used) continue;
+            const int lead = a.ft.group_leader[g];
+            float acc[G::H_PER_THREAD][kNC];
 #pragma unroll
-            for (int h = 0; h < G::H_PER_THREAD; ++h) {
-                int y, x;
-                item_origin<K>(h, y0, x0, y, x);
-                if (y >= a.H || x >= a.W) continue;
-                const int n = min(kNC, a.W - x);
-                const bool vec = kp.vec_ok && n == kNC;
-                const long long off = vplane + static_cast<long long>(y) * a.W + x;
-                float phi[kNC];
-                load16_phi(a.phi, a.phi_u16, off, vec, n, phi);
-                float r[kNC];
+            for (int h = 0; h < G::H_PER_THREAD; ++h)
 #pragma unroll
-                for (int j = 0; j < kNC; ++j) r[j] = __fdividef(phi[j], fmaxf(acc[h][j], a.eps));
-                store16(a.ratio + off, vec, n, r);
+                for (int j = 0; j < kNC; ++j) acc[h][j] = 0.0f;
+            for (int q = 0; q < a.ft.rank[lead]; ++q) {
+                const float *tq = ts.base + (a.ft.tap_off[lead] + q) * ts.stride;
+                vertical_pass<K>(tile, stage, tq);
+                __syncthreads();
+                if (--left == 0 && use_tma && threadIdx.x == 0 && t_next < n_tiles) {
+                    const TileCoord c = tile_coord<K>(t_next, tiles_x, tiles_y);
+                    tma::fence_proxy_async_smem();
+                    tma::mbar_arrive_expect_tx(bar, G::TILE_BYTES);
+                    tma::load_3d(tile, &kp.map, bar, c.x0 - G::R4, c.y0 - G::R, c.p);
+                }
+                horizontal_pass<K>(stage, tq + ts.hoff, acc);
+                __syncthreads();
+            }
+            for (int v = a.view_lo; v < a.view_hi; ++v) {
+                if (a.ft.group[v] != g) continue;
+                const long long vplane = (static_cast<long long>(v) * a.P + p) * plane_px;
+#pragma unroll
+                for (int h = 0; h < G::H_PER_THREAD; ++h) {
+                    int y, x;
+                    item_origin<K>(h, y0, x0, y, x);
+                    if (y >= a.H || x >= a.W) continue;
+                    const int n = min(kNC, a.W - x);
+                    const bool vec = kp.vec_ok && n == kNC;
+                    const long long off = vplane + static_cast<long long>(y) * a.W + x;
+                    float phi[kNC];
+                    load16_phi(a.phi, a.phi_u16, off, vec, n, phi);
+                    float r[kNC];
+#pragma unroll
+                    for (int j = 0; j < kNC; ++j) r[j] = __fdividef(phi[j], fmaxf(acc[h][j], a.eps));
+                    store16(a.ratio + off, vec, n, r);
+                }
             }
         }
     }
 }
 
+// Persistent like kernel A.  The ratio box of the next (tile, view) is
+// requested right after the last vertical pass of the current view.
 template <int K>
 __global__ void __launch_bounds__(kThreads, Geo<K>::MIN_BLOCKS)
 correlate_update_kernel(const __grid_constant__ KParams kp) {
@@ -219,79 +266,99 @@ correlate_update_kernel(const __grid_constant__ KParams kp) {
     float *tile = reinterpret_cast<float *>(smem + kTileOffset);
     float *stage = tile + G::BOX_H * G::BOX_W;
 
-    const int p = blockIdx.z;
-    const int y0 = blockIdx.y * G::TY;
-    const int x0 = blockIdx.x * G::TX;
+    const int tiles_x = (a.W + G::TX - 1) / G::TX;
+    const int tiles_y = (a.H + G::TY - 1) / G::TY;
+    const int n_tiles = tiles_x * tiles_y * a.P;
     const long long plane_px = static_cast<long long>(a.H) * a.W;
+    const bool use_tma = kp.use_tma;
     if (threadIdx.x == 0) {
         *abort_flag = 0;
-        if (kp.use_tma) {
+        if (use_tma) {
             tma::mbar_init(bar, 1);
             tma::fence_barrier_init();
         }
     }
     const TapSrc ts = stage_taps<K>(taps_s, a, 2);
     __syncthreads();
-
-    float prod[G::H_PER_THREAD][kNC];
-#pragma unroll
-    for (int h = 0; h < G::H_PER_THREAD; ++h)
-#pragma unroll
-        for (int j = 0; j < kNC; ++j) prod[h][j] = 1.0f;
-
-    uint32_t phase = 0;
-    for (int v = a.view_lo; v < a.view_hi; ++v) {
-        if (kp.use_tma) {
-            if (threadIdx.x == 0) {
-                tma::fence_proxy_async_smem();
-                tma::mbar_arrive_expect_tx(bar, G::TILE_BYTES);
-                tma::load_3d(tile, &kp.map, bar, x0 - G::R4, y0 - G::R, v * a.P + p);
-            }
-            if (!wait_tile(bar, phase, a, abort_flag)) return;
-            phase ^= 1u;
-        } else {
-            const float *rsrc = a.ratio + (static_cast<long long>(v) * a.P + p) * plane_px;
-            load_tile_sw<K>(tile, rsrc, 0.0f, y0, x0, a.H, a.W, a.circular);
-            __syncthreads();
-        }
-        float c[G::H_PER_THREAD][kNC];
-#pragma unroll
-        for (int h = 0; h < G::H_PER_THREAD; ++h)
-#pragma unroll
-            for (int j = 0; j < kNC; ++j) c[h][j] = 0.0f;
-        for (int q = 0; q < a.ft.rank[v]; ++q) {
-            const float *tq = ts.base + (a.ft.tap_off[v] + q) * ts.stride;
-            vertical_pass<K>(tile, stage, tq);
-            __syncthreads();
-            horizontal_pass<K>(stage, tq + ts.hoff, c);
-            __syncthreads();
-        }
-#pragma unroll
-        for (int h = 0; h < G::H_PER_THREAD; ++h)
-#pragma unroll
-            for (int j = 0; j < kNC; ++j) prod[h][j] *= c[h][j];
+    int t = blockIdx.x;
+    if (use_tma && threadIdx.x == 0 && t < n_tiles) {
+        const TileCoord c = tile_coord<K>(t, tiles_x, tiles_y);
+        tma::mbar_arrive_expect_tx(bar, G::TILE_BYTES);
+        tma::load_3d(tile, &kp.map, bar, c.x0 - G::R4, c.y0 - G::R, a.view_lo * a.P + c.p);
     }
+    uint32_t phase = 0;
+    for (; t < n_tiles; t += gridDim.x) {
+        const TileCoord tc = tile_coord<K>(t, tiles_x, tiles_y);
+        const int p = tc.p, y0 = tc.y0, x0 = tc.x0;
+        const int t_next = t + gridDim.x;
+        float prod[G::H_PER_THREAD][kNC];
+#pragma unroll
+        for (int h = 0; h < G::H_PER_THREAD; ++h)
+#pragma unroll
+            for (int j = 0; j < kNC; ++j) prod[h][j] = 1.0f;
 
-    const float mean = a.psi_in ? 0.0f : __ldg(a.means + p);
+        for (int v = a.view_lo; v < a.view_hi; ++v) {
+            if (use_tma) {
+                if (!wait_tile(bar, phase, a, abort_flag)) return;
+                phase ^= 1u;
+            } else {
+                const float *rsrc = a.ratio + (static_cast<long long>(v) * a.P + p) * plane_px;
+                load_tile_sw<K>(tile, rsrc, 0.0f, y0, x0, a.H, a.W, a.circular);
+                __syncthreads();
+            }
+            float c[G::H_PER_THREAD][kNC];
 #pragma unroll
-    for (int h = 0; h < G::H_PER_THREAD; ++h) {
-        int y, x;
-        item_origin<K>(h, y0, x0, y, x);
-        if (y >= a.H || x >= a.W) continue;
-        const int n = min(kNC, a.W - x);
-        const bool vec = kp.vec_ok && n == kNC;
-        const long long off = p * plane_px + static_cast<long long>(y) * a.W + x;
-        float old[kNC];
-        if (a.psi_in) {
-            load16_phi(a.psi_in, 0, off, vec, n, old);
-        } else {
+            for (int h = 0; h < G::H_PER_THREAD; ++h)
 #pragma unroll
-            for (int j = 0; j < kNC; ++j) old[j] = mean;
+                for (int j = 0; j < kNC; ++j) c[h][j] = 0.0f;
+            for (int q = 0; q < a.ft.rank[v]; ++q) {
+                const float *tq = ts.base + (a.ft.tap_off[v] + q) * ts.stride;
+                vertical_pass<K>(tile, stage, tq);
+                __syncthreads();
+                if (q == a.ft.rank[v] - 1 && use_tma && threadIdx.x == 0) {
+                    // next box: the next view of this tile, else the first view of the next tile
+                    int nt = t, nv = v + 1;
+                    if (nv >= a.view_hi) {
+                        nt = t_next;
+                        nv = a.view_lo;
+                    }
+                    if (nt < n_tiles) {
+                        const TileCoord c2 = tile_coord<K>(nt, tiles_x, tiles_y);
+                        tma::fence_proxy_async_smem();
+                        tma::mbar_arrive_expect_tx(bar, G::TILE_BYTES);
+                        tma::load_3d(tile, &kp.map, bar, c2.x0 - G::R4, c2.y0 - G::R, nv * a.P + c2.p);
+                    }
+                }
+                horizontal_pass<K>(stage, tq + ts.hoff, c);
+                __syncthreads();
+            }
+#pragma unroll
+            for (int h = 0; h < G::H_PER_THREAD; ++h)
+#pragma unroll
+                for (int j = 0; j < kNC; ++j) prod[h][j] *= c[h][j];
         }
-        float out[kNC];
+
+        const float mean = a.psi_in ? 0.0f : __ldg(a.means + p);
 #pragma unroll
-        for (int j = 0; j < kNC; ++j) out[j] = old[j] * prod[h][j];
-        store16(a.psi_out + off, vec, n, out);
+        for (int h = 0; h < G::H_PER_THREAD; ++h) {
+            int y, x;
+            item_origin<K>(h, y0, x0, y, x);
+            if (y >= a.H || x >= a.W) continue;
+            const int n = min(kNC, a.W - x);
+            const bool vec = kp.vec_ok && n == kNC;
+            const long long off = p * plane_px + static_cast<long long>(y) * a.W + x;
+            float old[kNC];
+            if (a.psi_in) {
+                load16_phi(a.psi_in, 0, off, vec, n, old);
+            } else {
+#pragma unroll
+                for (int j = 0; j < kNC; ++j) old[j] = mean;
+            }
+            float out[kNC];
+#pragma unroll
+            for (int j = 0; j < kNC; ++j) out[j] = old[j] * prod[h][j];
+            store16(a.psi_out + off, vec, n, out);
+        }
     }
 }
 
@@ -344,7 +411,21 @@ cudaError_t launch_pair(const FusedArgs &a, int which, cudaStream_t s) {
         if (e != cudaSuccess) return e;
         attr_set |= bit;
     }
-    const dim3 grid((a.W + G::TX - 1) / G::TX, (a.H + G::TY - 1) / G::TY, a.P);
+    // persistent grid: as many CTAs as fit on the device at once, at most one per tile
+    static int resident[64][2] = {};
+    if (!resident[dev & 63][which]) {
+        int sms = 0, per_sm = 0;
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (which == 0)
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, blur_ratio_kernel<K>, kThreads, G::SMEM_BYTES);
+        else
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, correlate_update_kernel<K>, kThreads,
+                                                          G::SMEM_BYTES);
+        resident[dev & 63][which] = (sms > 0 ? sms : 1) * (per_sm > 0 ? per_sm : 1);
+    }
+    const long long n_tiles = static_cast<long long>((a.W + G::TX - 1) / G::TX) * ((a.H + G::TY - 1) / G::TY) * a.P;
+    if (n_tiles > 0x7fffffffLL) return cudaErrorInvalidValue;
+    const dim3 grid(static_cast<unsigned>(n_tiles < resident[dev & 63][which] ? n_tiles : resident[dev & 63][which]));
     KParams kp;
     std::memset(&kp, 0, sizeof kp);
     kp.a = a;

@@ -102,34 +102,52 @@ __device__ __forceinline__ void load_tile_sw(float *__restrict__ tile, const flo
     }
 }
 
+// One vertical item: NR consecutive output rows r0.. of column c.
+template <int K, int NR>
+__device__ __forceinline__ void vertical_item(const float *__restrict__ tile, float *__restrict__ stage,
+                                              const float (&t)[K], int c, int r0) {
+    using G = Geo<K>;
+    const float *col = tile + r0 * G::BOX_W + G::COL0 + c;
+    float acc[NR];
+#pragma unroll
+    for (int i = 0; i < NR; ++i) acc[i] = 0.0f;
+#pragma unroll
+    for (int m = 0; m < NR + K - 1; ++m) {
+        const float x = col[m * G::BOX_W];
+#pragma unroll
+        for (int i = 0; i < NR; ++i) {
+            const int j = m - i;
+            if (j >= 0 && j < K) acc[i] = fmaf(t[j], x, acc[i]);
+        }
+    }
+    float *dst = stage + r0 * G::VB_LD + c;
+#pragma unroll
+    for (int i = 0; i < NR; ++i) dst[i * G::VB_LD] = acc[i];
+}
+
 // Vertical pass: stage[i][c] = sum_m t[m] * tile[i + m][COL0 + c] for the TY
-// output rows and IN_W columns.
+// output rows and IN_W columns.  The TX columns under the output tile run as
+// 16-row items (TX*TY/16 = a whole number of rounds of the CTA), the 2R halo
+// columns as 8-row items (one more round), so that no warp idles for long
+// at the barrier that follows.
 template <int K>
 __device__ __forceinline__ void vertical_pass(const float *__restrict__ tile, float *__restrict__ stage,
                                               const float *__restrict__ taps_s) {
     using G = Geo<K>;
+    static_assert((G::TX * (G::TY / kNR)) % kThreads == 0, "main vertical items must tile the CTA");
     float t[K];
 #pragma unroll
     for (int m = 0; m < K; ++m) t[m] = taps_s[m];
-    for (int it = threadIdx.x; it < G::V_ITEMS; it += kThreads) {
-        const int rb = it / G::IN_W;
-        const int c = it - rb * G::IN_W;
-        const float *col = tile + rb * kNR * G::BOX_W + G::COL0 + c;
-        float acc[kNR];
-#pragma unroll
-        for (int i = 0; i < kNR; ++i) acc[i] = 0.0f;
-#pragma unroll
-        for (int m = 0; m < kNR + K - 1; ++m) {
-            const float x = col[m * G::BOX_W];
-#pragma unroll
-            for (int i = 0; i < kNR; ++i) {
-                const int j = m - i;
-                if (j >= 0 && j < K) acc[i] = fmaf(t[j], x, acc[i]);
-            }
+    for (int it = threadIdx.x; it < G::TX * (G::TY / kNR); it += kThreads) {
+        const int rb = it / G::TX;
+        vertical_item<K, kNR>(tile, stage, t, it - rb * G::TX, rb * kNR);
+    }
+    if (G::R > 0) {
+        constexpr int HC = 2 * G::R;             // halo columns TX .. TX+2R-1
+        for (int it = threadIdx.x; it < HC * (G::TY / 8); it += kThreads) {
+            const int r8 = it / HC;
+            vertical_item<K, 8>(tile, stage, t, G::TX + (it - r8 * HC), r8 * 8);
         }
-        float *dst = stage + rb * kNR * G::VB_LD + c;
-#pragma unroll
-        for (int i = 0; i < kNR; ++i) dst[i * G::VB_LD] = acc[i];
     }
 }
 
