@@ -83,50 +83,91 @@ __device__ __forceinline__ TapSrc stage_taps(float *taps_s, const FusedArgs &a, 
     return {a.taps + kind0 * K, 4 * K, K};
 }
 
-__device__ __forceinline__ void load16_phi(const void *phi, int u16, long long off, bool vec, int n,
-                                           float (&out)[kNC]) {
+// Four consecutive values of one row: uint16 or FP32 source.
+__device__ __forceinline__ void load4(const void *src, int u16, long long off, bool vec, int n, float (&o)[4]) {
     if (u16) {
-        const uint16_t *p = static_cast<const uint16_t *>(phi) + off;
+        const uint16_t *p = static_cast<const uint16_t *>(src) + off;
         if (vec) {
-            const uint4 a = __ldg(reinterpret_cast<const uint4 *>(p));
-            const uint4 b = __ldg(reinterpret_cast<const uint4 *>(p) + 1);
-            const unsigned w[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
-#pragma unroll
-            for (int k = 0; k < 8; ++k) {
-                out[2 * k] = static_cast<float>(w[k] & 0xffffu);
-                out[2 * k + 1] = static_cast<float>(w[k] >> 16);
-            }
+            const uint2 w = __ldg(reinterpret_cast<const uint2 *>(p));
+            o[0] = static_cast<float>(w.x & 0xffffu);
+            o[1] = static_cast<float>(w.x >> 16);
+            o[2] = static_cast<float>(w.y & 0xffffu);
+            o[3] = static_cast<float>(w.y >> 16);
         } else {
 #pragma unroll
-            for (int j = 0; j < kNC; ++j) out[j] = j < n ? static_cast<float>(p[j]) : 0.0f;
+            for (int j = 0; j < 4; ++j) o[j] = j < n ? static_cast<float>(p[j]) : 0.0f;
         }
     } else {
-        const float *p = static_cast<const float *>(phi) + off;
+        const float *p = static_cast<const float *>(src) + off;
         if (vec) {
-#pragma unroll
-            for (int q = 0; q < kNC / 4; ++q) {
-                const float4 a = __ldg(reinterpret_cast<const float4 *>(p) + q);
-                out[4 * q + 0] = a.x;
-                out[4 * q + 1] = a.y;
-                out[4 * q + 2] = a.z;
-                out[4 * q + 3] = a.w;
-            }
+            const float4 w = __ldg(reinterpret_cast<const float4 *>(p));
+            o[0] = w.x;
+            o[1] = w.y;
+            o[2] = w.z;
+            o[3] = w.w;
         } else {
 #pragma unroll
-            for (int j = 0; j < kNC; ++j) out[j] = j < n ? __ldg(p + j) : 0.0f;
+            for (int j = 0; j < 4; ++j) o[j] = j < n ? __ldg(p + j) : 0.0f;
         }
     }
 }
 
-__device__ __forceinline__ void store16(float *dst, bool vec, int n, const float (&v)[kNC]) {
+__device__ __forceinline__ void store4(float *dst, bool vec, int n, const float (&v)[4]) {
     if (vec) {
-#pragma unroll
-        for (int q = 0; q < kNC / 4; ++q)
-            reinterpret_cast<float4 *>(dst)[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+        *reinterpret_cast<float4 *>(dst) = make_float4(v[0], v[1], v[2], v[3]);
     } else {
 #pragma unroll
-        for (int j = 0; j < kNC; ++j)
+        for (int j = 0; j < 4; ++j)
             if (j < n) dst[j] = v[j];
+    }
+}
+
+// Row-wise epilogue over the TY x TX output tile held in the staging tile.
+// Warp w takes rows w, w+8, ...; lane l takes columns 4l .. 4l+3, so every
+// warp reads and writes whole contiguous 512-byte row segments, and all of a
+// warp's loads are issued before its stores.
+//   MODE 0 (ratio):  ratio = phi / max(stage, eps)   (base: plane of view v)
+//   MODE 1 (update): psi_out = psi_in * stage, or mean * stage on the first
+//                    iteration                         (base: plane p)
+template <int K, int MODE>
+__device__ __forceinline__ void row_epilogue(const FusedArgs &a, int vec_ok, const float *__restrict__ stage,
+                                             long long base, int y0, int x0, float mean) {
+    using G = Geo<K>;
+    constexpr int WARPS = kThreads / 32;
+    constexpr int ROWS = G::TY / WARPS;
+    static_assert(G::TX == 4 * 32, "one warp covers one tile row");
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int x = x0 + 4 * lane;
+    const int n = min(4, a.W - x);
+    if (n <= 0) return;
+    const bool vec = vec_ok && n == 4;
+    float in[ROWS][4];
+#pragma unroll
+    for (int k = 0; k < ROWS; ++k) {
+        const int y = y0 + warp + k * WARPS;
+        if (y >= a.H) continue;
+        const long long off = base + static_cast<long long>(y) * a.W + x;
+        if (MODE == 0) {
+            load4(a.phi, a.phi_u16, off, vec, n, in[k]);
+        } else if (a.psi_in) {
+            load4(a.psi_in, 0, off, vec, n, in[k]);
+        } else {
+#pragma unroll
+            for (int j = 0; j < 4; ++j) in[k][j] = mean;
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < ROWS; ++k) {
+        const int row = warp + k * WARPS;
+        const int y = y0 + row;
+        if (y >= a.H) continue;
+        const float4 s4 = *reinterpret_cast<const float4 *>(stage + row * G::VB_LD + 4 * lane);
+        const float s[4] = {s4.x, s4.y, s4.z, s4.w};
+        float o[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) o[j] = MODE == 0 ? __fdividef(in[k][j], fmaxf(s[j], a.eps)) : in[k][j] * s[j];
+        float *dst = (MODE == 0 ? a.ratio : a.psi_out) + base + static_cast<long long>(y) * a.W + x;
+        store4(dst, vec, n, o);
     }
 }
 
@@ -229,25 +270,16 @@ blur_ratio_kernel(const __grid_constant__ KParams kp) {
                 horizontal_pass<K>(stage, tq + ts.hoff, acc);
                 __syncthreads();
             }
+            // ratio epilogue, row by row: every warp loads phi and stores r as
+            // whole contiguous row segments of the tile
+            park_items<K>(stage, acc);
+            __syncthreads();
             for (int v = a.view_lo; v < a.view_hi; ++v) {
                 if (a.ft.group[v] != g) continue;
                 const long long vplane = (static_cast<long long>(v) * a.P + p) * plane_px;
-#pragma unroll
-                for (int h = 0; h < G::H_PER_THREAD; ++h) {
-                    int y, x;
-                    item_origin<K>(h, y0, x0, y, x);
-                    if (y >= a.H || x >= a.W) continue;
-                    const int n = min(kNC, a.W - x);
-                    const bool vec = kp.vec_ok && n == kNC;
-                    const long long off = vplane + static_cast<long long>(y) * a.W + x;
-                    float phi[kNC];
-                    load16_phi(a.phi, a.phi_u16, off, vec, n, phi);
-                    float r[kNC];
-#pragma unroll
-                    for (int j = 0; j < kNC; ++j) r[j] = __fdividef(phi[j], fmaxf(acc[h][j], a.eps));
-                    store16(a.ratio + off, vec, n, r);
-                }
+                row_epilogue<K, 0>(a, kp.vec_ok, stage, vplane, y0, x0, 0.0f);
             }
+            __syncthreads();   // the staging tile is rewritten by the next pass
         }
     }
 }
@@ -306,59 +338,55 @@ correlate_update_kernel(const __grid_constant__ KParams kp) {
                 load_tile_sw<K>(tile, rsrc, 0.0f, y0, x0, a.H, a.W, a.circular);
                 __syncthreads();
             }
-            float c[G::H_PER_THREAD][kNC];
-#pragma unroll
-            for (int h = 0; h < G::H_PER_THREAD; ++h)
-#pragma unroll
-                for (int j = 0; j < kNC; ++j) c[h][j] = 0.0f;
-            for (int q = 0; q < a.ft.rank[v]; ++q) {
-                const float *tq = ts.base + (a.ft.tap_off[v] + q) * ts.stride;
+            // the ratio box of the next (tile, view), requested once the tile is free
+            auto prefetch_next = [&]() {
+                if (!use_tma || threadIdx.x != 0) return;
+                int nt = t, nv = v + 1;
+                if (nv >= a.view_hi) {
+                    nt = t_next;
+                    nv = a.view_lo;
+                }
+                if (nt < n_tiles) {
+                    const TileCoord c2 = tile_coord<K>(nt, tiles_x, tiles_y);
+                    tma::fence_proxy_async_smem();
+                    tma::mbar_arrive_expect_tx(bar, G::TILE_BYTES);
+                    tma::load_3d(tile, &kp.map, bar, c2.x0 - G::R4, c2.y0 - G::R, nv * a.P + c2.p);
+                }
+            };
+            if (a.ft.rank[v] == 1) {
+                const float *tq = ts.base + a.ft.tap_off[v] * ts.stride;
                 vertical_pass<K>(tile, stage, tq);
                 __syncthreads();
-                if (q == a.ft.rank[v] - 1 && use_tma && threadIdx.x == 0) {
-                    // next box: the next view of this tile, else the first view of the next tile
-                    int nt = t, nv = v + 1;
-                    if (nv >= a.view_hi) {
-                        nt = t_next;
-                        nv = a.view_lo;
-                    }
-                    if (nt < n_tiles) {
-                        const TileCoord c2 = tile_coord<K>(nt, tiles_x, tiles_y);
-                        tma::fence_proxy_async_smem();
-                        tma::mbar_arrive_expect_tx(bar, G::TILE_BYTES);
-                        tma::load_3d(tile, &kp.map, bar, c2.x0 - G::R4, c2.y0 - G::R, nv * a.P + c2.p);
-                    }
-                }
-                horizontal_pass<K>(stage, tq + ts.hoff, c);
+                prefetch_next();
+                horizontal_pass_mul<K>(stage, tq + ts.hoff, prod);
                 __syncthreads();
+            } else {
+                float c[G::H_PER_THREAD][kNC];
+#pragma unroll
+                for (int h = 0; h < G::H_PER_THREAD; ++h)
+#pragma unroll
+                    for (int j = 0; j < kNC; ++j) c[h][j] = 0.0f;
+                for (int q = 0; q < a.ft.rank[v]; ++q) {
+                    const float *tq = ts.base + (a.ft.tap_off[v] + q) * ts.stride;
+                    vertical_pass<K>(tile, stage, tq);
+                    __syncthreads();
+                    if (q == a.ft.rank[v] - 1) prefetch_next();
+                    horizontal_pass<K>(stage, tq + ts.hoff, c);
+                    __syncthreads();
+                }
+#pragma unroll
+                for (int h = 0; h < G::H_PER_THREAD; ++h)
+#pragma unroll
+                    for (int j = 0; j < kNC; ++j) prod[h][j] *= c[h][j];
             }
-#pragma unroll
-            for (int h = 0; h < G::H_PER_THREAD; ++h)
-#pragma unroll
-                for (int j = 0; j < kNC; ++j) prod[h][j] *= c[h][j];
         }
 
-        const float mean = a.psi_in ? 0.0f : __ldg(a.means + p);
-#pragma unroll
-        for (int h = 0; h < G::H_PER_THREAD; ++h) {
-            int y, x;
-            item_origin<K>(h, y0, x0, y, x);
-            if (y >= a.H || x >= a.W) continue;
-            const int n = min(kNC, a.W - x);
-            const bool vec = kp.vec_ok && n == kNC;
-            const long long off = p * plane_px + static_cast<long long>(y) * a.W + x;
-            float old[kNC];
-            if (a.psi_in) {
-                load16_phi(a.psi_in, 0, off, vec, n, old);
-            } else {
-#pragma unroll
-                for (int j = 0; j < kNC; ++j) old[j] = mean;
-            }
-            float out[kNC];
-#pragma unroll
-            for (int j = 0; j < kNC; ++j) out[j] = old[j] * prod[h][j];
-            store16(a.psi_out + off, vec, n, out);
-        }
+        // update epilogue, row by row: psi' = psi * prod with whole row segments
+        park_items<K>(stage, prod);
+        __syncthreads();
+        row_epilogue<K, 1>(a, kp.vec_ok, stage, p * plane_px, y0, x0,
+                          a.psi_in ? 0.0f : __ldg(a.means + p));
+        __syncthreads();   // the staging tile is rewritten by the next pass
     }
 }
 
@@ -431,7 +459,7 @@ cudaError_t launch_pair(const FusedArgs &a, int which, cudaStream_t s) {
     kp.a = a;
     const bool aligned = aligned16(a.phi) && aligned16(a.ratio) && aligned16(a.psi_out) &&
                          (a.psi_in == nullptr || aligned16(a.psi_in));
-    kp.vec_ok = aligned && (a.W % 16 == 0);
+    kp.vec_ok = aligned && (a.W % 4 == 0);
     const bool tma_ok = !a.circular && (a.W % 4 == 0);
     if (which == 0) {
         if (tma_ok && a.psi_in && aligned16(a.psi_in))

@@ -143,7 +143,7 @@ __device__ __forceinline__ void vertical_pass(const float *__restrict__ tile, fl
         vertical_item<K, kNR>(tile, stage, t, it - rb * G::TX, rb * kNR);
     }
     if (G::R > 0) {
-        constexpr int HC = 2 * G::R;             // halo columns TX .. TX+2R-1
+        constexpr int HC = G::R > 0 ? 2 * G::R : 1;   // halo columns TX .. TX+2R-1
         for (int it = threadIdx.x; it < HC * (G::TY / 8); it += kThreads) {
             const int r8 = it / HC;
             vertical_item<K, 8>(tile, stage, t, G::TX + (it - r8 * HC), r8 * 8);
@@ -184,6 +184,62 @@ __device__ __forceinline__ void horizontal_pass(const float *__restrict__ stage,
                 }
             }
         }
+    }
+}
+
+// Horizontal pass of a one-term factorisation whose result multiplies into
+// `prod` item by item (the running product over views of kernel B), so no
+// second set of accumulators stays live.
+template <int K>
+__device__ __forceinline__ void horizontal_pass_mul(const float *__restrict__ stage,
+                                                    const float *__restrict__ taps_s,
+                                                    float (&prod)[Geo<K>::H_PER_THREAD][kNC]) {
+    using G = Geo<K>;
+    constexpr int NIN = kNC + K - 1;
+    float t[K];
+#pragma unroll
+    for (int m = 0; m < K; ++m) t[m] = taps_s[m];
+#pragma unroll
+    for (int h = 0; h < G::H_PER_THREAD; ++h) {
+        const int it = threadIdx.x + h * kThreads;
+        const float4 *src = reinterpret_cast<const float4 *>(stage + (it % G::TY) * G::VB_LD + (it / G::TY) * kNC);
+        float acc[kNC];
+#pragma unroll
+        for (int j = 0; j < kNC; ++j) acc[j] = 0.0f;
+#pragma unroll
+        for (int q = 0; q < (NIN + 3) / 4; ++q) {
+            const float4 v = src[q];
+            const float x4[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const int i = 4 * q + e;
+#pragma unroll
+                for (int j = 0; j < kNC; ++j) {
+                    const int m = i - j;
+                    if (i < NIN && m >= 0 && m < K) acc[j] = fmaf(t[m], x4[e], acc[j]);
+                }
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < kNC; ++j) prod[h][j] *= acc[j];
+    }
+}
+
+// Park this thread's horizontal-pass results in the staging tile at their
+// output positions (row, 16g + j).  Lanes run along rows and the pitch is an
+// odd multiple of 4 floats, so the 16-byte stores are conflict-free.  The
+// caller synchronises before the tile is read back row by row.
+template <int K>
+__device__ __forceinline__ void park_items(float *__restrict__ stage,
+                                           const float (&acc)[Geo<K>::H_PER_THREAD][kNC]) {
+    using G = Geo<K>;
+#pragma unroll
+    for (int h = 0; h < G::H_PER_THREAD; ++h) {
+        const int it = threadIdx.x + h * kThreads;
+        float4 *dst = reinterpret_cast<float4 *>(stage + (it % G::TY) * G::VB_LD + (it / G::TY) * kNC);
+#pragma unroll
+        for (int q = 0; q < kNC / 4; ++q)
+            dst[q] = make_float4(acc[h][4 * q], acc[h][4 * q + 1], acc[h][4 * q + 2], acc[h][4 * q + 3]);
     }
 }
 
