@@ -153,6 +153,7 @@ struct mvd_ctx {
     mvd_update_order order = MVD_ORDER_SIMULTANEOUS;
     double rank_tol = kDefaultRankTol;
     std::vector<float> psfs;
+    std::vector<float> taps_host;
     mvd::FactorTable ft;
     DevBuf taps, psf_dev, means, ratio, plain;
     // end-to-end pipeline
@@ -167,7 +168,8 @@ namespace {
 
 mvd_status upload_factors(mvd_ctx *c) {
     const int cap = mvd::max_terms(c->V, c->K) * 4 * c->K;
-    std::vector<float> taps(static_cast<size_t>(cap));
+    std::vector<float> &taps = c->taps_host;
+    taps.assign(static_cast<size_t>(cap), 0.0f);
     char msg[256] = {0};
     if (!mvd::factorise_psfs(c->psfs.data(), c->V, c->K, c->rank_tol, c->ft, taps.data(), cap, msg, sizeof msg))
         return fail(MVD_ERR_ARG, "PSF factorisation failed: %s", msg);
@@ -188,6 +190,7 @@ mvd::FusedArgs fused_args(const mvd_ctx *c, const void *data, mvd_dtype dt, floa
     a.phi_u16 = dt == MVD_U16;
     a.ratio = c->ratio.as<float>();
     a.taps = c->taps.as<float>();
+    a.taps_host = c->taps_host.data();
     a.ft = c->ft;
     a.H = c->H;
     a.W = c->W;
@@ -439,7 +442,7 @@ mvd_status mvd_set_algo(mvd_ctx *c, mvd_algo algo) {
     if (!c) return fail(MVD_ERR_ARG, "ctx is NULL");
     if (algo != MVD_ALGO_FUSED && algo != MVD_ALGO_PLAIN && algo != MVD_ALGO_DIRECT)
         return fail(MVD_ERR_ARG, "unknown algo %d", static_cast<int>(algo));
-    if (algo == MVD_ALGO_FUSED && !mvd::fused_supported(c->K))
+    if (algo == MVD_ALGO_FUSED && !(mvd::fused_supported(c->K) && mvd::fused_taps_fit(c->ft)))
         return fail(MVD_ERR_UNSUPPORTED, "fused path takes K <= %d (got %d)", mvd::kFusedMaxK, c->K);
     c->algo = algo;
     return MVD_OK;
@@ -529,7 +532,10 @@ mvd_status mvd_deconvolve_planes(mvd_ctx *c, const void *data, mvd_dtype dt, flo
             return cuda_fail(e, "plane means kernel");
         c->prof.end(s);
     }
-    if (c->algo == MVD_ALGO_FUSED) return run_fused(c, data, dt, est, n_planes, init_mean, s);
+    // the fused kernels carry the taps in their parameter block: PSFs that need
+    // more separable terms than it holds run on the plain path
+    if (c->algo == MVD_ALGO_FUSED && mvd::fused_taps_fit(c->ft))
+        return run_fused(c, data, dt, est, n_planes, init_mean, s);
     return run_plain(c, data, dt, est, n_planes, init_mean, c->algo == MVD_ALGO_DIRECT, s);
 }
 

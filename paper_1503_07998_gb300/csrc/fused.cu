@@ -36,11 +36,17 @@ namespace {
 
 constexpr long long kDrainBudget = 4000000000LL;
 
+// Factor taps travel in the launch's parameter block (constant bank): the
+// kernel's two kinds (blur or correlation) of every term, [vertical K]
+// [horizontal K] per term.  Warp-uniform, they need no vector registers.
+constexpr int kParamTaps = 4096;
+
 struct KParams {
     CUtensorMap map;   // psi (kernel A) or the ratio planes (kernel B); valid if use_tma
     FusedArgs a;
     int use_tma;
     int vec_ok;
+    float taps[kParamTaps];
 };
 
 // Wait for the tile on `bar`; on an expired budget flag the device status,
@@ -56,31 +62,6 @@ __device__ __forceinline__ bool wait_tile(uint64_t *bar, uint32_t parity, const 
     }
     __syncthreads();
     return *abort_flag == 0;
-}
-
-// Where a kernel finds the factor taps: vertical taps of term tt at
-// base + tt * stride, the horizontal ones `hoff` floats later.
-struct TapSrc {
-    const float *base;
-    int stride;
-    int hoff;
-};
-
-// Copy kinds kind0 and kind0+1 (blur or correlation) of every term into
-// shared memory when they fit; else point into the global table.  The
-// caller synchronises before the taps are read.
-template <int K>
-__device__ __forceinline__ TapSrc stage_taps(float *taps_s, const FusedArgs &a, int kind0) {
-    const int n = a.ft.total_terms * 2 * K;
-    if (n * 4 <= kTapBytes) {
-        for (int i = threadIdx.x; i < n; i += kThreads) {
-            const int tt = i / (2 * K);
-            const int r = i - tt * 2 * K;
-            taps_s[i] = __ldg(a.taps + (tt * 4 + kind0) * K + r);
-        }
-        return {taps_s, 2 * K, K};
-    }
-    return {a.taps + kind0 * K, 4 * K, K};
 }
 
 // Four consecutive values of one row: uint16 or FP32 source.
@@ -199,7 +180,6 @@ blur_ratio_kernel(const __grid_constant__ KParams kp) {
     extern __shared__ __align__(128) unsigned char smem[];
     uint64_t *bar = reinterpret_cast<uint64_t *>(smem);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(smem + 8);
-    float *taps_s = reinterpret_cast<float *>(smem + kHeaderBytes);
     float *tile = reinterpret_cast<float *>(smem + kTileOffset);
     float *stage = tile + G::BOX_H * G::BOX_W;
 
@@ -224,7 +204,6 @@ blur_ratio_kernel(const __grid_constant__ KParams kp) {
             tma::fence_barrier_init();
         }
     }
-    const TapSrc ts = stage_taps<K>(taps_s, a, 0);
     __syncthreads();
     int t = blockIdx.x;
     if (use_tma && threadIdx.x == 0 && t < n_tiles) {
@@ -258,7 +237,7 @@ blur_ratio_kernel(const __grid_constant__ KParams kp) {
 #pragma unroll
                 for (int j = 0; j < kNC; ++j) acc[h][j] = 0.0f;
             for (int q = 0; q < a.ft.rank[lead]; ++q) {
-                const float *tq = ts.base + (a.ft.tap_off[lead] + q) * ts.stride;
+                const float *tq = kp.taps + (a.ft.tap_off[lead] + q) * 2 * K;
                 vertical_pass<K>(tile, stage, tq);
                 __syncthreads();
                 if (--left == 0 && use_tma && threadIdx.x == 0 && t_next < n_tiles) {
@@ -267,7 +246,7 @@ blur_ratio_kernel(const __grid_constant__ KParams kp) {
                     tma::mbar_arrive_expect_tx(bar, G::TILE_BYTES);
                     tma::load_3d(tile, &kp.map, bar, c.x0 - G::R4, c.y0 - G::R, c.p);
                 }
-                horizontal_pass<K>(stage, tq + ts.hoff, acc);
+                horizontal_pass<K>(stage, tq + K, acc);
                 __syncthreads();
             }
             // ratio epilogue, row by row: every warp loads phi and stores r as
@@ -294,7 +273,6 @@ correlate_update_kernel(const __grid_constant__ KParams kp) {
     extern __shared__ __align__(128) unsigned char smem[];
     uint64_t *bar = reinterpret_cast<uint64_t *>(smem);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(smem + 8);
-    float *taps_s = reinterpret_cast<float *>(smem + kHeaderBytes);
     float *tile = reinterpret_cast<float *>(smem + kTileOffset);
     float *stage = tile + G::BOX_H * G::BOX_W;
 
@@ -310,7 +288,6 @@ correlate_update_kernel(const __grid_constant__ KParams kp) {
             tma::fence_barrier_init();
         }
     }
-    const TapSrc ts = stage_taps<K>(taps_s, a, 2);
     __syncthreads();
     int t = blockIdx.x;
     if (use_tma && threadIdx.x == 0 && t < n_tiles) {
@@ -354,11 +331,11 @@ correlate_update_kernel(const __grid_constant__ KParams kp) {
                 }
             };
             if (a.ft.rank[v] == 1) {
-                const float *tq = ts.base + a.ft.tap_off[v] * ts.stride;
+                const float *tq = kp.taps + a.ft.tap_off[v] * 2 * K;
                 vertical_pass<K>(tile, stage, tq);
                 __syncthreads();
                 prefetch_next();
-                horizontal_pass_mul<K>(stage, tq + ts.hoff, prod);
+                horizontal_pass_mul<K>(stage, tq + K, prod);
                 __syncthreads();
             } else {
                 float c[G::H_PER_THREAD][kNC];
@@ -367,11 +344,11 @@ correlate_update_kernel(const __grid_constant__ KParams kp) {
 #pragma unroll
                     for (int j = 0; j < kNC; ++j) c[h][j] = 0.0f;
                 for (int q = 0; q < a.ft.rank[v]; ++q) {
-                    const float *tq = ts.base + (a.ft.tap_off[v] + q) * ts.stride;
+                    const float *tq = kp.taps + (a.ft.tap_off[v] + q) * 2 * K;
                     vertical_pass<K>(tile, stage, tq);
                     __syncthreads();
                     if (q == a.ft.rank[v] - 1) prefetch_next();
-                    horizontal_pass<K>(stage, tq + ts.hoff, c);
+                    horizontal_pass<K>(stage, tq + K, c);
                     __syncthreads();
                 }
 #pragma unroll
@@ -454,9 +431,13 @@ cudaError_t launch_pair(const FusedArgs &a, int which, cudaStream_t s) {
     const long long n_tiles = static_cast<long long>((a.W + G::TX - 1) / G::TX) * ((a.H + G::TY - 1) / G::TY) * a.P;
     if (n_tiles > 0x7fffffffLL) return cudaErrorInvalidValue;
     const dim3 grid(static_cast<unsigned>(n_tiles < resident[dev & 63][which] ? n_tiles : resident[dev & 63][which]));
-    KParams kp;
+    KParams kp;   // about 18 KB with the taps; the launch copies it
     std::memset(&kp, 0, sizeof kp);
     kp.a = a;
+    if (a.ft.total_terms * 2 * K > kParamTaps || !a.taps_host) return cudaErrorInvalidValue;
+    for (int tt = 0; tt < a.ft.total_terms; ++tt)
+        std::memcpy(kp.taps + tt * 2 * K, a.taps_host + (static_cast<size_t>(tt) * 4 + (which == 0 ? 0 : 2)) * K,
+                    2 * K * sizeof(float));
     const bool aligned = aligned16(a.phi) && aligned16(a.ratio) && aligned16(a.psi_out) &&
                          (a.psi_in == nullptr || aligned16(a.psi_in));
     kp.vec_ok = aligned && (a.W % 4 == 0);
@@ -496,6 +477,8 @@ cudaError_t dispatch(const FusedArgs &a, int which, cudaStream_t s) {
 }  // namespace fused
 
 bool fused_supported(int K) { return K >= 1 && K <= kFusedMaxK && (K % 2) == 1; }
+
+bool fused_taps_fit(const FactorTable &ft) { return ft.total_terms * 2 * ft.K <= fused::kParamTaps; }
 
 void fused_tile_shape(int K, int *tile_h, int *tile_w) {
     switch (K) {

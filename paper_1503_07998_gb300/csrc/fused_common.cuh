@@ -38,8 +38,7 @@ constexpr int kNR = 16;      // rows per vertical item
 constexpr int kNC = 16;      // columns per horizontal item
 constexpr int kTX = 128;     // output tile width
 constexpr int kHeaderBytes = 128;   // mbarrier + abort flag
-constexpr int kTapBytes = 1536;     // the launch's factor taps when they fit (else read from global)
-constexpr int kTileOffset = kHeaderBytes + kTapBytes;   // a multiple of 128 for the TMA destination
+constexpr int kTileOffset = kHeaderBytes;   // a multiple of 128 for the TMA destination
 // Two CTAs per SM: 228 KB per SM minus 1 KB reserved per CTA.
 constexpr int kTwoCtaSmem = 113 * 1024;
 

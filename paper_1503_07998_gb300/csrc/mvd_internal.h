@@ -60,6 +60,7 @@ struct FusedArgs {
     int phi_u16;
     float *ratio;            // [V][P][H][W] scratch
     const float *taps;       // device factor taps (see FactorTable)
+    const float *taps_host;  // the same table on the host (copied into each launch)
     FactorTable ft;
     int H, W, P;
     int circular;
@@ -73,6 +74,8 @@ constexpr int kDevTimeout = 1;
 constexpr long long kDefaultWaitBudget = 2000000000LL;   // about one second at 2 GHz
 
 bool fused_supported(int K);
+// The fused kernels carry the taps in their parameter block; false if they do not fit.
+bool fused_taps_fit(const FactorTable &ft);
 void fused_tile_shape(int K, int *tile_h, int *tile_w);
 cudaError_t launch_fused_blur_ratio(const FusedArgs &a, cudaStream_t s);
 cudaError_t launch_fused_correlate_update(const FusedArgs &a, cudaStream_t s);

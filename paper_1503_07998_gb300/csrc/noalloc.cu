@@ -105,6 +105,7 @@ extern "C" mvd_status mvd_deconvolve_planes_static(int views, const float *psfs_
     if (!mvd::factorise_psfs(psfs_host, views, psf_size, 3e-7, ft, g_taps_host,
                              static_cast<int>(sizeof g_taps_host / sizeof(float)), msg, sizeof msg))
         return fail(MVD_ERR_ARG, "PSF factorisation failed");
+    if (!mvd::fused_taps_fit(ft)) return fail(MVD_ERR_ARG, "the PSFs need too many separable terms for this call");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     // pageable source: the call returns once g_taps_host has been staged
     e = cudaMemcpyAsync(base + off_taps, g_taps_host, static_cast<size_t>(ft.total_terms) * 4 * psf_size * sizeof(float),
@@ -124,6 +125,7 @@ extern "C" mvd_status mvd_deconvolve_planes_static(int views, const float *psfs_
     a.phi_u16 = dt == MVD_U16;
     a.ratio = reinterpret_cast<float *>(base + off_ratio);
     a.taps = reinterpret_cast<const float *>(base + off_taps);
+    a.taps_host = g_taps_host;
     a.ft = ft;
     a.H = plane_h;
     a.W = plane_w;
