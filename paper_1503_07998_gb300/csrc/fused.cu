@@ -45,7 +45,8 @@ struct KParams {
     CUtensorMap map;   // psi (kernel A) or the ratio planes (kernel B); valid if use_tma
     FusedArgs a;
     int use_tma;
-    int vec_ok;
+    int vec_ok;    // rows are multiples of 4 elements and buffers 16-byte aligned
+    int vec16;     // rows are multiples of 16 elements as well
     float taps[kParamTaps];
 };
 
@@ -236,6 +237,14 @@ blur_ratio_kernel(const __grid_constant__ KParams kp) {
             for (int h = 0; h < G::H_PER_THREAD; ++h)
 #pragma unroll
                 for (int j = 0; j < kNC; ++j) acc[h][j] = 0.0f;
+            // the first view of the group: its uint16 data for this thread's
+            // items are requested before the last horizontal pass, so that the
+            // loads land while the FMAs run
+            int v_first = a.view_hi;
+            for (int v = a.view_hi - 1; v >= a.view_lo; --v)
+                if (a.ft.group[v] == g) v_first = v;
+            const bool pre = kp.vec16 && a.phi_u16;
+            uint4 pf[G::H_PER_THREAD][2];
             for (int q = 0; q < a.ft.rank[lead]; ++q) {
                 const float *tq = kp.taps + (a.ft.tap_off[lead] + q) * 2 * K;
                 vertical_pass<K>(tile, stage, tq);
@@ -246,19 +255,62 @@ blur_ratio_kernel(const __grid_constant__ KParams kp) {
                     tma::mbar_arrive_expect_tx(bar, G::TILE_BYTES);
                     tma::load_3d(tile, &kp.map, bar, c.x0 - G::R4, c.y0 - G::R, c.p);
                 }
+                if (pre && q == a.ft.rank[lead] - 1) {
+                    const long long vplane = (static_cast<long long>(v_first) * a.P + p) * plane_px;
+#pragma unroll
+                    for (int h = 0; h < G::H_PER_THREAD; ++h) {
+                        int y, x;
+                        item_origin<K>(h, y0, x0, y, x);
+                        if (y < a.H && x < a.W) {
+                            const uint4 *src = reinterpret_cast<const uint4 *>(
+                                static_cast<const uint16_t *>(a.phi) + vplane + static_cast<long long>(y) * a.W + x);
+                            pf[h][0] = __ldg(src);
+                            pf[h][1] = __ldg(src + 1);
+                        }
+                    }
+                }
                 horizontal_pass<K>(stage, tq + K, acc);
                 __syncthreads();
             }
-            // ratio epilogue, row by row: every warp loads phi and stores r as
-            // whole contiguous row segments of the tile
-            park_items<K>(stage, acc);
-            __syncthreads();
+            // ratio epilogue per item (16 consecutive pixels of one row)
             for (int v = a.view_lo; v < a.view_hi; ++v) {
                 if (a.ft.group[v] != g) continue;
                 const long long vplane = (static_cast<long long>(v) * a.P + p) * plane_px;
-                row_epilogue<K, 0>(a, kp.vec_ok, stage, vplane, y0, x0, 0.0f);
+#pragma unroll
+                for (int h = 0; h < G::H_PER_THREAD; ++h) {
+                    int y, x;
+                    item_origin<K>(h, y0, x0, y, x);
+                    if (y >= a.H || x >= a.W) continue;
+                    const int n = min(kNC, a.W - x);
+                    const long long off = vplane + static_cast<long long>(y) * a.W + x;
+                    float ph[kNC];
+                    if (pre && v == v_first) {
+                        const unsigned w[8] = {pf[h][0].x, pf[h][0].y, pf[h][0].z, pf[h][0].w,
+                                               pf[h][1].x, pf[h][1].y, pf[h][1].z, pf[h][1].w};
+#pragma unroll
+                        for (int k = 0; k < 8; ++k) {
+                            ph[2 * k] = static_cast<float>(w[k] & 0xffffu);
+                            ph[2 * k + 1] = static_cast<float>(w[k] >> 16);
+                        }
+                    } else {
+#pragma unroll
+                        for (int q4 = 0; q4 < kNC / 4; ++q4) {
+                            float f[4];
+                            load4(a.phi, a.phi_u16, off + 4 * q4, kp.vec_ok && n == kNC, max(0, min(4, n - 4 * q4)), f);
+#pragma unroll
+                            for (int e = 0; e < 4; ++e) ph[4 * q4 + e] = f[e];
+                        }
+                    }
+#pragma unroll
+                    for (int q4 = 0; q4 < kNC / 4; ++q4) {
+                        float r[4];
+#pragma unroll
+                        for (int e = 0; e < 4; ++e)
+                            r[e] = __fdividef(ph[4 * q4 + e], fmaxf(acc[h][4 * q4 + e], a.eps));
+                        store4(a.ratio + off + 4 * q4, kp.vec_ok && n == kNC, max(0, min(4, n - 4 * q4)), r);
+                    }
+                }
             }
-            __syncthreads();   // the staging tile is rewritten by the next pass
         }
     }
 }
@@ -441,6 +493,7 @@ cudaError_t launch_pair(const FusedArgs &a, int which, cudaStream_t s) {
     const bool aligned = aligned16(a.phi) && aligned16(a.ratio) && aligned16(a.psi_out) &&
                          (a.psi_in == nullptr || aligned16(a.psi_in));
     kp.vec_ok = aligned && (a.W % 4 == 0);
+    kp.vec16 = aligned && (a.W % 16 == 0);
     const bool tma_ok = !a.circular && (a.W % 4 == 0);
     if (which == 0) {
         if (tma_ok && a.psi_in && aligned16(a.psi_in))

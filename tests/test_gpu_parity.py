@@ -38,7 +38,14 @@ def run_gpu(mvd, phi, psfs, iters, boundary="zero", eps=1e-6, algo="fused", psi0
     K = psfs.shape[-1]
     ctx = mvd.mvd_create(V, psfs, K, H, W, iters, boundary, eps)
     try:
-        mvd.mvd_set_algo(ctx, algo)
+        try:
+            mvd.mvd_set_algo(ctx, algo)
+        except mvd.MvdError as e:
+            # PSFs needing more separable terms than the fused kernels carry
+            # run on the plain path
+            if algo != "fused" or e.status != mvd.MVD_ERR_UNSUPPORTED:
+                raise
+            mvd.mvd_set_algo(ctx, "plain")
         mvd.mvd_set_update_order(ctx, order)
         if rank_tol is not None:
             mvd.mvd_set_rank_tolerance(ctx, rank_tol)
@@ -110,6 +117,25 @@ def test_ragged_tiles_general_psfs(mvd, boundary, K, V, H, W, dtype):
     ref = oracle.rl_planes(phi, psfs, iters, boundary=boundary, eps=1e-6, route="fft")
     got = run_gpu(mvd, phi, psfs, iters, boundary)
     assert_parity(got, ref, what=f"fused K={K} V={V} {boundary}")
+
+
+@pytest.mark.parametrize("boundary", ["zero", "circular"])
+@pytest.mark.parametrize("K,angles,H,W", [(41, (0, 90, 180, 270), 150, 135), (47, (0, 90), 64, 256),
+                                          (45, (0, 90, 45), 100, 200)])
+def test_fused_large_psfs_few_terms(mvd, boundary, K, angles, H, W):
+    """Gaussian PSFs (one term when axis-aligned, a few when turned by 45
+    degrees) at the largest sizes the fused kernels take."""
+    c = synth.plane_case(seed=K, H=H, W=W, n_planes=2, n_blobs=50, K=K, sigma_axial=9.0,
+                         sigma_lateral=1.8, angles=angles, dtype=np.uint16)
+    ctx = mvd.mvd_create(len(angles), c.psfs, K, H, W, 3, boundary, 1e-6)
+    try:
+        mvd.mvd_set_algo(ctx, "fused")          # must be available
+    finally:
+        ctx.close()
+    order = "sequential" if len(angles) > 2 else "simultaneous"
+    ref = oracle.rl_planes(c.phi, c.psfs, 3, boundary=boundary, eps=1e-6, route="fft", order=order)
+    got = run_gpu(mvd, c.phi, c.psfs, 3, boundary, order=order)
+    assert_parity(got, ref, what=f"fused K={K} views={len(angles)} {boundary}")
 
 
 @pytest.mark.parametrize("boundary", ["zero", "circular"])
