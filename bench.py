@@ -57,7 +57,9 @@ HBM_PEAK_GBS = 6767.4
 ALU_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 # dram__bytes_read.sum + dram__bytes_write.sum per launch from one ncu capture,
 # scaled to the full workload (None until measured for the current kernels).
-NCU_TRAFFIC_PER_LAUNCH = {"blur_ratio": None, "correlate_update": None}
+# Taken on 128 of the 512 planes (--workload slab512) and scaled by 4; see
+# profiles/fused_kernels_volume512.md.
+NCU_TRAFFIC_PER_LAUNCH = {"blur_ratio": 1.9334e9, "correlate_update": 2.0165e9}
 
 
 def _peaks():
