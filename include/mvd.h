@@ -185,6 +185,32 @@ mvd_status mvd_device_status(mvd_ctx *ctx, void *stream);
  * its copy has landed, so the error path can be tested without a real one. */
 mvd_status mvd_set_wait_budget(mvd_ctx *ctx, long long cycles);
 
+/* PSF calibration: the Poisson data fit of the deconvolved estimate and its
+ * gradient with respect to every PSF entry.  The forward map is the
+ * context's `iters` simultaneous-order MV-RL iterations (Supp. Note 1) from
+ * the per-plane mean on n_planes planes of data_dev [V][P][H][W]; the loss is
+ *     L = sum_planes sum_v sum_x [ y_v(x) - phi_v(x) log max(y_v(x), eps) ],
+ *     y_v = P_v * psi_T
+ * (Poisson negative log-likelihood without constants).  The paper has no
+ * calibration step; this differentiates its iteration.  The gradient is
+ * taken with respect to the raw entries (non-negativity and normalisation
+ * are the optimiser's projection) by a hand-written reverse sweep; psi is
+ * kept every `checkpoint_every` iterations and each segment is recomputed
+ * before it is swept.  Tile sums are FP32, their combination FP64.
+ *   loss_host    receives L (may be NULL)
+ *   grad_dev     [V][K][K] FP32, receives dL/dP
+ *   estimate_dev [P][H][W] FP32 or NULL: receives psi_T
+ * Uses the context's PSFs, boundary and eps with direct K x K stencils
+ * (K <= 63).  MVD_ERR_UNSUPPORTED for the sequential update order.  Returns
+ * after the result is on the host (waits for `stream`). */
+mvd_status mvd_psf_grad(mvd_ctx *ctx, const void *data_dev, mvd_dtype dt, int n_planes,
+                        int checkpoint_every, double *loss_host, float *grad_dev,
+                        float *estimate_dev, void *stream);
+
+/* Replace the context's PSFs (same views and size), e.g. after an optimiser
+ * step of PSF calibration; same checks as mvd_create. */
+mvd_status mvd_set_psfs(mvd_ctx *ctx, const float *psfs_host);
+
 /* Fused deconvolution that allocates no GPU memory.  The paper has no
  * counterpart; this exists for callers that may not call cudaMalloc, such as
  * acquisition software deconvolving while a camera records (an allocation can

@@ -161,6 +161,7 @@ struct mvd_ctx {
     cudaStream_t copy_in = nullptr, copy_out = nullptr;
     Profiler prof;
     DevBuf status;                       // one int: device status word
+    DevBuf grad_ws, grad_acc;            // PSF-gradient workspace (floats) and FP64 sums
     long long wait_budget = mvd::kDefaultWaitBudget;
 };
 
@@ -304,6 +305,139 @@ const char *mvd_status_string(mvd_status s) {
 
 const char *mvd_last_error(void) { return t_last_error.c_str(); }
 
+mvd_status mvd_set_psfs(mvd_ctx *c, const float *psfs) {
+    t_last_error.clear();
+    if (!c || !psfs) return fail(MVD_ERR_ARG, "NULL argument");
+    const size_t KK = static_cast<size_t>(c->K) * c->K;
+    for (int v = 0; v < c->V; ++v) {
+        double sum = 0;
+        for (size_t i = 0; i < KK; ++i) {
+            const float x = psfs[v * KK + i];
+            if (!std::isfinite(x) || x < 0) return fail(MVD_ERR_ARG, "PSF %d has a negative or non-finite entry", v);
+            sum += x;
+        }
+        if (!(sum > 0)) return fail(MVD_ERR_ARG, "PSF %d sums to zero", v);
+    }
+    DeviceGuard g(c->device);
+    c->psfs.assign(psfs, psfs + c->V * KK);
+    if (c->psf_dev.ptr) {
+        cudaError_t e = cudaMemcpy(c->psf_dev.ptr, c->psfs.data(), c->psfs.size() * sizeof(float), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) return cuda_fail(e, "upload psfs");
+    }
+    return upload_factors(c);
+}
+
+mvd_status mvd_psf_grad(mvd_ctx *c, const void *data, mvd_dtype dt, int P, int ckpt, double *loss_host,
+                        float *grad_dev, float *est_dev, void *stream) {
+    t_last_error.clear();
+    if (!c) return fail(MVD_ERR_ARG, "ctx is NULL");
+    if (!data || !grad_dev) return fail(MVD_ERR_ARG, "NULL buffer");
+    if (dt != MVD_U16 && dt != MVD_F32) return fail(MVD_ERR_ARG, "unknown dtype");
+    if (P < 1 || P > 65535 || ckpt < 1) return fail(MVD_ERR_ARG, "need 1 <= n_planes <= 65535 and checkpoint_every >= 1");
+    if (c->order != MVD_ORDER_SIMULTANEOUS) return fail(MVD_ERR_UNSUPPORTED, "the gradient follows the simultaneous order");
+    if (c->K > mvd::adj::kMaxK) return fail(MVD_ERR_UNSUPPORTED, "the gradient takes K <= %d", mvd::adj::kMaxK);
+    DeviceGuard g(c->device);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int V = c->V, K = c->K, H = c->H, W = c->W, T = c->iters;
+    const long long plane = static_cast<long long>(H) * W, n = plane * P;
+    const int u16 = dt == MVD_U16;
+    const size_t es = u16 ? 2 : 4;
+    const int circ = c->boundary == MVD_BOUNDARY_CIRCULAR;
+    const float eps = c->eps;
+    const int nck = T > 0 ? (T + ckpt - 1) / ckpt : 0;
+    // float buffers, each n: checkpoints nck; psiA psiB; fb fr fc (V each);
+    // segment: psi (ckpt), b r c (V*ckpt each); psibar, psibar_new; cb (V), rb, bb
+    const long long nbuf = nck + 2 + 3LL * V + ckpt + 3LL * V * ckpt + 2 + V + 2;
+    cudaError_t e;
+    if ((e = c->grad_ws.ensure(static_cast<size_t>(nbuf * n) * sizeof(float))) != cudaSuccess ||
+        (e = c->grad_acc.ensure((static_cast<size_t>(V) * K * K + 1) * sizeof(double))) != cudaSuccess ||
+        (e = c->means.ensure(static_cast<size_t>(P) * sizeof(float))) != cudaSuccess)
+        return fail(MVD_ERR_NOMEM, "gradient workspace: %s", cudaGetErrorString(e));
+    if (!c->psf_dev.ptr) {
+        if ((e = c->psf_dev.ensure(c->psfs.size() * sizeof(float))) != cudaSuccess)
+            return fail(MVD_ERR_NOMEM, "psf copy: %s", cudaGetErrorString(e));
+        if ((e = cudaMemcpy(c->psf_dev.ptr, c->psfs.data(), c->psfs.size() * sizeof(float), cudaMemcpyHostToDevice)) !=
+            cudaSuccess)
+            return cuda_fail(e, "upload psfs");
+    }
+    float *w = c->grad_ws.as<float>();
+    auto take = [&](long long k) { float *p = w; w += k * n; return p; };
+    float *ck = take(nck), *psiA = take(1), *psiB = take(1);
+    float *fb = take(V), *fr = take(V), *fc = take(V);
+    float *sp = take(ckpt), *sb = take(static_cast<long long>(V) * ckpt), *sr = take(static_cast<long long>(V) * ckpt),
+          *sc = take(static_cast<long long>(V) * ckpt);
+    float *pbar = take(1), *pbar2 = take(1), *cb = take(V), *rb = take(1), *bb = take(1);
+    double *G = c->grad_acc.as<double>(), *loss = G + static_cast<size_t>(V) * K * K;
+    const float *psf = c->psf_dev.as<float>();
+    const char *phi = static_cast<const char *>(data);
+    auto phi_v = [&](int v) { return static_cast<const void *>(phi + static_cast<size_t>(v) * n * es); };
+    auto P_v = [&](int v) { return psf + static_cast<size_t>(v) * K * K; };
+#define MVD_TRY(x)                                           \
+    do {                                                     \
+        if ((e = (x)) != cudaSuccess) return cuda_fail(e, #x); \
+    } while (0)
+    // one forward iteration; b, r, cc hold the V intermediates
+    auto step = [&](const float *psi, float *next, float *b, float *r, float *cc) -> cudaError_t {
+        cudaError_t e2;
+        for (int v = 0; v < V; ++v) {
+            if ((e2 = mvd::adj::stencil(psi, b + v * n, P_v(v), K, H, W, P, circ, 0, 0, s)) != cudaSuccess) return e2;
+            if ((e2 = mvd::adj::ratio(phi_v(v), u16, b + v * n, r + v * n, n, eps, s)) != cudaSuccess) return e2;
+            if ((e2 = mvd::adj::stencil(r + v * n, cc + v * n, P_v(v), K, H, W, P, circ, 1, 0, s)) != cudaSuccess) return e2;
+        }
+        return mvd::adj::update(psi, cc, next, V, n, s);
+    };
+    c->prof.mark(s, "psf_grad");
+    MVD_TRY(cudaMemsetAsync(G, 0, (static_cast<size_t>(V) * K * K + 1) * sizeof(double), s));
+    MVD_TRY(mvd::launch_plane_means(data, u16, V, P, H, W, c->means.as<float>(), s));
+    MVD_TRY(mvd::adj::fill_means(psiA, c->means.as<float>(), plane, n, s));
+    // forward sweep, keeping psi at every checkpoint
+    float *cur = psiA, *nxt = psiB;
+    for (int t = 0; t < T; ++t) {
+        if (t % ckpt == 0) MVD_TRY(cudaMemcpyAsync(ck + (t / ckpt) * n, cur, n * sizeof(float), cudaMemcpyDeviceToDevice, s));
+        MVD_TRY(step(cur, nxt, fb, fr, fc));
+        std::swap(cur, nxt);
+    }
+    if (est_dev) MVD_TRY(cudaMemcpyAsync(est_dev, cur, n * sizeof(float), cudaMemcpyDeviceToDevice, s));
+    // terminal data fit
+    MVD_TRY(cudaMemsetAsync(pbar, 0, n * sizeof(float), s));
+    for (int v = 0; v < V; ++v) {
+        MVD_TRY(mvd::adj::stencil(cur, rb, P_v(v), K, H, W, P, circ, 0, 0, s));                 // y_v
+        MVD_TRY(mvd::adj::terminal(phi_v(v), u16, rb, bb, loss, n, eps, s));                  // ybar in bb
+        MVD_TRY(mvd::adj::stencil(bb, pbar, P_v(v), K, H, W, P, circ, 1, 1, s));              // psibar += P (*) ybar
+        MVD_TRY(mvd::adj::lag_sum(bb, cur, G + static_cast<size_t>(v) * K * K, K, H, W, P, circ, -1, s));
+    }
+    // reverse sweep, segment by segment
+    for (int sg = nck - 1; sg >= 0; --sg) {
+        const int t0 = sg * ckpt, L = std::min(T, t0 + ckpt) - t0;
+        MVD_TRY(cudaMemcpyAsync(sp, ck + sg * n, n * sizeof(float), cudaMemcpyDeviceToDevice, s));
+        for (int u = 0; u < L; ++u) {
+            float *next = (u + 1 < L) ? sp + (u + 1) * n : nxt;
+            MVD_TRY(step(sp + u * n, next, sb + u * V * n, sr + u * V * n, sc + u * V * n));
+        }
+        for (int u = L - 1; u >= 0; --u) {
+            const float *psi_t = sp + u * n, *b = sb + u * V * n, *r = sr + u * V * n, *cc = sc + u * V * n;
+            MVD_TRY(mvd::adj::cbar(pbar, psi_t, cc, pbar2, cb, V, n, s));
+            for (int v = 0; v < V; ++v) {
+                double *Gv = G + static_cast<size_t>(v) * K * K;
+                MVD_TRY(mvd::adj::stencil(cb + v * n, rb, P_v(v), K, H, W, P, circ, 0, 0, s));     // rbar = P * cbar
+                MVD_TRY(mvd::adj::lag_sum(cb + v * n, r + v * n, Gv, K, H, W, P, circ, 1, s));
+                MVD_TRY(mvd::adj::bbar(phi_v(v), u16, rb, b + v * n, bb, n, eps, s));
+                MVD_TRY(mvd::adj::stencil(bb, pbar2, P_v(v), K, H, W, P, circ, 1, 1, s));           // psibar += P (*) bbar
+                MVD_TRY(mvd::adj::lag_sum(bb, psi_t, Gv, K, H, W, P, circ, -1, s));
+            }
+            std::swap(pbar, pbar2);
+        }
+    }
+    MVD_TRY(mvd::adj::to_float(G, grad_dev, V * K * K, s));
+    c->prof.end(s);
+    double L_host = 0;
+    MVD_TRY(cudaMemcpyAsync(&L_host, loss, sizeof(double), cudaMemcpyDeviceToHost, s));
+    MVD_TRY(cudaStreamSynchronize(s));
+#undef MVD_TRY
+    if (loss_host) *loss_host = L_host;
+    return MVD_OK;
+}
+
 mvd_status mvd_device_status(mvd_ctx *c, void *stream) {
     if (!c) return fail(MVD_ERR_ARG, "ctx is NULL");
     DeviceGuard g(c->device);
@@ -432,6 +566,8 @@ mvd_status mvd_destroy(mvd_ctx *c) {
     c->run_planes.release();
     c->prof.destroy();
     c->status.release();
+    c->grad_ws.release();
+    c->grad_acc.release();
     if (c->copy_in) cudaStreamDestroy(c->copy_in);
     if (c->copy_out) cudaStreamDestroy(c->copy_out);
     delete c;

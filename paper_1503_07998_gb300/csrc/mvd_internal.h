@@ -80,6 +80,25 @@ void fused_tile_shape(int K, int *tile_h, int *tile_w);
 cudaError_t launch_fused_blur_ratio(const FusedArgs &a, cudaStream_t s);
 cudaError_t launch_fused_correlate_update(const FusedArgs &a, cudaStream_t s);
 
+// PSF-gradient building blocks (adjoint.cu); every call covers P planes.
+namespace adj {
+constexpr int kMaxK = 63;
+cudaError_t stencil(const float *in, float *out, const float *psf, int K, int H, int W, int P, int circular,
+                    int correlate, int accumulate, cudaStream_t s);
+cudaError_t lag_sum(const float *g, const float *img, double *G, int K, int H, int W, int P, int circular, int sign,
+                    cudaStream_t s);
+cudaError_t fill_means(float *psi, const float *means, long long plane, long long n, cudaStream_t s);
+cudaError_t ratio(const void *phi, int u16, const float *b, float *r, long long n, float eps, cudaStream_t s);
+cudaError_t update(const float *psi, const float *c, float *psi_next, int V, long long n, cudaStream_t s);
+cudaError_t terminal(const void *phi, int u16, const float *y, float *ybar, double *loss, long long n, float eps,
+                     cudaStream_t s);
+cudaError_t cbar(const float *psibar, const float *psi_t, const float *c, float *psibar_new, float *cb, int V,
+                 long long n, cudaStream_t s);
+cudaError_t bbar(const void *phi, int u16, const float *rbar, const float *b, float *bb, long long n, float eps,
+                 cudaStream_t s);
+cudaError_t to_float(const double *G, float *out, int n, cudaStream_t s);
+}  // namespace adj
+
 // Plain per-plane path (one plane, one step per launch).
 struct PlainArgs {
     const float *taps;       // device factor taps

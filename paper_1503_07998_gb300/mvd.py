@@ -67,6 +67,8 @@ def lib() -> ctypes.CDLL:
     L.mvd_set_rank_tolerance.argtypes = [vp, d]
     L.mvd_set_update_order.argtypes = [vp, i]
     L.mvd_device_status.argtypes = [vp, vp]
+    L.mvd_psf_grad.argtypes = [vp, vp, i, i, i, ctypes.POINTER(d), vp, vp, vp]
+    L.mvd_set_psfs.argtypes = [vp, vp]
     L.mvd_deconvolve_planes_static.argtypes = [i, vp, i, i, i, i, i, f, vp, i, vp, i, i, vp]
     L.mvd_set_wait_budget.argtypes = [vp, ctypes.c_longlong]
     L.mvd_get_info.argtypes = [vp, ctypes.POINTER(_Info)]
@@ -84,7 +86,7 @@ def lib() -> ctypes.CDLL:
     L.mvd_launch_count.restype = ctypes.c_uint64
     for name in ("mvd_create", "mvd_destroy", "mvd_set_algo", "mvd_set_rank_tolerance", "mvd_get_info",
                  "mvd_set_update_order", "mvd_device_status", "mvd_set_wait_budget",
-                 "mvd_deconvolve_planes_static",
+                 "mvd_deconvolve_planes_static", "mvd_psf_grad", "mvd_set_psfs",
                  "mvd_reslice", "mvd_deconvolve_planes", "mvd_run_host", "mvd_psf_factors",
                  "mvd_profile_enable", "mvd_profile_read"):
         getattr(L, name).restype = ctypes.c_int
@@ -305,6 +307,67 @@ def mvd_profile_read(ctx: Context) -> dict:
     n = ctypes.c_int(0)
     _check(lib().mvd_profile_read(ctx.handle, arr, cap, ctypes.byref(n)), "mvd_profile_read")
     return {arr[k].name.decode(): (arr[k].total_ms, int(arr[k].launches)) for k in range(min(n.value, cap))}
+
+
+def mvd_set_psfs(ctx: Context, psfs) -> None:
+    p = np.ascontiguousarray(np.asarray(psfs, dtype=np.float32))
+    if p.size != ctx.views * ctx.K * ctx.K:
+        raise ValueError("psfs must hold views * K * K values")
+    _check(lib().mvd_set_psfs(ctx.handle, p.ctypes.data_as(ctypes.c_void_p)), "mvd_set_psfs")
+
+
+def mvd_psf_grad(ctx: Context, data, checkpoint_every: int = 2, estimate=None, stream=None):
+    """Poisson data fit of the deconvolved estimate and its PSF gradient.
+
+    data [V][P][H][W] CUDA tensor.  Returns (loss: float, grad: float32 CUDA
+    tensor [V][K][K]); `estimate` ([P][H][W] float32 CUDA) receives psi_T."""
+    import torch
+    _require_cuda(data)
+    V, P, H, W = data.shape
+    if V != ctx.views or (H, W) != (ctx.H, ctx.W):
+        raise ValueError("data shape does not match the context")
+    grad = torch.empty((V, ctx.K, ctx.K), dtype=torch.float32, device=data.device)
+    loss = ctypes.c_double(0.0)
+    est_ptr = None
+    if estimate is not None:
+        _require_cuda(estimate)
+        if tuple(estimate.shape) != (P, H, W) or estimate.dtype != torch.float32:
+            raise ValueError("estimate must be float32 [P][H][W]")
+        est_ptr = ctypes.c_void_p(estimate.data_ptr())
+    _check(lib().mvd_psf_grad(ctx.handle, ctypes.c_void_p(data.data_ptr()), _dtype_code(data), P,
+                              int(checkpoint_every), ctypes.byref(loss), ctypes.c_void_p(grad.data_ptr()),
+                              est_ptr, _stream_of(data, stream)), "mvd_psf_grad")
+    return loss.value, grad
+
+
+def _psf_loss_function():
+    import torch
+
+    class PoissonFitOfDeconvolution(torch.autograd.Function):
+        """loss(psfs) = Poisson NLL of P_v * (MV-RL estimate after the
+        context's iterations) against the data; backward is the library's
+        hand-written adjoint (mvd_psf_grad)."""
+
+        @staticmethod
+        def forward(fctx, psfs, ctx, data, checkpoint_every):
+            mvd_set_psfs(ctx, psfs.detach().to("cpu", torch.float32).numpy())
+            loss, grad = mvd_psf_grad(ctx, data, checkpoint_every)
+            fctx.save_for_backward(grad)
+            return torch.tensor(loss, dtype=torch.float64, device=psfs.device)
+
+        @staticmethod
+        def backward(fctx, gout):
+            (grad,) = fctx.saved_tensors
+            g = grad.to(device=gout.device, dtype=torch.float64) * gout
+            return g, None, None, None
+
+    return PoissonFitOfDeconvolution
+
+
+def psf_fit_loss(psfs, ctx: Context, data, checkpoint_every: int = 2):
+    """Differentiable PSF-calibration loss (torch.autograd): gradients flow to
+    `psfs` ([V][K][K] tensor) through the library's adjoint."""
+    return _psf_loss_function().apply(psfs, ctx, data, checkpoint_every)
 
 
 def mvd_launch_count() -> int:
