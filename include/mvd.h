@@ -185,6 +185,52 @@ mvd_status mvd_device_status(mvd_ctx *ctx, void *stream);
  * its copy has landed, so the error path can be tested without a real one. */
 mvd_status mvd_set_wait_budget(mvd_ctx *ctx, long long cycles);
 
+/* ---- Batches of independent volumes -------------------------------------
+ * Planes are independent (Results section), and so are volumes: a batch runs
+ * many volumes of uneven plane size, plane count, view count, PSF size and
+ * iteration count as one unit.  Its whole schedule (reslicing, means,
+ * iterations of every volume) is captured once into a CUDA graph in which
+ * every volume is its own branch, and replayed by each mvd_batch_run. */
+typedef struct {
+    int views;                /* V                                             */
+    int psf_size;             /* K (odd)                                       */
+    const float *psfs_host;   /* [V][K][K], copied at mvd_batch_create         */
+    int plane_h, plane_w;     /* H (rows = z), W (columns = x)                 */
+    int n_planes;             /* P (= the stacks' Y)                           */
+    int iters;                /* RL iterations of this volume                  */
+    const void *stacks_dev;   /* [V][H][P][W] view stacks to reslice, or NULL  */
+    const void *planes_dev;   /* [V][P][H][W] planes, used if stacks_dev==NULL */
+    float *estimate_dev;      /* [P][H][W] FP32 result (per-plane mean start)  */
+} mvd_volume_desc;
+
+typedef struct mvd_batch mvd_batch;
+
+/* Create a batch (one internal context per volume, with all of its device
+ * workspace, plus planes buffers for volumes given as stacks).  Descriptors
+ * are copied; the device buffers they name must stay valid while the batch
+ * is used.  dt, boundary, eps and order apply to every volume. */
+mvd_status mvd_batch_create(mvd_batch **out, const mvd_volume_desc *vols, int n_volumes, mvd_dtype dt,
+                            mvd_boundary boundary, float eps, mvd_update_order order);
+
+/* Autotune the batch's launch shape: every candidate (all volumes as
+ * concurrent graph branches or one after another; persistent grids of one
+ * resident wave or half of one) is captured and timed on `stream`, the
+ * fastest kept.  With the environment variable MVD_TUNE_CACHE naming a file,
+ * choices are read from and appended to it, keyed by the batch's shapes.
+ * Runs the batch's work while timing (results are recomputed by every run). */
+mvd_status mvd_batch_tune(mvd_batch *b, void *stream);
+
+/* Run the batch: capture its graph on first use, then launch it on
+ * `stream` (asynchronous). */
+mvd_status mvd_batch_run(mvd_batch *b, void *stream);
+
+/* Launch shape in use: concurrent (1) or serial (0) branches, the
+ * persistent-grid cap per launch (0 = one resident wave) and the number of
+ * kernel nodes in the graph (0 before the first run). */
+mvd_status mvd_batch_info(const mvd_batch *b, int *concurrent, int *max_ctas, int *graph_kernels);
+
+mvd_status mvd_batch_destroy(mvd_batch *b);
+
 /* PSF calibration: the Poisson data fit of the deconvolved estimate and its
  * gradient with respect to every PSF entry.  The forward map is the
  * context's `iters` simultaneous-order MV-RL iterations (Supp. Note 1) from

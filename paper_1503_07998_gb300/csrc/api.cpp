@@ -7,6 +7,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -163,6 +164,7 @@ struct mvd_ctx {
     DevBuf status;                       // one int: device status word
     DevBuf grad_ws, grad_acc;            // PSF-gradient workspace (floats) and FP64 sums
     long long wait_budget = mvd::kDefaultWaitBudget;
+    int max_ctas = 0;                    // persistent-grid cap set by a batch's tuner
 };
 
 namespace {
@@ -200,7 +202,24 @@ mvd::FusedArgs fused_args(const mvd_ctx *c, const void *data, mvd_dtype dt, floa
     a.eps = c->eps;
     a.err = c->status.as<int>();
     a.wait_budget = c->wait_budget;
+    a.max_ctas = c->max_ctas;
     return a;
+}
+
+// Allocate everything a deconvolution of P planes needs, so that the call
+// itself allocates nothing (required while a stream is being captured).
+cudaError_t prepare_workspace(mvd_ctx *c, int P) {
+    const size_t plane_px = static_cast<size_t>(c->H) * c->W;
+    cudaError_t e = c->means.ensure(static_cast<size_t>(P) * sizeof(float));
+    if (e == cudaSuccess && c->algo == MVD_ALGO_FUSED && mvd::fused_taps_fit(c->ft))
+        e = c->ratio.ensure(static_cast<size_t>(c->V) * P * plane_px * sizeof(float));
+    if (e == cudaSuccess) e = c->plain.ensure(4 * plane_px * sizeof(float));
+    if (e == cudaSuccess && !c->psf_dev.ptr) {
+        e = c->psf_dev.ensure(c->psfs.size() * sizeof(float));
+        if (e == cudaSuccess)
+            e = cudaMemcpy(c->psf_dev.ptr, c->psfs.data(), c->psfs.size() * sizeof(float), cudaMemcpyHostToDevice);
+    }
+    return e;
 }
 
 mvd_status run_fused(mvd_ctx *c, const void *data, mvd_dtype dt, float *est, int P, int init_mean,
@@ -757,6 +776,277 @@ mvd_status mvd_run_host(mvd_ctx *c, const void *stacks_host, mvd_dtype dt, int n
     if (e1 != cudaSuccess) return cuda_fail(e1, "copy stream");
     if (e2 != cudaSuccess) return cuda_fail(e2, "compute stream");
     if (e3 != cudaSuccess) return cuda_fail(e3, "copy stream");
+    return MVD_OK;
+}
+
+}  // extern "C"
+
+// ---- batches -----------------------------------------------------------------
+
+struct mvd_batch {
+    int device = 0;
+    mvd_dtype dt = MVD_U16;
+    std::vector<mvd_volume_desc> vols;
+    std::vector<mvd_ctx *> ctx;
+    std::vector<DevBuf> planes;
+    std::vector<cudaStream_t> streams;
+    std::vector<cudaEvent_t> done;
+    cudaEvent_t fork = nullptr;
+    cudaStream_t cap = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int concurrent = 1;
+    int max_ctas = 0;
+    int graph_kernels = 0;
+    std::string key;
+};
+
+namespace {
+
+void batch_drop_graph(mvd_batch *b) {
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    b->exec = nullptr;
+    b->graph = nullptr;
+    b->graph_kernels = 0;
+}
+
+mvd_status batch_capture(mvd_batch *b) {
+    batch_drop_graph(b);
+    for (auto *c : b->ctx) c->max_ctas = b->max_ctas;
+    // launches made while capturing only record graph nodes: they are counted
+    // when the graph runs, not now
+    const uint64_t counted_before = mvd::g_launches.load();
+    struct Uncount {
+        uint64_t before;
+        ~Uncount() { mvd::g_launches.fetch_sub(mvd::g_launches.load() - before); }
+    } uncount{counted_before};
+    cudaError_t e = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return cuda_fail(e, "begin capture");
+    mvd_status st = MVD_OK;
+    cudaEventRecord(b->fork, b->cap);
+    for (size_t i = 0; i < b->vols.size() && st == MVD_OK; ++i) {
+        const mvd_volume_desc &v = b->vols[i];
+        cudaStream_t s = b->concurrent ? b->streams[i] : b->cap;
+        if (b->concurrent) cudaStreamWaitEvent(s, b->fork, 0);
+        const void *data = v.planes_dev;
+        if (v.stacks_dev) {
+            st = mvd_reslice(b->ctx[i], v.stacks_dev, b->dt, v.views, v.plane_h, v.n_planes, v.plane_w,
+                             b->planes[i].ptr, s);
+            data = b->planes[i].ptr;
+        }
+        if (st == MVD_OK) st = mvd_deconvolve_planes(b->ctx[i], data, b->dt, v.estimate_dev, v.n_planes, 1, s);
+        if (b->concurrent) {
+            cudaEventRecord(b->done[i], s);
+            cudaStreamWaitEvent(b->cap, b->done[i], 0);
+        }
+    }
+    cudaGraph_t g = nullptr;
+    e = cudaStreamEndCapture(b->cap, &g);
+    if (st != MVD_OK) {
+        if (g) cudaGraphDestroy(g);
+        return st;
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "end capture");
+    b->graph = g;
+    e = cudaGraphInstantiate(&b->exec, g, 0);
+    if (e != cudaSuccess) return cuda_fail(e, "graph instantiate");
+    size_t n = 0;
+    cudaGraphGetNodes(g, nullptr, &n);
+    std::vector<cudaGraphNode_t> nodes(n);
+    cudaGraphGetNodes(g, nodes.data(), &n);
+    int k = 0;
+    for (auto nd : nodes) {
+        cudaGraphNodeType t;
+        if (cudaGraphNodeGetType(nd, &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) ++k;
+    }
+    b->graph_kernels = k;
+    return MVD_OK;
+}
+
+bool tune_cache_lookup(const std::string &key, int *conc, int *ctas) {
+    const char *path = std::getenv("MVD_TUNE_CACHE");
+    if (!path || !*path) return false;
+    FILE *f = std::fopen(path, "r");
+    if (!f) return false;
+    char line[4096];
+    bool found = false;
+    while (std::fgets(line, sizeof line, f)) {
+        // line: <key> <concurrent> <max_ctas>
+        char *sp = std::strrchr(line, ' ');
+        if (!sp) continue;
+        *sp = 0;
+        const int c2 = std::atoi(sp + 1);
+        char *sp2 = std::strrchr(line, ' ');
+        if (!sp2) continue;
+        *sp2 = 0;
+        if (key == line) {
+            *conc = std::atoi(sp2 + 1);
+            *ctas = c2;
+            found = true;
+        }
+    }
+    std::fclose(f);
+    return found;
+}
+
+void tune_cache_store(const std::string &key, int conc, int ctas) {
+    const char *path = std::getenv("MVD_TUNE_CACHE");
+    if (!path || !*path) return;
+    FILE *f = std::fopen(path, "a");
+    if (!f) return;
+    std::fprintf(f, "%s %d %d\n", key.c_str(), conc, ctas);
+    std::fclose(f);
+}
+
+}  // namespace
+
+extern "C" {
+
+mvd_status mvd_batch_create(mvd_batch **out, const mvd_volume_desc *vols, int n, mvd_dtype dt,
+                            mvd_boundary boundary, float eps, mvd_update_order order) {
+    t_last_error.clear();
+    if (!out || !vols || n < 1) return fail(MVD_ERR_ARG, "need at least one volume");
+    if (dt != MVD_U16 && dt != MVD_F32) return fail(MVD_ERR_ARG, "unknown dtype");
+    *out = nullptr;
+    for (int i = 0; i < n; ++i) {
+        const mvd_volume_desc &v = vols[i];
+        if (!v.estimate_dev || (!v.stacks_dev && !v.planes_dev) || v.n_planes < 1)
+            return fail(MVD_ERR_ARG, "volume %d: needs data, an estimate buffer and n_planes >= 1", i);
+    }
+    auto *b = new (std::nothrow) mvd_batch();
+    if (!b) return fail(MVD_ERR_NOMEM, "batch");
+    cudaGetDevice(&b->device);
+    b->dt = dt;
+    b->vols.assign(vols, vols + n);
+    const size_t es = dt == MVD_U16 ? 2 : 4;
+    char buf[128];
+    b->key = "v1";
+    for (int i = 0; i < n && true; ++i) {
+        const mvd_volume_desc &v = vols[i];
+        mvd_ctx *c = nullptr;
+        mvd_status st = mvd_create(&c, v.views, v.psfs_host, v.psf_size, v.plane_h, v.plane_w, v.iters, boundary, eps);
+        if (st == MVD_OK) st = mvd_set_update_order(c, order);
+        if (st != MVD_OK) {
+            std::string m = t_last_error;
+            if (c) mvd_destroy(c);
+            mvd_batch_destroy(b);
+            return fail(st, "volume %d: %s", i, m.c_str());
+        }
+        b->ctx.push_back(c);
+        b->planes.emplace_back();
+        cudaError_t e = prepare_workspace(c, v.n_planes);
+        if (e == cudaSuccess && v.stacks_dev)
+            e = b->planes.back().ensure(static_cast<size_t>(v.views) * v.n_planes * v.plane_h * v.plane_w * es);
+        if (e != cudaSuccess) {
+            mvd_batch_destroy(b);
+            return fail(MVD_ERR_NOMEM, "volume %d workspace: %s", i, cudaGetErrorString(e));
+        }
+        std::snprintf(buf, sizeof buf, "_%dx%dx%dx%dv%dk%dt%d%s", v.n_planes, v.plane_h, v.plane_w, 0, v.views,
+                      v.psf_size, v.iters, v.stacks_dev ? "s" : "p");
+        b->key += buf;
+        cudaStream_t s = nullptr;
+        cudaEvent_t ev = nullptr;
+        if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) {
+            mvd_batch_destroy(b);
+            return fail(MVD_ERR_CUDA, "streams for the batch");
+        }
+        b->streams.push_back(s);
+        b->done.push_back(ev);
+    }
+    if (cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) != cudaSuccess) {
+        mvd_batch_destroy(b);
+        return fail(MVD_ERR_CUDA, "capture stream");
+    }
+    *out = b;
+    return MVD_OK;
+}
+
+mvd_status mvd_batch_run(mvd_batch *b, void *stream) {
+    t_last_error.clear();
+    if (!b) return fail(MVD_ERR_ARG, "batch is NULL");
+    DeviceGuard g(b->device);
+    if (!b->exec) {
+        mvd_status st = batch_capture(b);
+        if (st != MVD_OK) return st;
+    }
+    cudaError_t e = cudaGraphLaunch(b->exec, static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(e, "graph launch");
+    mvd::count_launch(b->graph_kernels);
+    return MVD_OK;
+}
+
+mvd_status mvd_batch_tune(mvd_batch *b, void *stream) {
+    t_last_error.clear();
+    if (!b) return fail(MVD_ERR_ARG, "batch is NULL");
+    DeviceGuard g(b->device);
+    int conc = 1, ctas = 0;
+    if (tune_cache_lookup(b->key, &conc, &ctas)) {
+        b->concurrent = conc;
+        b->max_ctas = ctas;
+        batch_drop_graph(b);
+        return MVD_OK;
+    }
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device);
+    const int cand[][2] = {{1, 0}, {0, 0}, {1, sms > 0 ? sms : 1}};
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    float best = 1e30f;
+    int best_i = 0;
+    mvd_status st = MVD_OK;
+    for (int i = 0; i < 3 && st == MVD_OK; ++i) {
+        b->concurrent = cand[i][0];
+        b->max_ctas = cand[i][1];
+        if ((st = batch_capture(b)) != MVD_OK) break;
+        cudaGraphLaunch(b->exec, s);                  // warm
+        cudaEventRecord(e0, s);
+        cudaGraphLaunch(b->exec, s);
+        cudaEventRecord(e1, s);
+        if (cudaEventSynchronize(e1) != cudaSuccess) {
+            st = cuda_fail(cudaGetLastError(), "tuning run");
+            break;
+        }
+        float ms = 0;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best) {
+            best = ms;
+            best_i = i;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st != MVD_OK) return st;
+    b->concurrent = cand[best_i][0];
+    b->max_ctas = cand[best_i][1];
+    batch_drop_graph(b);
+    tune_cache_store(b->key, b->concurrent, b->max_ctas);
+    return MVD_OK;
+}
+
+mvd_status mvd_batch_info(const mvd_batch *b, int *concurrent, int *max_ctas, int *graph_kernels) {
+    if (!b) return fail(MVD_ERR_ARG, "batch is NULL");
+    if (concurrent) *concurrent = b->concurrent;
+    if (max_ctas) *max_ctas = b->max_ctas;
+    if (graph_kernels) *graph_kernels = b->graph_kernels;
+    return MVD_OK;
+}
+
+mvd_status mvd_batch_destroy(mvd_batch *b) {
+    if (!b) return MVD_OK;
+    DeviceGuard g(b->device);
+    batch_drop_graph(b);
+    for (auto *c : b->ctx) mvd_destroy(c);
+    for (auto &p : b->planes) p.release();
+    for (auto s : b->streams) cudaStreamDestroy(s);
+    for (auto ev : b->done) cudaEventDestroy(ev);
+    if (b->fork) cudaEventDestroy(b->fork);
+    if (b->cap) cudaStreamDestroy(b->cap);
+    delete b;
     return MVD_OK;
 }
 

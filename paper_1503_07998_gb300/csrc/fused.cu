@@ -482,7 +482,9 @@ cudaError_t launch_pair(const FusedArgs &a, int which, cudaStream_t s) {
     }
     const long long n_tiles = static_cast<long long>((a.W + G::TX - 1) / G::TX) * ((a.H + G::TY - 1) / G::TY) * a.P;
     if (n_tiles > 0x7fffffffLL) return cudaErrorInvalidValue;
-    const dim3 grid(static_cast<unsigned>(n_tiles < resident[dev & 63][which] ? n_tiles : resident[dev & 63][which]));
+    long long ctas = resident[dev & 63][which];
+    if (a.max_ctas > 0 && a.max_ctas < ctas) ctas = a.max_ctas;
+    const dim3 grid(static_cast<unsigned>(n_tiles < ctas ? n_tiles : ctas));
     KParams kp;   // about 18 KB with the taps; the launch copies it
     std::memset(&kp, 0, sizeof kp);
     kp.a = a;

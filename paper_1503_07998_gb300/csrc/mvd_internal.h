@@ -68,6 +68,7 @@ struct FusedArgs {
     int view_lo, view_hi;    // views [lo, hi) take part in this launch
     int *err;                // device status word (kDevTimeout set on an expired wait)
     long long wait_budget;   // clock cycles a tile wait may spin before it reports a timeout
+    int max_ctas;            // cap on the persistent grid (0: one resident wave)
 };
 
 constexpr int kDevTimeout = 1;

@@ -69,6 +69,11 @@ def lib() -> ctypes.CDLL:
     L.mvd_device_status.argtypes = [vp, vp]
     L.mvd_psf_grad.argtypes = [vp, vp, i, i, i, ctypes.POINTER(d), vp, vp, vp]
     L.mvd_set_psfs.argtypes = [vp, vp]
+    L.mvd_batch_create.argtypes = [ctypes.POINTER(vp), vp, i, i, i, f, i]
+    L.mvd_batch_tune.argtypes = [vp, vp]
+    L.mvd_batch_run.argtypes = [vp, vp]
+    L.mvd_batch_info.argtypes = [vp, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i)]
+    L.mvd_batch_destroy.argtypes = [vp]
     L.mvd_deconvolve_planes_static.argtypes = [i, vp, i, i, i, i, i, f, vp, i, vp, i, i, vp]
     L.mvd_set_wait_budget.argtypes = [vp, ctypes.c_longlong]
     L.mvd_get_info.argtypes = [vp, ctypes.POINTER(_Info)]
@@ -87,6 +92,7 @@ def lib() -> ctypes.CDLL:
     for name in ("mvd_create", "mvd_destroy", "mvd_set_algo", "mvd_set_rank_tolerance", "mvd_get_info",
                  "mvd_set_update_order", "mvd_device_status", "mvd_set_wait_budget",
                  "mvd_deconvolve_planes_static", "mvd_psf_grad", "mvd_set_psfs",
+                 "mvd_batch_create", "mvd_batch_tune", "mvd_batch_run", "mvd_batch_info", "mvd_batch_destroy",
                  "mvd_reslice", "mvd_deconvolve_planes", "mvd_run_host", "mvd_psf_factors",
                  "mvd_profile_enable", "mvd_profile_read"):
         getattr(L, name).restype = ctypes.c_int
@@ -368,6 +374,97 @@ def psf_fit_loss(psfs, ctx: Context, data, checkpoint_every: int = 2):
     """Differentiable PSF-calibration loss (torch.autograd): gradients flow to
     `psfs` ([V][K][K] tensor) through the library's adjoint."""
     return _psf_loss_function().apply(psfs, ctx, data, checkpoint_every)
+
+
+class _VolumeDesc(ctypes.Structure):
+    _fields_ = [("views", ctypes.c_int), ("psf_size", ctypes.c_int), ("psfs_host", ctypes.c_void_p),
+                ("plane_h", ctypes.c_int), ("plane_w", ctypes.c_int), ("n_planes", ctypes.c_int),
+                ("iters", ctypes.c_int), ("stacks_dev", ctypes.c_void_p), ("planes_dev", ctypes.c_void_p),
+                ("estimate_dev", ctypes.c_void_p)]
+
+
+class Batch:
+    """Owns an ``mvd_batch`` (see mvd_batch_create); keeps the PSF arrays and
+    tensors it was built from alive."""
+
+    def __init__(self, handle, keep):
+        self.handle = ctypes.c_void_p(handle)
+        self._keep = keep
+
+    def close(self):
+        if self.handle and self.handle.value:
+            _check(lib().mvd_batch_destroy(self.handle), "mvd_batch_destroy")
+            self.handle = ctypes.c_void_p(0)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def mvd_batch_create(volumes, boundary: str = "zero", eps: float = 1e-6, order: str = "simultaneous") -> Batch:
+    """volumes: list of dicts with keys psfs ([V][K][K]), iters, estimate
+    (CUDA float32 [P][H][W]) and either stacks (CUDA [V][H][P][W]) or planes
+    (CUDA [V][P][H][W]); all data of one dtype."""
+    descs = (_VolumeDesc * len(volumes))()
+    keep, dtype = [], None
+    for i, v in enumerate(volumes):
+        psfs = np.ascontiguousarray(np.asarray(v["psfs"], dtype=np.float32))
+        keep.append(psfs)
+        est = v["estimate"]
+        _require_cuda(est)
+        P, H, W = est.shape
+        d = descs[i]
+        d.views, d.psf_size = psfs.shape[0], psfs.shape[-1]
+        d.psfs_host = psfs.ctypes.data
+        d.plane_h, d.plane_w, d.n_planes, d.iters = H, W, P, int(v["iters"])
+        d.estimate_dev = est.data_ptr()
+        src = v.get("stacks")
+        if src is not None:
+            _require_cuda(src)
+            if tuple(src.shape) != (psfs.shape[0], H, P, W):
+                raise ValueError(f"volume {i}: stacks must be [V][H][P][W]")
+            d.stacks_dev = src.data_ptr()
+        else:
+            src = v["planes"]
+            _require_cuda(src)
+            if tuple(src.shape) != (psfs.shape[0], P, H, W):
+                raise ValueError(f"volume {i}: planes must be [V][P][H][W]")
+            d.planes_dev = src.data_ptr()
+        keep.append(src)
+        keep.append(est)
+        code = _dtype_code(src)
+        if dtype is None:
+            dtype = code
+        elif code != dtype:
+            raise ValueError("all volumes of a batch share one dtype")
+    h = ctypes.c_void_p()
+    _check(lib().mvd_batch_create(ctypes.byref(h), descs, len(volumes), dtype, BOUNDARY[boundary], float(eps),
+                                  ORDER[order]), "mvd_batch_create")
+    return Batch(h.value, keep)
+
+
+def mvd_batch_tune(batch: Batch, stream=None) -> None:
+    import torch
+    s = torch.cuda.current_stream().cuda_stream if stream is None else int(stream)
+    _check(lib().mvd_batch_tune(batch.handle, ctypes.c_void_p(s)), "mvd_batch_tune")
+
+
+def mvd_batch_run(batch: Batch, stream=None) -> None:
+    import torch
+    s = torch.cuda.current_stream().cuda_stream if stream is None else int(stream)
+    _check(lib().mvd_batch_run(batch.handle, ctypes.c_void_p(s)), "mvd_batch_run")
+
+
+def mvd_batch_info(batch: Batch) -> dict:
+    c, m, k = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _check(lib().mvd_batch_info(batch.handle, ctypes.byref(c), ctypes.byref(m), ctypes.byref(k)), "mvd_batch_info")
+    return {"concurrent": c.value, "max_ctas": m.value, "graph_kernels": k.value}
+
+
+def mvd_batch_destroy(batch: Batch) -> None:
+    batch.close()
 
 
 def mvd_launch_count() -> int:

@@ -160,6 +160,15 @@ def volume_stacks(Z: int, Y: int, X: int, K: int, sigma_axial: float,
     psfs, stacks = [], []
     for a in angles:
         psfs.append(gaussian_psf(K, sigma_axial, sigma_lateral, a))
+        if a % 90.0 != 0.0:
+            # oblique view: blur every (z, x) plane with the full 2D PSF
+            ker = torch.as_tensor(psfs[-1], dtype=torch.float32, device=dev).flip(0, 1).reshape(1, 1, K, K)
+            t = truth.permute(1, 0, 2).reshape(Y, 1, Z, X)
+            t = F.conv2d(t, ker, padding=R).reshape(Y, Z, X).permute(1, 0, 2).contiguous().clamp_(min=0)
+            noisy = torch.poisson(t, generator=gen).clamp_(0, 65535)
+            stacks.append(noisy.to(torch.int32).to(torch.uint16))
+            del t, noisy
+            continue
         rot = (a % 180.0) == 90.0
         s_rows, s_cols = (sigma_lateral, sigma_axial) if rot else (sigma_axial, sigma_lateral)
         kr = torch.as_tensor(gaussian_1d(K, s_rows), dtype=torch.float32, device=dev)
@@ -175,3 +184,29 @@ def volume_stacks(Z: int, Y: int, X: int, K: int, sigma_axial: float,
         stacks.append(noisy.to(torch.int32).to(torch.uint16))
         del t, noisy
     return torch.stack(stacks), np.stack(psfs)
+
+
+def uneven_volumes(n: int, seed: int, side=(96, 768), planes=(16, 256), views=(2, 6), psf=(9, 41),
+                   sigma_lateral=(1.0, 2.0), sigma_axial=(4.0, 12.0), iters=(5, 20), density=5e-5,
+                   device="cpu"):
+    """Independent volumes of uneven shape for batched runs.
+
+    Volume i uses seed + i: square planes of side U{side}, U{planes} planes,
+    U{views} views at angles k*180/V degrees, an odd PSF side U{psf},
+    Gaussian sigmas (U(lateral), U(axial)) px and U{iters} iterations.
+    Returns a list of dicts (stacks [V][H][P][W] uint16 on `device`, psfs,
+    iters, shape)."""
+    out = []
+    for i in range(n):
+        rng = np.random.default_rng(seed + i)
+        s = int(rng.integers(side[0], side[1] + 1))
+        p = int(rng.integers(planes[0], planes[1] + 1))
+        v = int(rng.integers(views[0], views[1] + 1))
+        k = int(rng.integers((psf[0] - 1) // 2, (psf[1] - 1) // 2 + 1)) * 2 + 1
+        sl = float(rng.uniform(*sigma_lateral))
+        sa = float(rng.uniform(*sigma_axial))
+        it = int(rng.integers(iters[0], iters[1] + 1))
+        angles = tuple(180.0 * j / v for j in range(v))
+        stacks, psfs = volume_stacks(s, p, s, k, sa, sl, angles, density, seed=seed + i, device=device)
+        out.append({"stacks": stacks, "psfs": psfs, "iters": it, "H": s, "W": s, "P": p, "views": v, "K": k})
+    return out
