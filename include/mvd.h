@@ -78,7 +78,15 @@ typedef enum {
      * Kept as the comparison baseline. */
     MVD_ALGO_PLAIN = 1,
     /* Plain per-plane path with K x K direct convolutions (no factorisation). */
-    MVD_ALGO_DIRECT = 2
+    MVD_ALGO_DIRECT = 2,
+    /* Fourier route (Supp. Note 2 sec. 4): both convolutions as products of
+     * spectra, with the library's own batched mixed-radix FFT and the ratio,
+     * product and update fused into the transforms.  The grid is padded to
+     * the smallest 2^a 3^b 5^c sizes >= H + R and W + R (ZERO boundary) or is
+     * the plane itself (CIRCULAR, whose sides must then be such sizes);
+     * padded sides <= 2048.  Its cost does not grow with K or with the PSFs'
+     * separable rank (oblique views). */
+    MVD_ALGO_FFT = 3
 } mvd_algo;
 
 typedef enum {

@@ -165,6 +165,13 @@ struct mvd_ctx {
     DevBuf grad_ws, grad_acc;            // PSF-gradient workspace (floats) and FP64 sums
     long long wait_budget = mvd::kDefaultWaitBudget;
     int max_ctas = 0;                    // persistent-grid cap set by a batch's tuner
+    // Fourier route: padded grid, radix lists, twiddles, PSF spectra, spectra scratch
+    struct {
+        bool planned = false;
+        int Ly = 0, Lx = 0, Lc = 0, LcP = 0;
+        int rad_x[mvd::fftr::kMaxRadices], nrad_x = 0, rad_y[mvd::fftr::kMaxRadices], nrad_y = 0;
+        DevBuf tw_x, tw_y, spec, S0, T;
+    } fft;
 };
 
 namespace {
@@ -206,11 +213,19 @@ mvd::FusedArgs fused_args(const mvd_ctx *c, const void *data, mvd_dtype dt, floa
     return a;
 }
 
+mvd_status fft_plan(mvd_ctx *c);
+
 // Allocate everything a deconvolution of P planes needs, so that the call
 // itself allocates nothing (required while a stream is being captured).
 cudaError_t prepare_workspace(mvd_ctx *c, int P) {
     const size_t plane_px = static_cast<size_t>(c->H) * c->W;
     cudaError_t e = c->means.ensure(static_cast<size_t>(P) * sizeof(float));
+    if (e == cudaSuccess && c->algo == MVD_ALGO_FFT) {
+        if (fft_plan(c) != MVD_OK) return cudaErrorInvalidValue;
+        const size_t rows = static_cast<size_t>(P) * c->H * c->fft.LcP;
+        e = c->fft.S0.ensure(rows * sizeof(float2));
+        if (e == cudaSuccess) e = c->fft.T.ensure(rows * c->V * sizeof(float2));
+    }
     if (e == cudaSuccess && c->algo == MVD_ALGO_FUSED && mvd::fused_taps_fit(c->ft))
         e = c->ratio.ensure(static_cast<size_t>(c->V) * P * plane_px * sizeof(float));
     if (e == cudaSuccess) e = c->plain.ensure(4 * plane_px * sizeof(float));
@@ -250,6 +265,107 @@ mvd_status run_fused(mvd_ctx *c, const void *data, mvd_dtype dt, float *est, int
             c->prof.mark(s, "correlate_update");
             e = mvd::launch_fused_correlate_update(a, s);
             if (e != cudaSuccess) return cuda_fail(e, "correlate/update kernel");
+        }
+    }
+    c->prof.end(s);
+    return MVD_OK;
+}
+
+// Padded grid of the Fourier route for this context; false if it has none.
+bool fft_grid(const mvd_ctx *c, int *Ly, int *Lx) {
+    const int R = (c->K - 1) / 2;
+    int ly = c->H, lx = c->W;
+    if (c->boundary == MVD_BOUNDARY_ZERO) {
+        if (!mvd::fftr::smooth_size(c->H + R, &ly) || !mvd::fftr::smooth_size(c->W + R, &lx)) return false;
+    }
+    int r[mvd::fftr::kMaxRadices], n = 0;
+    if (!mvd::fftr::radix_list(ly, r, &n) || !mvd::fftr::radix_list(lx, r, &n)) return false;
+    if (ly > mvd::fftr::kMaxLen || lx > mvd::fftr::kMaxLen || ly < 2 || lx < 2) return false;
+    *Ly = ly;
+    *Lx = lx;
+    return true;
+}
+
+// Twiddle tables and PSF spectra (host FP64 transforms) for the Fourier route.
+mvd_status fft_plan(mvd_ctx *c) {
+    if (c->fft.planned) return MVD_OK;
+    auto &f = c->fft;
+    if (!fft_grid(c, &f.Ly, &f.Lx)) return fail(MVD_ERR_UNSUPPORTED, "no Fourier grid for this plane size");
+    f.Lc = f.Lx / 2 + 1;
+    f.LcP = (f.Lc + 7) / 8 * 8;
+    mvd::fftr::radix_list(f.Lx, f.rad_x, &f.nrad_x);
+    mvd::fftr::radix_list(f.Ly, f.rad_y, &f.nrad_y);
+    std::vector<float2> tx, ty, spec, all;
+    mvd::fftr::twiddles(f.Lx, tx);
+    mvd::fftr::twiddles(f.Ly, ty);
+    const size_t per = static_cast<size_t>(f.Ly) * f.LcP;
+    all.resize(per * c->V);
+    for (int v = 0; v < c->V; ++v) {
+        mvd::fftr::psf_spectrum(c->psfs.data() + static_cast<size_t>(v) * c->K * c->K, c->K, f.Ly, f.Lx, f.Lc, f.LcP,
+                                spec);
+        std::copy(spec.begin(), spec.end(), all.begin() + v * per);
+    }
+    cudaError_t e;
+    if ((e = f.tw_x.ensure(tx.size() * sizeof(float2))) != cudaSuccess ||
+        (e = f.tw_y.ensure(ty.size() * sizeof(float2))) != cudaSuccess ||
+        (e = f.spec.ensure(all.size() * sizeof(float2))) != cudaSuccess)
+        return fail(MVD_ERR_NOMEM, "Fourier tables: %s", cudaGetErrorString(e));
+    if ((e = cudaMemcpy(f.tw_x.ptr, tx.data(), tx.size() * sizeof(float2), cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMemcpy(f.tw_y.ptr, ty.data(), ty.size() * sizeof(float2), cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMemcpy(f.spec.ptr, all.data(), all.size() * sizeof(float2), cudaMemcpyHostToDevice)) != cudaSuccess)
+        return cuda_fail(e, "upload Fourier tables");
+    f.planned = true;
+    return MVD_OK;
+}
+
+mvd_status run_fft(mvd_ctx *c, const void *data, mvd_dtype dt, float *est, int P, int init_mean, cudaStream_t s) {
+    mvd_status st = fft_plan(c);
+    if (st != MVD_OK) return st;
+    auto &f = c->fft;
+    const size_t rows = static_cast<size_t>(P) * c->H * f.LcP;
+    cudaError_t e;
+    if ((e = f.S0.ensure(rows * sizeof(float2))) != cudaSuccess ||
+        (e = f.T.ensure(rows * c->V * sizeof(float2))) != cudaSuccess)
+        return fail(MVD_ERR_NOMEM, "Fourier workspace: %s", cudaGetErrorString(e));
+    const size_t plane_px = static_cast<size_t>(c->H) * c->W;
+    if (c->iters == 0 && init_mean) {
+        for (int p = 0; p < P; ++p)
+            if ((e = mvd::plain_fill(est + p * plane_px, c->means.as<float>(), p, plane_px, s)) != cudaSuccess)
+                return cuda_fail(e, "fill");
+        return MVD_OK;
+    }
+    mvd::fftr::FftArgs a{};
+    a.Ly = f.Ly;
+    a.Lx = f.Lx;
+    a.Lc = f.Lc;
+    a.LcP = f.LcP;
+    std::copy(f.rad_x, f.rad_x + f.nrad_x, a.rad_x);
+    std::copy(f.rad_y, f.rad_y + f.nrad_y, a.rad_y);
+    a.nrad_x = f.nrad_x;
+    a.nrad_y = f.nrad_y;
+    a.tw_x = f.tw_x.as<float2>();
+    a.tw_y = f.tw_y.as<float2>();
+    a.spec = f.spec.as<float2>();
+    a.H = c->H;
+    a.W = c->W;
+    a.P = P;
+    a.eps = c->eps;
+    a.means = c->means.as<float>();
+    a.psi_out = est;
+    a.phi = data;
+    a.u16 = dt == MVD_U16;
+    a.S0 = f.S0.as<float2>();
+    a.T = f.T.as<float2>();
+    const int step = c->order == MVD_ORDER_SEQUENTIAL ? 1 : c->V;
+    bool first = init_mean != 0;
+    for (int t = 0; t < c->iters; ++t) {
+        for (int v0 = 0; v0 < c->V; v0 += step) {
+            a.view_lo = v0;
+            a.view_hi = v0 + step;
+            a.psi_in = first ? nullptr : est;
+            first = false;
+            c->prof.mark(s, "fft_iteration");
+            if ((e = mvd::fftr::launch_iteration(a, s)) != cudaSuccess) return cuda_fail(e, "Fourier kernels");
         }
     }
     c->prof.end(s);
@@ -339,6 +455,7 @@ mvd_status mvd_set_psfs(mvd_ctx *c, const float *psfs) {
     }
     DeviceGuard g(c->device);
     c->psfs.assign(psfs, psfs + c->V * KK);
+    c->fft.planned = false;   // the PSF spectra change with the PSFs
     if (c->psf_dev.ptr) {
         cudaError_t e = cudaMemcpy(c->psf_dev.ptr, c->psfs.data(), c->psfs.size() * sizeof(float), cudaMemcpyHostToDevice);
         if (e != cudaSuccess) return cuda_fail(e, "upload psfs");
@@ -587,6 +704,11 @@ mvd_status mvd_destroy(mvd_ctx *c) {
     c->status.release();
     c->grad_ws.release();
     c->grad_acc.release();
+    c->fft.tw_x.release();
+    c->fft.tw_y.release();
+    c->fft.spec.release();
+    c->fft.S0.release();
+    c->fft.T.release();
     if (c->copy_in) cudaStreamDestroy(c->copy_in);
     if (c->copy_out) cudaStreamDestroy(c->copy_out);
     delete c;
@@ -595,10 +717,16 @@ mvd_status mvd_destroy(mvd_ctx *c) {
 
 mvd_status mvd_set_algo(mvd_ctx *c, mvd_algo algo) {
     if (!c) return fail(MVD_ERR_ARG, "ctx is NULL");
-    if (algo != MVD_ALGO_FUSED && algo != MVD_ALGO_PLAIN && algo != MVD_ALGO_DIRECT)
+    if (algo != MVD_ALGO_FUSED && algo != MVD_ALGO_PLAIN && algo != MVD_ALGO_DIRECT && algo != MVD_ALGO_FFT)
         return fail(MVD_ERR_ARG, "unknown algo %d", static_cast<int>(algo));
     if (algo == MVD_ALGO_FUSED && !(mvd::fused_supported(c->K) && mvd::fused_taps_fit(c->ft)))
         return fail(MVD_ERR_UNSUPPORTED, "fused path takes K <= %d (got %d)", mvd::kFusedMaxK, c->K);
+    if (algo == MVD_ALGO_FFT) {
+        int ly, lx;
+        if (!fft_grid(c, &ly, &lx))
+            return fail(MVD_ERR_UNSUPPORTED, "no Fourier grid: padded sides must be 2^a 3^b 5^c and <= %d",
+                        mvd::fftr::kMaxLen);
+    }
     c->algo = algo;
     return MVD_OK;
 }
@@ -691,6 +819,7 @@ mvd_status mvd_deconvolve_planes(mvd_ctx *c, const void *data, mvd_dtype dt, flo
     // more separable terms than it holds run on the plain path
     if (c->algo == MVD_ALGO_FUSED && mvd::fused_taps_fit(c->ft))
         return run_fused(c, data, dt, est, n_planes, init_mean, s);
+    if (c->algo == MVD_ALGO_FFT) return run_fft(c, data, dt, est, n_planes, init_mean, s);
     return run_plain(c, data, dt, est, n_planes, init_mean, c->algo == MVD_ALGO_DIRECT, s);
 }
 

@@ -4,6 +4,7 @@
 
 #include <cstddef>
 #include <cstdint>
+#include <vector>
 #include <cuda_runtime.h>
 
 namespace mvd {
@@ -80,6 +81,32 @@ bool fused_taps_fit(const FactorTable &ft);
 void fused_tile_shape(int K, int *tile_h, int *tile_w);
 cudaError_t launch_fused_blur_ratio(const FusedArgs &a, cudaStream_t s);
 cudaError_t launch_fused_correlate_update(const FusedArgs &a, cudaStream_t s);
+
+// Fourier route (fft.cu).
+namespace fftr {
+constexpr int kMaxRadices = 16;
+constexpr int kMaxLen = 2048;          // largest padded side
+struct FftArgs {
+    int Ly, Lx, Lc, LcP;               // padded grid, half-spectrum columns and their pitch
+    int rad_x[kMaxRadices], nrad_x, rad_y[kMaxRadices], nrad_y;
+    const float2 *tw_x, *tw_y;         // exp(+2 pi i k / L) tables
+    const float2 *spec;                // [V][Ly][LcP] PSF spectra / (Ly Lx)
+    int H, W, P, view_lo, view_hi;
+    float eps;
+    const float *psi_in;               // nullptr: constant first estimate (means)
+    const float *means;
+    float *psi_out;
+    const void *phi;
+    int u16;
+    float2 *S0;                        // [P][H][LcP]
+    float2 *T;                         // [V][P][H][LcP]
+};
+bool smooth_size(int n, int *out);
+bool radix_list(int n, int *rad, int *nrad);
+void twiddles(int N, std::vector<float2> &out);
+void psf_spectrum(const float *psf, int K, int Ly, int Lx, int Lc, int LcP, std::vector<float2> &out);
+cudaError_t launch_iteration(const FftArgs &a, cudaStream_t s);
+}  // namespace fftr
 
 // PSF-gradient building blocks (adjoint.cu); every call covers P planes.
 namespace adj {
