@@ -140,6 +140,15 @@ mvd_status mvd_set_algo(mvd_ctx *ctx, mvd_algo algo);
 /* Select how the views combine within one iteration (default simultaneous). */
 mvd_status mvd_set_update_order(mvd_ctx *ctx, mvd_update_order order);
 
+/* Pick the context's route by timing: every route that can take its PSFs
+ * and plane (the fused separable kernels, the Fourier route) runs twice on
+ * the first min(n_planes, 8) planes of data_dev [V][n_planes][H][W] and the
+ * faster is kept.  Without tuning a context starts on the fused kernels when
+ * the PSFs' separable terms fit them, else on the Fourier route.  With
+ * MVD_TUNE_CACHE naming a file, choices are cached there by shape.  Uses
+ * temporary device buffers; waits for `stream`. */
+mvd_status mvd_autotune(mvd_ctx *ctx, const void *data_dev, mvd_dtype dt, int n_planes, void *stream);
+
 /* Relative Frobenius tolerance below which trailing SVD terms of a PSF are
  * dropped (default 3e-7, below the FP32 rounding of the PSF's entries).
  * 0 keeps every non-zero term. */

@@ -46,6 +46,10 @@ mvd_status cuda_fail(cudaError_t e, const char *what) {
     return fail(MVD_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
 }
 
+// Tuning cache (MVD_TUNE_CACHE): lines "<key> <a> <b>".
+bool tune_cache_lookup(const std::string &key, int *a, int *b);
+void tune_cache_store(const std::string &key, int a, int b);
+
 struct DeviceGuard {
     int prev = -1, want;
     explicit DeviceGuard(int d) : want(d) {
@@ -685,7 +689,88 @@ mvd_status mvd_create(mvd_ctx **out, int views, const float *psfs_host, int psf_
         mvd_destroy(c);
         return s;
     }
+    // default route: the fused separable kernels when the PSFs' terms fit
+    // them, else the Fourier route when the plane has a grid, else plain
+    int ly, lx;
+    if (!(c->algo == MVD_ALGO_FUSED && mvd::fused_taps_fit(c->ft)))
+        c->algo = fft_grid(c, &ly, &lx) ? MVD_ALGO_FFT : MVD_ALGO_PLAIN;
     *out = c;
+    return MVD_OK;
+}
+
+mvd_status mvd_autotune(mvd_ctx *c, const void *data, mvd_dtype dt, int n_planes, void *stream) {
+    t_last_error.clear();
+    if (!c || !data) return fail(MVD_ERR_ARG, "NULL argument");
+    if (dt != MVD_U16 && dt != MVD_F32) return fail(MVD_ERR_ARG, "unknown dtype");
+    if (n_planes < 1) return fail(MVD_ERR_ARG, "n_planes must be >= 1");
+    DeviceGuard g(c->device);
+    char key[256];
+    std::snprintf(key, sizeof key, "route_v%d_k%d_%dx%d_t%d_b%d_o%d_r%d", c->V, c->K, c->H, c->W, c->iters,
+                  static_cast<int>(c->boundary), static_cast<int>(c->order), c->ft.total_terms);
+    int cached = -1, unused = 0;
+    if (tune_cache_lookup(key, &cached, &unused) && cached >= 0) {
+        c->algo = static_cast<mvd_algo>(cached);
+        return MVD_OK;
+    }
+    int ly, lx;
+    std::vector<mvd_algo> cand;
+    if (mvd::fused_supported(c->K) && mvd::fused_taps_fit(c->ft)) cand.push_back(MVD_ALGO_FUSED);
+    if (fft_grid(c, &ly, &lx)) cand.push_back(MVD_ALGO_FFT);
+    if (cand.empty()) cand.push_back(MVD_ALGO_PLAIN);
+    if (cand.size() == 1) {
+        c->algo = cand[0];
+        return MVD_OK;
+    }
+    const int P = std::min(n_planes, 8);
+    const size_t plane_px = static_cast<size_t>(c->H) * c->W;
+    DevBuf est;
+    cudaError_t e = est.ensure(static_cast<size_t>(P) * plane_px * sizeof(float));
+    if (e != cudaSuccess) return fail(MVD_ERR_NOMEM, "autotune buffer: %s", cudaGetErrorString(e));
+    // the first P planes of every view: planes are contiguous per view, so a
+    // sub-batch needs its own copy of the data
+    const size_t es = dt == MVD_U16 ? 2 : 4;
+    DevBuf sub;
+    if ((e = sub.ensure(static_cast<size_t>(c->V) * P * plane_px * es)) != cudaSuccess) {
+        est.release();
+        return fail(MVD_ERR_NOMEM, "autotune buffer: %s", cudaGetErrorString(e));
+    }
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    for (int v = 0; v < c->V; ++v)
+        cudaMemcpyAsync(sub.as<char>() + static_cast<size_t>(v) * P * plane_px * es,
+                        static_cast<const char *>(data) + static_cast<size_t>(v) * n_planes * plane_px * es,
+                        P * plane_px * es, cudaMemcpyDeviceToDevice, s);
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    const mvd_algo keep = c->algo;
+    float best = 1e30f;
+    mvd_algo best_a = keep;
+    mvd_status st = MVD_OK;
+    for (mvd_algo a : cand) {
+        c->algo = a;
+        if ((st = mvd_deconvolve_planes(c, sub.ptr, dt, est.as<float>(), P, 1, s)) != MVD_OK) break;   // warm
+        cudaEventRecord(e0, s);
+        if ((st = mvd_deconvolve_planes(c, sub.ptr, dt, est.as<float>(), P, 1, s)) != MVD_OK) break;
+        cudaEventRecord(e1, s);
+        cudaEventSynchronize(e1);
+        float ms = 0;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best) {
+            best = ms;
+            best_a = a;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaStreamSynchronize(s);
+    est.release();
+    sub.release();
+    if (st != MVD_OK) {
+        c->algo = keep;
+        return st;
+    }
+    c->algo = best_a;
+    tune_cache_store(key, static_cast<int>(best_a), 0);
     return MVD_OK;
 }
 
@@ -1111,6 +1196,25 @@ mvd_status mvd_batch_tune(mvd_batch *b, void *stream) {
     t_last_error.clear();
     if (!b) return fail(MVD_ERR_ARG, "batch is NULL");
     DeviceGuard g(b->device);
+    cudaStream_t s0 = static_cast<cudaStream_t>(stream);
+    // 1. the route of every volume (fused separable kernels or Fourier route),
+    //    timed on its own data; volumes given as stacks are resliced first
+    {
+        mvd_status st = b->exec ? MVD_OK : batch_capture(b);
+        if (st != MVD_OK) return st;
+        cudaGraphLaunch(b->exec, s0);
+        cudaError_t e = cudaStreamSynchronize(s0);
+        if (e != cudaSuccess) return cuda_fail(e, "batch run before tuning");
+        for (size_t i = 0; i < b->vols.size(); ++i) {
+            const mvd_volume_desc &v = b->vols[i];
+            const void *data = v.stacks_dev ? b->planes[i].ptr : v.planes_dev;
+            if ((st = mvd_autotune(b->ctx[i], data, b->dt, v.n_planes, stream)) != MVD_OK) return st;
+            if ((e = prepare_workspace(b->ctx[i], v.n_planes)) != cudaSuccess)
+                return fail(MVD_ERR_NOMEM, "volume %zu workspace: %s", i, cudaGetErrorString(e));
+        }
+        batch_drop_graph(b);
+    }
+    // 2. the launch shape
     int conc = 1, ctas = 0;
     if (tune_cache_lookup(b->key, &conc, &ctas)) {
         b->concurrent = conc;

@@ -69,6 +69,7 @@ def lib() -> ctypes.CDLL:
     L.mvd_device_status.argtypes = [vp, vp]
     L.mvd_psf_grad.argtypes = [vp, vp, i, i, i, ctypes.POINTER(d), vp, vp, vp]
     L.mvd_set_psfs.argtypes = [vp, vp]
+    L.mvd_autotune.argtypes = [vp, vp, i, i, vp]
     L.mvd_batch_create.argtypes = [ctypes.POINTER(vp), vp, i, i, i, f, i]
     L.mvd_batch_tune.argtypes = [vp, vp]
     L.mvd_batch_run.argtypes = [vp, vp]
@@ -91,7 +92,7 @@ def lib() -> ctypes.CDLL:
     L.mvd_launch_count.restype = ctypes.c_uint64
     for name in ("mvd_create", "mvd_destroy", "mvd_set_algo", "mvd_set_rank_tolerance", "mvd_get_info",
                  "mvd_set_update_order", "mvd_device_status", "mvd_set_wait_budget",
-                 "mvd_deconvolve_planes_static", "mvd_psf_grad", "mvd_set_psfs",
+                 "mvd_deconvolve_planes_static", "mvd_psf_grad", "mvd_set_psfs", "mvd_autotune",
                  "mvd_batch_create", "mvd_batch_tune", "mvd_batch_run", "mvd_batch_info", "mvd_batch_destroy",
                  "mvd_reslice", "mvd_deconvolve_planes", "mvd_run_host", "mvd_psf_factors",
                  "mvd_profile_enable", "mvd_profile_read"):
@@ -196,6 +197,16 @@ def mvd_destroy(ctx: Context) -> None:
 
 def mvd_set_algo(ctx: Context, algo: str) -> None:
     _check(lib().mvd_set_algo(ctx.handle, ALGO[algo]), "mvd_set_algo")
+
+
+def mvd_autotune(ctx: Context, data, stream=None) -> str:
+    """Time the routes that can take this context's PSFs on `data` and keep
+    the fastest; returns its name."""
+    _require_cuda(data)
+    _check(lib().mvd_autotune(ctx.handle, ctypes.c_void_p(data.data_ptr()), _dtype_code(data), data.shape[1],
+                              _stream_of(data, stream)), "mvd_autotune")
+    algo = mvd_get_info(ctx).algo
+    return {v: k for k, v in ALGO.items()}[algo]
 
 
 def mvd_set_update_order(ctx: Context, order: str) -> None:

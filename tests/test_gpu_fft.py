@@ -87,3 +87,24 @@ def test_given_start_and_agreement_with_fused(mvd):
     psi0 = np.full((2, 64, 96), 30.0, np.float32)
     ref = oracle.rl_planes(c.phi, c.psfs, 3, psi0=psi0.astype(np.float64))
     assert_parity(run_fft(mvd, c.phi, c.psfs, 3, psi0=psi0), ref, what="fft psi0")
+
+
+def test_autotune_picks_a_route_and_keeps_parity(mvd, tmp_path, monkeypatch):
+    monkeypatch.setenv("MVD_TUNE_CACHE", str(tmp_path / "tune.txt"))
+    c = synth.plane_case(seed=11, H=160, W=160, n_planes=4, n_blobs=50, K=31, sigma_axial=8.0,
+                         sigma_lateral=1.5, angles=(0, 45), dtype=np.uint16)
+    V, P, H, W = c.phi.shape
+    ctx = mvd.mvd_create(V, c.psfs, 31, H, W, 4, "zero", 1e-6)
+    try:
+        d = torch.from_numpy(c.phi).cuda()
+        route = mvd.mvd_autotune(ctx, d)
+        assert route in ("fused", "fft")
+        assert "route_" in (tmp_path / "tune.txt").read_text()
+        assert mvd.mvd_autotune(ctx, d) == route          # from the cache
+        est = torch.empty((P, H, W), device="cuda")
+        mvd.mvd_deconvolve_planes(ctx, d, est)
+        torch.cuda.synchronize()
+    finally:
+        ctx.close()
+    ref = oracle.rl_planes(c.phi, c.psfs, 4, eps=1e-6, route="fft")
+    assert_parity(est.cpu().numpy(), ref, what=f"autotuned ({route})")
