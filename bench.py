@@ -178,11 +178,8 @@ def barrier(world):
 def reduce_max(x, world):
     if world == 1:
         return x
-    import torch
-    import torch.distributed as dist
-    t = torch.tensor([float(x)], device="cuda" if torch.cuda.is_available() else "cpu")
-    dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    return float(t.item())
+    from paper_1503_07998_gb300 import shard
+    return shard.max_over_ranks(x)
 
 
 def make_inputs(wl, seed, device):

@@ -50,44 +50,90 @@ __device__ __forceinline__ float2 twid(const float2 *tw, int e, int N) {
     return INV ? t : make_float2(t.x, -t.y);
 }
 
-// One transform of length N over x (input) / y (scratch): radix stages of
-// the Stockham autosort; threads `lane` .. step `nl` of a group share it.
-// Returns the buffer that holds the result.  Every thread of the CTA must
-// call it with the same N and radix list (the stages synchronise the CTA).
+// -i*d (forward) or +i*d (inverse)
+template <bool INV>
+__device__ __forceinline__ float2 rot(float2 d) {
+    return INV ? make_float2(-d.y, d.x) : make_float2(d.y, -d.x);
+}
+
+// Size-R DFT in registers, exponent sign -1 (forward) or +1 (inverse).  The
+// constants are cos/sin of 2 pi/3, 2 pi/5 and 4 pi/5.
+template <int R, bool INV>
+__device__ __forceinline__ void small_dft(float2 (&a)[R]) {
+    if (R == 2) {
+        const float2 s = cadd(a[0], a[1]), d = csub(a[0], a[1]);
+        a[0] = s;
+        a[1] = d;
+    } else if (R == 4) {
+        const float2 s02 = cadd(a[0], a[2]), d02 = csub(a[0], a[2]);
+        const float2 s13 = cadd(a[1], a[3]), d13 = rot<INV>(csub(a[1], a[3]));
+        a[0] = cadd(s02, s13);
+        a[1] = cadd(d02, d13);
+        a[2] = csub(s02, s13);
+        a[3] = csub(d02, d13);
+    } else if (R == 3) {
+        constexpr float s3 = 0.8660254037844386f;       // sin(2 pi / 3)
+        const float2 t1 = cadd(a[1], a[2]);
+        const float2 t2 = rot<INV>(csub(a[1], a[2]));
+        const float2 m = make_float2(a[0].x - 0.5f * t1.x, a[0].y - 0.5f * t1.y);
+        a[0] = cadd(a[0], t1);
+        a[1] = make_float2(m.x + s3 * t2.x, m.y + s3 * t2.y);
+        a[2] = make_float2(m.x - s3 * t2.x, m.y - s3 * t2.y);
+    } else if (R == 5) {
+        constexpr float c1 = 0.30901699437494745f, c2 = -0.8090169943749475f;   // cos(2pi/5), cos(4pi/5)
+        constexpr float s1 = 0.9510565162951535f, s2 = 0.5877852522924731f;     // sin(2pi/5), sin(4pi/5)
+        const float2 t1 = cadd(a[1], a[4]), t2 = cadd(a[2], a[3]);
+        const float2 t3 = csub(a[1], a[4]), t4 = csub(a[2], a[3]);
+        const float2 b1 = make_float2(a[0].x + c1 * t1.x + c2 * t2.x, a[0].y + c1 * t1.y + c2 * t2.y);
+        const float2 b2 = make_float2(a[0].x + c2 * t1.x + c1 * t2.x, a[0].y + c2 * t1.y + c1 * t2.y);
+        const float2 d1 = rot<INV>(make_float2(s1 * t3.x + s2 * t4.x, s1 * t3.y + s2 * t4.y));
+        const float2 d2 = rot<INV>(make_float2(s2 * t3.x - s1 * t4.x, s2 * t3.y - s1 * t4.y));
+        a[0] = cadd(a[0], cadd(t1, t2));
+        a[1] = cadd(b1, d1);
+        a[4] = csub(b1, d1);
+        a[2] = cadd(b2, d2);
+        a[3] = csub(b2, d2);
+    }
+}
+
+// One radix-R stage of the Stockham autosort: p = product of the radices
+// before it.  q*k*stride < N, so the twiddle index needs no reduction.
+template <int R, bool INV>
+__device__ __forceinline__ void fft_stage(const float2 *__restrict__ x, float2 *__restrict__ y, int N, int p,
+                                          const float2 *tw, int lane, int nl) {
+    const int M = N / R, stride = N / (p * R);
+    for (int i = lane; i < M; i += nl) {
+        const int k = i % p;
+        float2 a[R];
+#pragma unroll
+        for (int q = 0; q < R; ++q) a[q] = x[i + q * M];
+#pragma unroll
+        for (int q = 1; q < R; ++q) {
+            const float2 t = tw[q * k * stride];
+            a[q] = cmul(a[q], INV ? t : make_float2(t.x, -t.y));
+        }
+        small_dft<R, INV>(a);
+        const int j = (i - k) * R + k;
+#pragma unroll
+        for (int m = 0; m < R; ++m) y[j + m * p] = a[m];
+    }
+}
+
+// One transform of length N over x (input) / y (scratch); threads `lane` ..
+// step `nl` of a group share it.  Returns the buffer that holds the result.
+// Every thread of the CTA must call it with the same N and radix list (the
+// stages synchronise the CTA).
 template <bool INV>
 __device__ float2 *fft_group(float2 *x, float2 *y, int N, const int *rad, int nrad, const float2 *tw, int lane,
                              int nl) {
     int p = 1;
     for (int s = 0; s < nrad; ++s) {
-        const int R = rad[s], M = N / R, stride = N / (p * R);
-        for (int i = lane; i < M; i += nl) {
-            const int k = i % p;
-            float2 a[5];
-            for (int q = 0; q < R; ++q) a[q] = x[i + q * M];
-            for (int q = 1; q < R; ++q) a[q] = cmul(a[q], twid<INV>(tw, q * k * stride, N));
-            float2 o[5];
-            if (R == 2) {
-                o[0] = cadd(a[0], a[1]);
-                o[1] = csub(a[0], a[1]);
-            } else if (R == 4) {
-                const float2 s02 = cadd(a[0], a[2]), d02 = csub(a[0], a[2]);
-                const float2 s13 = cadd(a[1], a[3]), d13 = csub(a[1], a[3]);
-                // -i * d13 (forward) or +i * d13 (inverse)
-                const float2 rot = INV ? make_float2(-d13.y, d13.x) : make_float2(d13.y, -d13.x);
-                o[0] = cadd(s02, s13);
-                o[1] = cadd(d02, rot);
-                o[2] = csub(s02, s13);
-                o[3] = csub(d02, rot);
-            } else {
-                const int base = N / R;
-                for (int m = 0; m < R; ++m) {
-                    float2 acc = a[0];
-                    for (int q = 1; q < R; ++q) acc = cadd(acc, cmul(a[q], twid<INV>(tw, q * m * base, N)));
-                    o[m] = acc;
-                }
-            }
-            const int j = (i / p) * p * R + k;
-            for (int m = 0; m < R; ++m) y[j + m * p] = o[m];
+        const int R = rad[s];
+        switch (R) {
+            case 4: fft_stage<4, INV>(x, y, N, p, tw, lane, nl); break;
+            case 2: fft_stage<2, INV>(x, y, N, p, tw, lane, nl); break;
+            case 3: fft_stage<3, INV>(x, y, N, p, tw, lane, nl); break;
+            default: fft_stage<5, INV>(x, y, N, p, tw, lane, nl); break;
         }
         __syncthreads();
         float2 *t = x;

@@ -244,6 +244,33 @@ def test_launch_count_and_errors(mvd):
         ctx.close()
 
 
+def test_volume_1024_cubed_four_views_sampled_planes(mvd):
+    """Four views of 1024^3 uint16 blobs (density 5e-5) at 0/90/180/270
+    degrees with 41x41 PSFs sigma (1.8, 10), resliced on the GPU, 10
+    iterations in sequential order over all 1024 planes; sampled planes
+    against the FP64 oracle."""
+    stacks, psfs = synth.volume_stacks(1024, 1024, 1024, 41, 10.0, 1.8, (0, 90, 180, 270), 5e-5, seed=0,
+                                       device=DEV)
+    V, Z, Y, X = stacks.shape
+    ctx = mvd.mvd_create(V, psfs, 41, Z, X, 10, "zero", 1e-6)
+    try:
+        mvd.mvd_set_update_order(ctx, "sequential")
+        assert mvd.mvd_get_info(ctx).algo == mvd.ALGO["fused"]
+        planes = torch.empty((V, Y, Z, X), dtype=stacks.dtype, device=DEV)
+        mvd.mvd_reslice(ctx, stacks, planes)
+        del stacks
+        est = torch.empty((Y, Z, X), dtype=torch.float32, device=DEV)
+        mvd.mvd_deconvolve_planes(ctx, planes, est)
+        torch.cuda.synchronize()
+        mvd.mvd_device_status(ctx)
+    finally:
+        ctx.close()
+    sample = [3, 700]
+    phi = np.stack([planes[:, i].cpu().numpy() for i in sample], axis=1)
+    ref = oracle.rl_planes(phi, psfs, 10, eps=1e-6, route="fft", order="sequential")
+    assert_parity(est[sample].cpu().numpy(), ref, what="1024^3 4 views sampled planes")
+
+
 def test_volume_512_cubed_two_views_sampled_planes(mvd):
     """The benchmarked workload in its launch configuration: 2 views of
     512^3 uint16 blobs (density 1e-4), 31x31 PSFs sigma (1.5, 8) turned by 90
