@@ -58,7 +58,12 @@ def test_uneven_batch_matches_single_volumes_and_oracle(mvd, tune, tmp_path, mon
         assert mvd.mvd_launch_count() - n0 == 2 * info["graph_kernels"]
         for v, e in zip(vols, ests):
             want, planes = single(mvd, v, order)
-            np.testing.assert_array_equal(e.cpu().numpy(), want)
+            if tune:
+                # the tuner may pick another route than a context's default:
+                # equal up to FP32 rounding
+                assert_parity(e.cpu().numpy(), want, what="tuned batch vs single context")
+            else:
+                np.testing.assert_array_equal(e.cpu().numpy(), want)
             p = v["P"] // 2
             phi = planes[:, p].cpu().numpy()[:, None]
             ref = oracle.rl_planes(phi, v["psfs"], v["iters"], eps=1e-6, order=order)
