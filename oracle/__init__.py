@@ -11,6 +11,7 @@ Modules
 rl       the forward method (Supp. Note 1, update equation; Fig. 1a reslicing)
 adjoint  reverse-mode gradient of a Poisson data fit through unrolled
          iterations with respect to the PSFs (PSF calibration)
+variants correlation kernels X_v of the MV-RL variants (Supp. Note 2 sec. 1)
 
 Every function is pinned by ``tests/test_oracle.py`` against brute force,
 library routines, closed forms and invariants; none is "parity unpinned".
@@ -28,3 +29,4 @@ from .rl import (  # noqa: F401
     reslice,
 )
 from .adjoint import poisson_nll, rl_loss, rl_loss_and_psf_grad  # noqa: F401
+from .variants import VARIANTS, correlation_kernels  # noqa: F401

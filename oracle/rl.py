@@ -150,7 +150,7 @@ def init_mean(phi: np.ndarray) -> np.ndarray:
 
 
 def rl_step(psi, phi_planes, psfs, boundary=ZERO, eps=1e-6, route="direct",
-            order="simultaneous"):
+            order="simultaneous", corr_kernels=None):
     """One MV-RL update of one plane (Supp. Note 1, update equation).
 
     psi: [H][W]; phi_planes: [V][H][W]; psfs: [V][K][K].
@@ -164,12 +164,19 @@ def rl_step(psi, phi_planes, psfs, boundary=ZERO, eps=1e-6, route="direct",
     """
     conv = convolve if route == "direct" else convolve_fft
     corr = correlate if route == "direct" else correlate_fft
+    if corr_kernels is not None:
+        # variant kernels X_v (Supp. Note 2 sec. 1): the ratio is convolved with
+        # X_v, i.e. correlated with its flip
+        xs = [flip_psf(x) for x in corr_kernels]
+        corr_of = lambda img, v, b: corr(img, xs[v], b)  # noqa: E731
+    else:
+        corr_of = lambda img, v, b: corr(img, psfs[v], b)  # noqa: E731
     psi = np.asarray(psi, dtype=np.float64)
     if order == "sequential":
         for v in range(len(psfs)):
             blur = conv(psi, psfs[v], boundary)
             ratio = np.asarray(phi_planes[v], dtype=np.float64) / np.maximum(blur, eps)
-            psi = psi * corr(ratio, psfs[v], boundary)
+            psi = psi * corr_of(ratio, v, boundary)
         return psi
     if order != "simultaneous":
         raise ValueError(f"unknown update order {order!r}")
@@ -177,12 +184,12 @@ def rl_step(psi, phi_planes, psfs, boundary=ZERO, eps=1e-6, route="direct",
     for v in range(len(psfs)):
         blur = conv(psi, psfs[v], boundary)
         ratio = np.asarray(phi_planes[v], dtype=np.float64) / np.maximum(blur, eps)
-        update *= corr(ratio, psfs[v], boundary)
+        update *= corr_of(ratio, v, boundary)
     return psi * update
 
 
 def rl_planes(phi, psfs, iters, boundary=ZERO, eps=1e-6, psi0=None,
-              route="direct", planes=None, order="simultaneous"):
+              route="direct", planes=None, order="simultaneous", corr_kernels=None):
     """Plane-wise MV-RL over a stack of planes.
 
     phi:  [V][P][H][W] data (any real dtype; used as FP64)
@@ -191,6 +198,9 @@ def rl_planes(phi, psfs, iters, boundary=ZERO, eps=1e-6, psi0=None,
     planes: optional iterable of plane indices to compute (others skipped;
             the result then holds only those planes, in that order)
     order:  "simultaneous" (default, as printed) or "sequential" (see rl_step)
+    corr_kernels: optional [V][K][K] kernels X_v of a variant (oracle.variants);
+            the ratio of view v is then convolved with X_v instead of being
+            correlated with P_v
     Returns the estimate after ``iters`` updates, FP64 [n][H][W].
     """
     phi = np.asarray(phi)
@@ -207,7 +217,7 @@ def rl_planes(phi, psfs, iters, boundary=ZERO, eps=1e-6, psi0=None,
         else:
             psi = np.asarray(psi0[p], dtype=np.float64).copy()
         for _ in range(iters):
-            psi = rl_step(psi, phi[:, p], psfs, boundary, eps, route, order)
+            psi = rl_step(psi, phi[:, p], psfs, boundary, eps, route, order, corr_kernels)
         out[n] = psi
     return out
 

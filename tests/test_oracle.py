@@ -298,3 +298,91 @@ def test_sequential_order_matches_textbook_and_conserves_last_view_flux(boundary
     np.testing.assert_allclose(out[0].ravel(), psi, rtol=1e-12)
     one = oracle.rl_planes(phi[:1], psfs[:1], 3, boundary=boundary, order="sequential")
     np.testing.assert_allclose(one, oracle.rl_planes(phi[:1], psfs[:1], 3, boundary=boundary), rtol=1e-14)
+
+
+def brute_conv_same(A, B):
+    """c[i, j] = sum_{a,b} A[a, b] B[i+R-a, j+R-b] over in-range indices."""
+    K = A.shape[0]
+    R = (K - 1) // 2
+    c = np.zeros((K, K))
+    for i in range(K):
+        for j in range(K):
+            for a in range(K):
+                for b in range(K):
+                    m, n = i + R - a, j + R - b
+                    if 0 <= m < K and 0 <= n < K:
+                        c[i, j] += A[a, b] * B[m, n]
+    return c
+
+
+def test_variant_kernels_brute_force():
+    """Each X_v written out with loops from its definition (Supp. Note 2
+    sec. 1, readings in oracle.variants) on random non-symmetric PSFs."""
+    rng = np.random.default_rng(13)
+    V, K = 3, 5
+    psfs = rng.random((V, K, K)) + 0.05
+    fl = psfs[:, ::-1, ::-1]
+    for variant in oracle.VARIANTS:
+        X = oracle.correlation_kernels(psfs, variant)
+        for v in range(V):
+            x = fl[v].copy()
+            for w in range(V):
+                if w == v:
+                    continue
+                if variant == "efficient_bayesian":
+                    x = x * brute_conv_same(brute_conv_same(fl[v], psfs[w]), fl[w])
+                elif variant == "optimization_1":
+                    x = x * brute_conv_same(fl[v], psfs[w])
+                elif variant == "optimization_2":
+                    x = x * fl[w]
+            np.testing.assert_allclose(X[v], x / x.sum(), rtol=1e-12, err_msg=variant)
+
+
+def test_variant_kernels_gaussian_closed_form():
+    """Isotropic Gaussians (sigma_1, sigma_2), wide support: convolutions add
+    variances and products add precisions, so X_1 of each variant is a
+    Gaussian of known width."""
+    K, s1, s2 = 41, 1.6, 2.2
+    r = np.arange(K) - (K - 1) / 2
+    r2 = r[:, None] ** 2 + r[None, :] ** 2
+
+    def g(s):
+        e = np.exp(-r2 / (2 * s * s))
+        return e / e.sum()
+
+    psfs = np.stack([g(s1), g(s2)])
+    widths = {
+        "independent": [s1 * s1],
+        "efficient_bayesian": [s1 * s1, s1 * s1 + 2 * s2 * s2],
+        "optimization_1": [s1 * s1, s1 * s1 + s2 * s2],
+        "optimization_2": [s1 * s1, s2 * s2],
+    }
+    for variant, variances in widths.items():
+        var = 1.0 / sum(1.0 / q for q in variances)
+        X = oracle.correlation_kernels(psfs, variant)
+        np.testing.assert_allclose(X[0], g(np.sqrt(var)), atol=1e-9, err_msg=variant)
+
+
+@pytest.mark.parametrize("variant", ["efficient_bayesian", "optimization_1", "optimization_2"])
+def test_variants_single_view_delta_and_fixed_point(variant):
+    """One view: every variant is plain RL.  Delta PSFs: X = delta.  Noise-free
+    circular data: psi stays a fixed point (X_v has unit sum)."""
+    rng = np.random.default_rng(14)
+    phi1 = rng.uniform(1, 30, size=(1, 2, 9, 8))
+    P1 = rng.random((1, 5, 5)) + 0.1
+    X1 = oracle.correlation_kernels(P1, variant)
+    np.testing.assert_allclose(X1[0], P1[0, ::-1, ::-1] / P1[0].sum(), rtol=1e-14)
+    P1n = P1 / P1.sum()
+    np.testing.assert_allclose(oracle.rl_planes(phi1, P1n, 3, corr_kernels=X1), oracle.rl_planes(phi1, P1n, 3),
+                               rtol=1e-13)
+    delta = np.zeros((3, 5, 5))
+    delta[:, 2, 2] = 1.0
+    np.testing.assert_allclose(oracle.correlation_kernels(delta, variant), delta, atol=0)
+    psi_true = rng.uniform(10, 100, size=(16, 12))
+    psfs = np.stack([synth.gaussian_psf(5, 2.0, 0.7, a).astype(np.float64) for a in (0, 90, 45)])
+    psfs /= psfs.sum(axis=(1, 2), keepdims=True)
+    phi = np.stack([convolve2d(psi_true, P, mode="same", boundary="wrap") for P in psfs])[:, None]
+    X = oracle.correlation_kernels(psfs, variant)
+    for order in ("simultaneous", "sequential"):
+        out = oracle.rl_planes(phi, psfs, 4, boundary="circular", psi0=psi_true[None], order=order, corr_kernels=X)
+        np.testing.assert_allclose(out[0], psi_true, rtol=1e-11)
