@@ -102,6 +102,25 @@ typedef enum {
     MVD_ORDER_SEQUENTIAL = 1
 } mvd_update_order;
 
+/* Variants of multi-view RL (Supp. Note 2 sec. 1).  All keep the update
+ * psi <- psi * prod_v [(phi_v / (psi * P_v)) * X_v] and differ in the kernel
+ * X_v the ratio of view v is convolved with.  With P^* the flipped PSF, '.'
+ * the entry-wise product over the K x K support, '*' a convolution of two
+ * K x K kernels cropped to the K x K centre, and products over the other
+ * views w != v, each X_v scaled to unit sum:
+ *   INDEPENDENT          X_v = P_v^* (plain MV-RL; the PSF as given, unscaled)
+ *   EFFICIENT_BAYESIAN   X_v = P_v^* . prod_w (P_v^* * P_w * P_w^*)
+ *   OPTIMIZATION_1       X_v = P_v^* . prod_w (P_v^* * P_w)
+ *   OPTIMIZATION_2       X_v = P_v^* . prod_w P_w^*
+ * The printed formulas leave the support, the normalisation and, for
+ * optimization I, an index open; these are the readings taken. */
+typedef enum {
+    MVD_VARIANT_INDEPENDENT = 0,
+    MVD_VARIANT_EFFICIENT_BAYESIAN = 1,
+    MVD_VARIANT_OPTIMIZATION_1 = 2,
+    MVD_VARIANT_OPTIMIZATION_2 = 3
+} mvd_variant;
+
 /* Summary of what a context decided; filled by mvd_get_info. */
 typedef struct {
     int views;
@@ -116,6 +135,9 @@ typedef struct {
     int blur_terms;             /* SVD terms summed over distinct PSFs      */
     int tile_h, tile_w;         /* fused path output tile                   */
     size_t workspace_bytes;     /* device scratch currently held            */
+    int variant;                /* mvd_variant in use                       */
+    int corr_rank[16];          /* SVD terms of the correlation kernel per
+                                   view (= rank for INDEPENDENT)            */
 } mvd_info;
 
 /* Create a context for `views` views with K x K PSFs psfs_host[V][K][K]
@@ -139,6 +161,12 @@ mvd_status mvd_set_algo(mvd_ctx *ctx, mvd_algo algo);
 
 /* Select how the views combine within one iteration (default simultaneous). */
 mvd_status mvd_set_update_order(mvd_ctx *ctx, mvd_update_order order);
+
+/* Select the RL variant (default INDEPENDENT).  The variant's kernels X_v are
+ * built from the context's PSFs on the host in FP64 and factorised like the
+ * PSFs; every route (fused, plain, direct, Fourier) then correlates with
+ * them.  mvd_set_psfs rebuilds them.  MVD_ERR_ARG for an unknown variant. */
+mvd_status mvd_set_variant(mvd_ctx *ctx, mvd_variant variant);
 
 /* Pick the context's route by timing: every route that can take its PSFs
  * and plane (the fused separable kernels, the Fourier route) runs twice on
@@ -218,6 +246,7 @@ typedef struct {
     const void *stacks_dev;   /* [V][H][P][W] view stacks to reslice, or NULL  */
     const void *planes_dev;   /* [V][P][H][W] planes, used if stacks_dev==NULL */
     float *estimate_dev;      /* [P][H][W] FP32 result (per-plane mean start)  */
+    int variant;              /* mvd_variant of this volume                   */
 } mvd_volume_desc;
 
 typedef struct mvd_batch mvd_batch;
@@ -264,7 +293,8 @@ mvd_status mvd_batch_destroy(mvd_batch *b);
  *   grad_dev     [V][K][K] FP32, receives dL/dP
  *   estimate_dev [P][H][W] FP32 or NULL: receives psi_T
  * Uses the context's PSFs, boundary and eps with direct K x K stencils
- * (K <= 63).  MVD_ERR_UNSUPPORTED for the sequential update order.  Returns
+ * (K <= 63).  MVD_ERR_UNSUPPORTED for the sequential update order and for a
+ * variant other than INDEPENDENT (the gradient does not follow X_v).  Returns
  * after the result is on the host (waits for `stream`). */
 mvd_status mvd_psf_grad(mvd_ctx *ctx, const void *data_dev, mvd_dtype dt, int n_planes,
                         int checkpoint_every, double *loss_host, float *grad_dev,
@@ -330,6 +360,13 @@ mvd_status mvd_profile_read(mvd_ctx *ctx, mvd_kernel_stat *out, int capacity, in
  * are stored once.  Needs no GPU. */
 mvd_status mvd_psf_factors(const float *psfs_host, int views, int psf_size, double rank_tol,
                            int *rank_out, float *taps_out, int taps_capacity);
+
+/* Host-only: the kernels X_v of `variant` (see mvd_variant) for the PSFs
+ * psfs_host [V][K][K], written to x_out [V][K][K] (FP64 arithmetic, rounded
+ * to FP32; each unit sum, INDEPENDENT included).  MVD_ERR_ARG on an invalid
+ * size, variant or PSF.  Needs no GPU. */
+mvd_status mvd_variant_kernels(const float *psfs_host, int views, int psf_size, mvd_variant variant,
+                               float *x_out);
 
 const char *mvd_status_string(mvd_status s);
 

@@ -156,8 +156,11 @@ struct mvd_ctx {
     float eps = 1e-6f;
     mvd_algo algo = MVD_ALGO_FUSED;
     mvd_update_order order = MVD_ORDER_SIMULTANEOUS;
+    mvd_variant variant = MVD_VARIANT_INDEPENDENT;
     double rank_tol = kDefaultRankTol;
     std::vector<float> psfs;
+    std::vector<float> corr_psfs;        // a variant's flip(X_v), [V][K][K]; empty for plain MV-RL
+    bool psf_dev_fresh = false;          // psf_dev holds the current psfs (+ corr_psfs)
     std::vector<float> taps_host;
     mvd::FactorTable ft;
     DevBuf taps, psf_dev, means, ratio, plain;
@@ -174,18 +177,53 @@ struct mvd_ctx {
         bool planned = false;
         int Ly = 0, Lx = 0, Lc = 0, LcP = 0;
         int rad_x[mvd::fftr::kMaxRadices], nrad_x = 0, rad_y[mvd::fftr::kMaxRadices], nrad_y = 0;
-        DevBuf tw_x, tw_y, spec, S0, T;
+        DevBuf tw_x, tw_y, spec, cspec, S0, T;
     } fft;
 };
 
 namespace {
+
+// A variant's correlation kernels: the ratio is convolved with X_v, i.e.
+// correlated with flip(X_v), which is what the correlation taps implement.
+void build_corr_psfs(mvd_ctx *c) {
+    c->corr_psfs.clear();
+    if (c->variant == MVD_VARIANT_INDEPENDENT) return;
+    const int K = c->K;
+    const size_t KK = static_cast<size_t>(K) * K;
+    std::vector<double> X(KK * c->V);
+    mvd::variant_kernels(c->psfs.data(), c->V, K, c->variant, X.data());
+    c->corr_psfs.resize(KK * c->V);
+    for (int v = 0; v < c->V; ++v)
+        for (int i = 0; i < K; ++i)
+            for (int j = 0; j < K; ++j)
+                c->corr_psfs[KK * v + static_cast<size_t>(i) * K + j] =
+                    static_cast<float>(X[KK * v + static_cast<size_t>(K - 1 - i) * K + (K - 1 - j)]);
+}
+
+// Device copy of the PSFs followed, for a variant, by its correlation kernels.
+cudaError_t upload_psf_dev(mvd_ctx *c) {
+    if (c->psf_dev_fresh) return cudaSuccess;
+    const size_t n = c->psfs.size() + c->corr_psfs.size();
+    cudaError_t e = c->psf_dev.ensure(n * sizeof(float));
+    if (e == cudaSuccess)
+        e = cudaMemcpy(c->psf_dev.ptr, c->psfs.data(), c->psfs.size() * sizeof(float), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && !c->corr_psfs.empty())
+        e = cudaMemcpy(c->psf_dev.as<float>() + c->psfs.size(), c->corr_psfs.data(),
+                       c->corr_psfs.size() * sizeof(float), cudaMemcpyHostToDevice);
+    c->psf_dev_fresh = e == cudaSuccess;
+    return e;
+}
 
 mvd_status upload_factors(mvd_ctx *c) {
     const int cap = mvd::max_terms(c->V, c->K) * 4 * c->K;
     std::vector<float> &taps = c->taps_host;
     taps.assign(static_cast<size_t>(cap), 0.0f);
     char msg[256] = {0};
-    if (!mvd::factorise_psfs(c->psfs.data(), c->V, c->K, c->rank_tol, c->ft, taps.data(), cap, msg, sizeof msg))
+    build_corr_psfs(c);
+    c->psf_dev_fresh = false;
+    c->fft.planned = false;   // the spectra follow the PSFs and the variant
+    if (!mvd::factorise_psfs(c->psfs.data(), c->V, c->K, c->rank_tol, c->ft, taps.data(), cap, msg, sizeof msg,
+                             c->corr_psfs.empty() ? nullptr : c->corr_psfs.data()))
         return fail(MVD_ERR_ARG, "PSF factorisation failed: %s", msg);
     const size_t bytes = static_cast<size_t>(c->ft.total_terms) * 4 * c->K * sizeof(float);
     cudaError_t e = c->taps.ensure(bytes);
@@ -233,11 +271,7 @@ cudaError_t prepare_workspace(mvd_ctx *c, int P) {
     if (e == cudaSuccess && c->algo == MVD_ALGO_FUSED && mvd::fused_taps_fit(c->ft))
         e = c->ratio.ensure(static_cast<size_t>(c->V) * P * plane_px * sizeof(float));
     if (e == cudaSuccess) e = c->plain.ensure(4 * plane_px * sizeof(float));
-    if (e == cudaSuccess && !c->psf_dev.ptr) {
-        e = c->psf_dev.ensure(c->psfs.size() * sizeof(float));
-        if (e == cudaSuccess)
-            e = cudaMemcpy(c->psf_dev.ptr, c->psfs.data(), c->psfs.size() * sizeof(float), cudaMemcpyHostToDevice);
-    }
+    if (e == cudaSuccess) e = upload_psf_dev(c);
     return e;
 }
 
@@ -299,7 +333,7 @@ mvd_status fft_plan(mvd_ctx *c) {
     f.LcP = (f.Lc + 7) / 8 * 8;
     mvd::fftr::radix_list(f.Lx, f.rad_x, &f.nrad_x);
     mvd::fftr::radix_list(f.Ly, f.rad_y, &f.nrad_y);
-    std::vector<float2> tx, ty, spec, all;
+    std::vector<float2> tx, ty, spec, all, call;
     mvd::fftr::twiddles(f.Lx, tx);
     mvd::fftr::twiddles(f.Ly, ty);
     const size_t per = static_cast<size_t>(f.Ly) * f.LcP;
@@ -309,11 +343,24 @@ mvd_status fft_plan(mvd_ctx *c) {
                                 spec);
         std::copy(spec.begin(), spec.end(), all.begin() + v * per);
     }
+    // a variant correlates with its own kernels: spectra of their flips
+    if (!c->corr_psfs.empty()) {
+        call.resize(per * c->V);
+        for (int v = 0; v < c->V; ++v) {
+            mvd::fftr::psf_spectrum(c->corr_psfs.data() + static_cast<size_t>(v) * c->K * c->K, c->K, f.Ly, f.Lx,
+                                    f.Lc, f.LcP, spec);
+            std::copy(spec.begin(), spec.end(), call.begin() + v * per);
+        }
+    }
     cudaError_t e;
     if ((e = f.tw_x.ensure(tx.size() * sizeof(float2))) != cudaSuccess ||
         (e = f.tw_y.ensure(ty.size() * sizeof(float2))) != cudaSuccess ||
-        (e = f.spec.ensure(all.size() * sizeof(float2))) != cudaSuccess)
+        (e = f.spec.ensure(all.size() * sizeof(float2))) != cudaSuccess ||
+        (!call.empty() && (e = f.cspec.ensure(call.size() * sizeof(float2))) != cudaSuccess))
         return fail(MVD_ERR_NOMEM, "Fourier tables: %s", cudaGetErrorString(e));
+    if (!call.empty() &&
+        (e = cudaMemcpy(f.cspec.ptr, call.data(), call.size() * sizeof(float2), cudaMemcpyHostToDevice)) != cudaSuccess)
+        return cuda_fail(e, "upload Fourier tables");
     if ((e = cudaMemcpy(f.tw_x.ptr, tx.data(), tx.size() * sizeof(float2), cudaMemcpyHostToDevice)) != cudaSuccess ||
         (e = cudaMemcpy(f.tw_y.ptr, ty.data(), ty.size() * sizeof(float2), cudaMemcpyHostToDevice)) != cudaSuccess ||
         (e = cudaMemcpy(f.spec.ptr, all.data(), all.size() * sizeof(float2), cudaMemcpyHostToDevice)) != cudaSuccess)
@@ -350,6 +397,7 @@ mvd_status run_fft(mvd_ctx *c, const void *data, mvd_dtype dt, float *est, int P
     a.tw_x = f.tw_x.as<float2>();
     a.tw_y = f.tw_y.as<float2>();
     a.spec = f.spec.as<float2>();
+    a.cspec = c->corr_psfs.empty() ? a.spec : f.cspec.as<float2>();
     a.H = c->H;
     a.W = c->W;
     a.P = P;
@@ -381,16 +429,12 @@ mvd_status run_plain(mvd_ctx *c, const void *data, mvd_dtype dt, float *est, int
     const size_t n = static_cast<size_t>(c->H) * c->W;
     cudaError_t e = c->plain.ensure(4 * n * sizeof(float));
     if (e != cudaSuccess) return fail(MVD_ERR_NOMEM, "plain workspace: %s", cudaGetErrorString(e));
-    if (direct && !c->psf_dev.ptr) {
-        e = c->psf_dev.ensure(c->psfs.size() * sizeof(float));
-        if (e != cudaSuccess) return fail(MVD_ERR_NOMEM, "psf copy: %s", cudaGetErrorString(e));
-        e = cudaMemcpy(c->psf_dev.ptr, c->psfs.data(), c->psfs.size() * sizeof(float), cudaMemcpyHostToDevice);
-        if (e != cudaSuccess) return cuda_fail(e, "upload psfs");
-    }
+    if (direct && (e = upload_psf_dev(c)) != cudaSuccess) return cuda_fail(e, "upload psfs");
     float *b = c->plain.as<float>(), *tmp = b + n, *cv = b + 2 * n, *prod = b + 3 * n;
     mvd::PlainArgs a{};
     a.taps = c->taps.as<float>();
     a.psf_dev = c->psf_dev.as<float>();
+    a.psf_corr = c->corr_psfs.empty() ? a.psf_dev : a.psf_dev + c->psfs.size();
     a.ft = c->ft;
     a.H = c->H;
     a.W = c->W;
@@ -459,12 +503,13 @@ mvd_status mvd_set_psfs(mvd_ctx *c, const float *psfs) {
     }
     DeviceGuard g(c->device);
     c->psfs.assign(psfs, psfs + c->V * KK);
-    c->fft.planned = false;   // the PSF spectra change with the PSFs
+    mvd_status st = upload_factors(c);   // also rebuilds a variant's kernels
+    if (st != MVD_OK) return st;
     if (c->psf_dev.ptr) {
-        cudaError_t e = cudaMemcpy(c->psf_dev.ptr, c->psfs.data(), c->psfs.size() * sizeof(float), cudaMemcpyHostToDevice);
+        cudaError_t e = upload_psf_dev(c);
         if (e != cudaSuccess) return cuda_fail(e, "upload psfs");
     }
-    return upload_factors(c);
+    return MVD_OK;
 }
 
 mvd_status mvd_psf_grad(mvd_ctx *c, const void *data, mvd_dtype dt, int P, int ckpt, double *loss_host,
@@ -475,6 +520,8 @@ mvd_status mvd_psf_grad(mvd_ctx *c, const void *data, mvd_dtype dt, int P, int c
     if (dt != MVD_U16 && dt != MVD_F32) return fail(MVD_ERR_ARG, "unknown dtype");
     if (P < 1 || P > 65535 || ckpt < 1) return fail(MVD_ERR_ARG, "need 1 <= n_planes <= 65535 and checkpoint_every >= 1");
     if (c->order != MVD_ORDER_SIMULTANEOUS) return fail(MVD_ERR_UNSUPPORTED, "the gradient follows the simultaneous order");
+    if (c->variant != MVD_VARIANT_INDEPENDENT)
+        return fail(MVD_ERR_UNSUPPORTED, "the gradient follows plain MV-RL (variant INDEPENDENT)");
     if (c->K > mvd::adj::kMaxK) return fail(MVD_ERR_UNSUPPORTED, "the gradient takes K <= %d", mvd::adj::kMaxK);
     DeviceGuard g(c->device);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -493,13 +540,7 @@ mvd_status mvd_psf_grad(mvd_ctx *c, const void *data, mvd_dtype dt, int P, int c
         (e = c->grad_acc.ensure((static_cast<size_t>(V) * K * K + 1) * sizeof(double))) != cudaSuccess ||
         (e = c->means.ensure(static_cast<size_t>(P) * sizeof(float))) != cudaSuccess)
         return fail(MVD_ERR_NOMEM, "gradient workspace: %s", cudaGetErrorString(e));
-    if (!c->psf_dev.ptr) {
-        if ((e = c->psf_dev.ensure(c->psfs.size() * sizeof(float))) != cudaSuccess)
-            return fail(MVD_ERR_NOMEM, "psf copy: %s", cudaGetErrorString(e));
-        if ((e = cudaMemcpy(c->psf_dev.ptr, c->psfs.data(), c->psfs.size() * sizeof(float), cudaMemcpyHostToDevice)) !=
-            cudaSuccess)
-            return cuda_fail(e, "upload psfs");
-    }
+    if ((e = upload_psf_dev(c)) != cudaSuccess) return cuda_fail(e, "upload psfs");
     float *w = c->grad_ws.as<float>();
     auto take = [&](long long k) { float *p = w; w += k * n; return p; };
     float *ck = take(nck), *psiA = take(1), *psiB = take(1);
@@ -705,8 +746,9 @@ mvd_status mvd_autotune(mvd_ctx *c, const void *data, mvd_dtype dt, int n_planes
     if (n_planes < 1) return fail(MVD_ERR_ARG, "n_planes must be >= 1");
     DeviceGuard g(c->device);
     char key[256];
-    std::snprintf(key, sizeof key, "route_v%d_k%d_%dx%d_t%d_b%d_o%d_r%d", c->V, c->K, c->H, c->W, c->iters,
-                  static_cast<int>(c->boundary), static_cast<int>(c->order), c->ft.total_terms);
+    std::snprintf(key, sizeof key, "route_v%d_k%d_%dx%d_t%d_b%d_o%d_r%d_x%d", c->V, c->K, c->H, c->W, c->iters,
+                  static_cast<int>(c->boundary), static_cast<int>(c->order), c->ft.total_terms,
+                  static_cast<int>(c->variant));
     int cached = -1, unused = 0;
     if (tune_cache_lookup(key, &cached, &unused) && cached >= 0) {
         c->algo = static_cast<mvd_algo>(cached);
@@ -824,6 +866,44 @@ mvd_status mvd_set_update_order(mvd_ctx *c, mvd_update_order order) {
     return MVD_OK;
 }
 
+mvd_status mvd_set_variant(mvd_ctx *c, mvd_variant variant) {
+    t_last_error.clear();
+    if (!c) return fail(MVD_ERR_ARG, "ctx is NULL");
+    if (variant < MVD_VARIANT_INDEPENDENT || variant > MVD_VARIANT_OPTIMIZATION_2)
+        return fail(MVD_ERR_ARG, "unknown variant %d", static_cast<int>(variant));
+    if (variant == c->variant) return MVD_OK;
+    DeviceGuard g(c->device);
+    c->variant = variant;
+    mvd_status st = upload_factors(c);
+    if (st != MVD_OK) return st;
+    if (c->psf_dev.ptr) {
+        cudaError_t e = upload_psf_dev(c);
+        if (e != cudaSuccess) return cuda_fail(e, "upload psfs");
+    }
+    return MVD_OK;
+}
+
+mvd_status mvd_variant_kernels(const float *psfs, int views, int K, mvd_variant variant, float *x_out) {
+    t_last_error.clear();
+    if (!psfs || !x_out) return fail(MVD_ERR_ARG, "NULL argument");
+    if (views < 1 || views > mvd::kMaxViews || K < 1 || K % 2 == 0) return fail(MVD_ERR_ARG, "bad sizes");
+    if (variant < MVD_VARIANT_INDEPENDENT || variant > MVD_VARIANT_OPTIMIZATION_2)
+        return fail(MVD_ERR_ARG, "unknown variant %d", static_cast<int>(variant));
+    const size_t KK = static_cast<size_t>(K) * K;
+    for (size_t i = 0; i < KK * views; ++i)
+        if (!std::isfinite(psfs[i]) || psfs[i] < 0) return fail(MVD_ERR_ARG, "PSF entry %zu negative or not finite", i);
+    std::vector<double> X(KK * views);
+    mvd::variant_kernels(psfs, views, K, variant, X.data());
+    for (int v = 0; v < views; ++v) {
+        double sum = 0;
+        for (size_t i = 0; i < KK; ++i) sum += X[KK * v + i];
+        if (!(sum > 0)) return fail(MVD_ERR_ARG, "kernel of view %d sums to zero", v);
+        // INDEPENDENT is returned at unit sum as well
+        for (size_t i = 0; i < KK; ++i) x_out[KK * v + i] = static_cast<float>(X[KK * v + i] / sum);
+    }
+    return MVD_OK;
+}
+
 mvd_status mvd_set_rank_tolerance(mvd_ctx *c, double tol) {
     if (!c) return fail(MVD_ERR_ARG, "ctx is NULL");
     if (!(tol >= 0.0) || !std::isfinite(tol)) return fail(MVD_ERR_ARG, "tolerance must be >= 0");
@@ -844,6 +924,8 @@ mvd_status mvd_get_info(const mvd_ctx *c, mvd_info *info) {
     info->algo = c->algo;
     info->order = c->order;
     for (int v = 0; v < c->V && v < 16; ++v) info->rank[v] = c->ft.rank[v];
+    for (int v = 0; v < c->V && v < 16; ++v) info->corr_rank[v] = c->ft.crank[v];
+    info->variant = c->variant;
     info->blur_groups = c->ft.n_groups;
     info->blur_terms = c->ft.total_terms;
     mvd::fused_tile_shape(c->K, &info->tile_h, &info->tile_w);
@@ -1141,6 +1223,7 @@ mvd_status mvd_batch_create(mvd_batch **out, const mvd_volume_desc *vols, int n,
         mvd_ctx *c = nullptr;
         mvd_status st = mvd_create(&c, v.views, v.psfs_host, v.psf_size, v.plane_h, v.plane_w, v.iters, boundary, eps);
         if (st == MVD_OK) st = mvd_set_update_order(c, order);
+        if (st == MVD_OK) st = mvd_set_variant(c, static_cast<mvd_variant>(v.variant));
         if (st != MVD_OK) {
             std::string m = t_last_error;
             if (c) mvd_destroy(c);
@@ -1156,8 +1239,8 @@ mvd_status mvd_batch_create(mvd_batch **out, const mvd_volume_desc *vols, int n,
             mvd_batch_destroy(b);
             return fail(MVD_ERR_NOMEM, "volume %d workspace: %s", i, cudaGetErrorString(e));
         }
-        std::snprintf(buf, sizeof buf, "_%dx%dx%dx%dv%dk%dt%d%s", v.n_planes, v.plane_h, v.plane_w, 0, v.views,
-                      v.psf_size, v.iters, v.stacks_dev ? "s" : "p");
+        std::snprintf(buf, sizeof buf, "_%dx%dx%dx%dv%dk%dt%d%s", v.n_planes, v.plane_h, v.plane_w, v.variant,
+                      v.views, v.psf_size, v.iters, v.stacks_dev ? "s" : "p");
         b->key += buf;
         cudaStream_t s = nullptr;
         cudaEvent_t ev = nullptr;

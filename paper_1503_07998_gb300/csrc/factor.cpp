@@ -62,10 +62,65 @@ void jacobi_svd(std::vector<double> &A, std::vector<double> &Vm, int K) {
 
 }  // namespace
 
-int max_terms(int views, int K) { return views * K; }
+int max_terms(int views, int K) { return 2 * views * K; }
+
+namespace {
+
+// Separable factors of one K x K kernel (row-major, FP64): on return r terms
+// with kernel ~= sum_q u_q w_q^T, u_q (scaled by the singular value) in
+// U[q*K .. q*K+K) and w_q in Wv likewise; r = 0 if the kernel is zero.
+int factor_kernel(const double *kernel, int K, double rank_tol, std::vector<double> &U, std::vector<double> &Wv) {
+    const size_t KK = static_cast<size_t>(K) * K;
+    std::vector<double> A(KK), Vm;
+    for (int i = 0; i < K; ++i)
+        for (int j = 0; j < K; ++j) A[i + static_cast<size_t>(K) * j] = kernel[static_cast<size_t>(i) * K + j];
+    jacobi_svd(A, Vm, K);
+    std::vector<double> sig(K);
+    for (int j = 0; j < K; ++j) {
+        double s = 0;
+        for (int i = 0; i < K; ++i) s += A[i + static_cast<size_t>(K) * j] * A[i + static_cast<size_t>(K) * j];
+        sig[j] = std::sqrt(s);
+    }
+    std::vector<int> order(K);
+    std::iota(order.begin(), order.end(), 0);
+    std::sort(order.begin(), order.end(), [&](int a, int b) { return sig[a] > sig[b]; });
+    double total = 0;
+    for (double s : sig) total += s * s;
+    if (!(total > 0)) return 0;
+    // smallest r whose dropped tail is within tolerance
+    int r = K;
+    double tail = 0;
+    for (int q = K - 1; q >= 0; --q) {
+        const double s = sig[order[q]];
+        if (rank_tol > 0) {
+            if (std::sqrt(tail + s * s) <= rank_tol * std::sqrt(total)) {
+                tail += s * s;
+                r = q;
+                continue;
+            }
+        } else if (s == 0.0) {
+            r = q;
+            continue;
+        }
+        break;
+    }
+    if (r < 1) r = 1;
+    U.assign(static_cast<size_t>(r) * K, 0.0);
+    Wv.assign(static_cast<size_t>(r) * K, 0.0);
+    for (int q = 0; q < r; ++q) {
+        const int j = order[q];
+        for (int m = 0; m < K; ++m) {
+            U[static_cast<size_t>(q) * K + m] = A[m + static_cast<size_t>(K) * j];
+            Wv[static_cast<size_t>(q) * K + m] = Vm[m + static_cast<size_t>(K) * j];
+        }
+    }
+    return r;
+}
+
+}  // namespace
 
 bool factorise_psfs(const float *psfs, int views, int K, double rank_tol, FactorTable &ft,
-                    float *taps_out, int taps_capacity, char *msg, size_t msg_len) {
+                    float *taps_out, int taps_capacity, char *msg, size_t msg_len, const float *corr) {
     ft = FactorTable{};
     ft.K = K;
     ft.views = views;
@@ -86,6 +141,14 @@ bool factorise_psfs(const float *psfs, int views, int K, double rank_tol, Factor
         ft.group[v] = g;
     }
     int off = 0;
+    std::vector<double> kern(KK), U, Wv;
+    auto reserve = [&](int r) {
+        if ((off + r) * 4 * K > taps_capacity) {
+            std::snprintf(msg, msg_len, "factor table overflow");
+            return false;
+        }
+        return true;
+    };
     for (int v = 0; v < views; ++v) {
         const int leader = ft.group_leader[ft.group[v]];
         if (leader != v) {            // identical PSF: reuse the leader's terms
@@ -93,62 +156,50 @@ bool factorise_psfs(const float *psfs, int views, int K, double rank_tol, Factor
             ft.tap_off[v] = ft.tap_off[leader];
             continue;
         }
-        std::vector<double> A(KK), Vm;
-        for (int i = 0; i < K; ++i)
-            for (int j = 0; j < K; ++j) A[i + static_cast<size_t>(K) * j] = psfs[KK * v + static_cast<size_t>(i) * K + j];
-        jacobi_svd(A, Vm, K);
-        std::vector<double> sig(K);
-        for (int j = 0; j < K; ++j) {
-            double s = 0;
-            for (int i = 0; i < K; ++i) s += A[i + static_cast<size_t>(K) * j] * A[i + static_cast<size_t>(K) * j];
-            sig[j] = std::sqrt(s);
-        }
-        std::vector<int> order(K);
-        std::iota(order.begin(), order.end(), 0);
-        std::sort(order.begin(), order.end(), [&](int a, int b) { return sig[a] > sig[b]; });
-        double total = 0;
-        for (double s : sig) total += s * s;
-        if (!(total > 0)) {
+        for (size_t i = 0; i < KK; ++i) kern[i] = psfs[KK * v + i];
+        const int r = factor_kernel(kern.data(), K, rank_tol, U, Wv);
+        if (r == 0) {
             std::snprintf(msg, msg_len, "PSF of view %d is zero", v);
             return false;
         }
-        // smallest r whose dropped tail is within tolerance
-        int r = K;
-        double tail = 0;
-        for (int q = K - 1; q >= 0; --q) {
-            const double s = sig[order[q]];
-            if (rank_tol > 0) {
-                if (std::sqrt(tail + s * s) <= rank_tol * std::sqrt(total)) {
-                    tail += s * s;
-                    r = q;
-                    continue;
-                }
-            } else if (s == 0.0) {
-                r = q;
-                continue;
-            }
-            break;
-        }
-        if (r < 1) r = 1;
-        if ((off + r) * 4 * K > taps_capacity) {
-            std::snprintf(msg, msg_len, "factor table overflow");
-            return false;
-        }
+        if (!reserve(r)) return false;
         ft.rank[v] = r;
         ft.tap_off[v] = off;
         for (int q = 0; q < r; ++q) {
-            const int j = order[q];
+            const double *u = U.data() + static_cast<size_t>(q) * K, *w = Wv.data() + static_cast<size_t>(q) * K;
             float *t = taps_out + static_cast<size_t>(off + q) * 4 * K;
             for (int m = 0; m < K; ++m) {
-                // u = A[:, j] (= s * left vector), w = Vm[:, j]
-                const double u_m = A[m + static_cast<size_t>(K) * j];
-                const double u_r = A[(K - 1 - m) + static_cast<size_t>(K) * j];
-                const double w_m = Vm[m + static_cast<size_t>(K) * j];
-                const double w_r = Vm[(K - 1 - m) + static_cast<size_t>(K) * j];
-                t[0 * K + m] = static_cast<float>(u_r);   // blur vertical
-                t[1 * K + m] = static_cast<float>(w_r);   // blur horizontal
-                t[2 * K + m] = static_cast<float>(u_m);   // correlation vertical
-                t[3 * K + m] = static_cast<float>(w_m);   // correlation horizontal
+                t[0 * K + m] = static_cast<float>(u[K - 1 - m]);   // blur vertical
+                t[1 * K + m] = static_cast<float>(w[K - 1 - m]);   // blur horizontal
+                t[2 * K + m] = static_cast<float>(u[m]);           // correlation vertical
+                t[3 * K + m] = static_cast<float>(w[m]);           // correlation horizontal
+            }
+        }
+        off += r;
+    }
+    for (int v = 0; v < views; ++v) {
+        ft.crank[v] = ft.rank[v];
+        ft.ctap_off[v] = ft.tap_off[v];
+    }
+    // a variant's correlation kernels: terms of their own, correlation taps only
+    for (int v = 0; corr && v < views; ++v) {
+        for (size_t i = 0; i < KK; ++i) kern[i] = corr[KK * v + i];
+        const int r = factor_kernel(kern.data(), K, rank_tol, U, Wv);
+        if (r == 0) {
+            std::snprintf(msg, msg_len, "correlation kernel of view %d is zero", v);
+            return false;
+        }
+        if (!reserve(r)) return false;
+        ft.crank[v] = r;
+        ft.ctap_off[v] = off;
+        for (int q = 0; q < r; ++q) {
+            const double *u = U.data() + static_cast<size_t>(q) * K, *w = Wv.data() + static_cast<size_t>(q) * K;
+            float *t = taps_out + static_cast<size_t>(off + q) * 4 * K;
+            for (int m = 0; m < K; ++m) {
+                t[0 * K + m] = 0.0f;
+                t[1 * K + m] = 0.0f;
+                t[2 * K + m] = static_cast<float>(u[m]);
+                t[3 * K + m] = static_cast<float>(w[m]);
             }
         }
         off += r;

@@ -313,7 +313,7 @@ __global__ void __launch_bounds__(kThreads) fft_cols_kernel(const FftArgs a, int
     } else {
         for (int v = a.view_lo; v < a.view_hi; ++v) {
             float2 *T = a.T + (static_cast<long long>(v) * a.P + p) * splane;
-            const float2 *Hs = a.spec + static_cast<long long>(v) * hplane;
+            const float2 *Hs = a.cspec + static_cast<long long>(v) * hplane;
             load(T, b0);
             __syncthreads();
             float2 *F = fft_group<false>(b0 + cl * LD, b1 + cl * LD, Ly, a.rad_y, a.nrad_y, tw, lane, per);

@@ -382,8 +382,8 @@ correlate_update_kernel(const __grid_constant__ KParams kp) {
                     tma::load_3d(tile, &kp.map, bar, c2.x0 - G::R4, c2.y0 - G::R, nv * a.P + c2.p);
                 }
             };
-            if (a.ft.rank[v] == 1) {
-                const float *tq = kp.taps + a.ft.tap_off[v] * 2 * K;
+            if (a.ft.crank[v] == 1) {
+                const float *tq = kp.taps + a.ft.ctap_off[v] * 2 * K;
                 vertical_pass<K>(tile, stage, tq);
                 __syncthreads();
                 prefetch_next();
@@ -395,11 +395,11 @@ correlate_update_kernel(const __grid_constant__ KParams kp) {
                 for (int h = 0; h < G::H_PER_THREAD; ++h)
 #pragma unroll
                     for (int j = 0; j < kNC; ++j) c[h][j] = 0.0f;
-                for (int q = 0; q < a.ft.rank[v]; ++q) {
-                    const float *tq = kp.taps + (a.ft.tap_off[v] + q) * 2 * K;
+                for (int q = 0; q < a.ft.crank[v]; ++q) {
+                    const float *tq = kp.taps + (a.ft.ctap_off[v] + q) * 2 * K;
                     vertical_pass<K>(tile, stage, tq);
                     __syncthreads();
-                    if (q == a.ft.rank[v] - 1) prefetch_next();
+                    if (q == a.ft.crank[v] - 1) prefetch_next();
                     horizontal_pass<K>(stage, tq + K, c);
                     __syncthreads();
                 }

@@ -30,6 +30,8 @@ struct FactorTable {
     int views = 0;
     int rank[kMaxViews] = {};
     int tap_off[kMaxViews] = {};     // in units of terms
+    int crank[kMaxViews] = {};       // terms of the correlation step (= rank for plain MV-RL)
+    int ctap_off[kMaxViews] = {};    // their offset (= tap_off for plain MV-RL)
     int group[kMaxViews] = {};       // blur group (views with identical PSFs)
     int n_groups = 0;
     int group_leader[kMaxViews] = {};
@@ -37,11 +39,18 @@ struct FactorTable {
 };
 
 // Host-side PSF analysis (factor.cpp).  psfs: [V][K][K] FP32.  Fills `ft` and
-// the host tap array (total_terms * 4 * K floats).  Returns false with a
-// message when the factorisation fails.
+// the host tap array (total_terms * 4 * K floats).  With `corr` ([V][K][K],
+// the kernels the ratio is correlated with) the correlation step gets terms of
+// its own; without it, it uses the PSFs' terms.  Returns false with a message
+// when the factorisation fails.
 bool factorise_psfs(const float *psfs, int views, int K, double rank_tol,
-                    FactorTable &ft, float *taps_out, int taps_capacity, char *msg, size_t msg_len);
+                    FactorTable &ft, float *taps_out, int taps_capacity, char *msg, size_t msg_len,
+                    const float *corr = nullptr);
 int max_terms(int views, int K);
+
+// Correlation kernels of the MV-RL variants (variants.cpp): X_v, [V][K][K],
+// unit sum, FP64 (Supp. Note 2 sec. 1).  variant: an mvd_variant value.
+void variant_kernels(const float *psfs, int views, int K, int variant, double *X);
 
 // ---- kernel launchers (return cudaGetLastError after the launch) ---------
 
@@ -91,6 +100,7 @@ struct FftArgs {
     int rad_x[kMaxRadices], nrad_x, rad_y[kMaxRadices], nrad_y;
     const float2 *tw_x, *tw_y;         // exp(+2 pi i k / L) tables
     const float2 *spec;                // [V][Ly][LcP] PSF spectra / (Ly Lx)
+    const float2 *cspec;               // spectra the correlation uses (= spec for plain MV-RL)
     int H, W, P, view_lo, view_hi;
     float eps;
     const float *psi_in;               // nullptr: constant first estimate (means)
@@ -131,6 +141,7 @@ cudaError_t to_float(const double *G, float *out, int n, cudaStream_t s);
 struct PlainArgs {
     const float *taps;       // device factor taps
     const float *psf_dev;    // [V][K][K] raw PSFs (direct route)
+    const float *psf_corr;   // [V][K][K] kernels the direct correlation uses (= psf_dev for plain MV-RL)
     FactorTable ft;
     int H, W, circular;
     float eps;

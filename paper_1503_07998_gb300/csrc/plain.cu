@@ -111,13 +111,15 @@ cudaError_t plain_convolve(const PlainArgs &a, int v, int correlate, int direct,
     const long long n = static_cast<long long>(a.H) * a.W;
     const int K = a.ft.K;
     if (direct) {
-        direct2d<<<blocks(n), kThreads, 0, s>>>(in, out, a.psf_dev + static_cast<long long>(v) * K * K, K,
-                                                a.H, a.W, a.circular, correlate);
+        const float *P = (correlate ? a.psf_corr : a.psf_dev) + static_cast<long long>(v) * K * K;
+        direct2d<<<blocks(n), kThreads, 0, s>>>(in, out, P, K, a.H, a.W, a.circular, correlate);
         count_launch();
         return cudaGetLastError();
     }
-    for (int q = 0; q < a.ft.rank[v]; ++q) {
-        const float *tq = a.taps + static_cast<long long>(a.ft.tap_off[v] + q) * 4 * K + (correlate ? 2 * K : 0);
+    const int rank = correlate ? a.ft.crank[v] : a.ft.rank[v];
+    const int off = correlate ? a.ft.ctap_off[v] : a.ft.tap_off[v];
+    for (int q = 0; q < rank; ++q) {
+        const float *tq = a.taps + static_cast<long long>(off + q) * 4 * K + (correlate ? 2 * K : 0);
         pass1d<<<blocks(n), kThreads, 0, s>>>(in, tmp, tq, K, a.H, a.W, a.circular, 0, 0);
         pass1d<<<blocks(n), kThreads, 0, s>>>(tmp, out, tq + K, K, a.H, a.W, a.circular, 1, q > 0);
         count_launch(2);

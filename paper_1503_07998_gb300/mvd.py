@@ -26,6 +26,7 @@ BOUNDARY = {"zero": 0, "circular": 1}
 DTYPE = {"u16": 0, "f32": 1}
 ALGO = {"fused": 0, "plain": 1, "direct": 2, "fft": 3}
 ORDER = {"simultaneous": 0, "sequential": 1}
+VARIANT = {"independent": 0, "efficient_bayesian": 1, "optimization_1": 2, "optimization_2": 3}
 
 
 class MvdError(RuntimeError):
@@ -46,6 +47,7 @@ class _Info(ctypes.Structure):
         ("rank", ctypes.c_int * 16), ("blur_groups", ctypes.c_int), ("blur_terms", ctypes.c_int),
         ("tile_h", ctypes.c_int), ("tile_w", ctypes.c_int),
         ("workspace_bytes", ctypes.c_size_t),
+        ("variant", ctypes.c_int), ("corr_rank", ctypes.c_int * 16),
     ]
 
 
@@ -66,6 +68,8 @@ def lib() -> ctypes.CDLL:
     L.mvd_set_algo.argtypes = [vp, i]
     L.mvd_set_rank_tolerance.argtypes = [vp, d]
     L.mvd_set_update_order.argtypes = [vp, i]
+    L.mvd_set_variant.argtypes = [vp, i]
+    L.mvd_variant_kernels.argtypes = [vp, i, i, i, vp]
     L.mvd_device_status.argtypes = [vp, vp]
     L.mvd_psf_grad.argtypes = [vp, vp, i, i, i, ctypes.POINTER(d), vp, vp, vp]
     L.mvd_set_psfs.argtypes = [vp, vp]
@@ -91,7 +95,7 @@ def lib() -> ctypes.CDLL:
     L.mvd_launch_count.argtypes = []
     L.mvd_launch_count.restype = ctypes.c_uint64
     for name in ("mvd_create", "mvd_destroy", "mvd_set_algo", "mvd_set_rank_tolerance", "mvd_get_info",
-                 "mvd_set_update_order", "mvd_device_status", "mvd_set_wait_budget",
+                 "mvd_set_update_order", "mvd_set_variant", "mvd_variant_kernels", "mvd_device_status", "mvd_set_wait_budget",
                  "mvd_deconvolve_planes_static", "mvd_psf_grad", "mvd_set_psfs", "mvd_autotune",
                  "mvd_batch_create", "mvd_batch_tune", "mvd_batch_run", "mvd_batch_info", "mvd_batch_destroy",
                  "mvd_reslice", "mvd_deconvolve_planes", "mvd_run_host", "mvd_psf_factors",
@@ -211,6 +215,22 @@ def mvd_autotune(ctx: Context, data, stream=None) -> str:
 
 def mvd_set_update_order(ctx: Context, order: str) -> None:
     _check(lib().mvd_set_update_order(ctx.handle, ORDER[order]), "mvd_set_update_order")
+
+
+def mvd_set_variant(ctx: Context, variant: str) -> None:
+    """Select the MV-RL variant (keys of VARIANT; default "independent")."""
+    _check(lib().mvd_set_variant(ctx.handle, VARIANT[variant]), "mvd_set_variant")
+
+
+def mvd_variant_kernels(psfs, variant: str) -> np.ndarray:
+    """Host-only: the kernels X_v [V][K][K] (unit sum) the library builds for
+    a variant of the given PSFs."""
+    p = np.ascontiguousarray(np.asarray(psfs, dtype=np.float32))
+    V, K, _ = p.shape
+    out = np.zeros_like(p)
+    _check(lib().mvd_variant_kernels(p.ctypes.data_as(ctypes.c_void_p), V, K, VARIANT[variant],
+                                     out.ctypes.data_as(ctypes.c_void_p)), "mvd_variant_kernels")
+    return out
 
 
 def mvd_device_status(ctx: Context, stream=None) -> None:
@@ -391,7 +411,7 @@ class _VolumeDesc(ctypes.Structure):
     _fields_ = [("views", ctypes.c_int), ("psf_size", ctypes.c_int), ("psfs_host", ctypes.c_void_p),
                 ("plane_h", ctypes.c_int), ("plane_w", ctypes.c_int), ("n_planes", ctypes.c_int),
                 ("iters", ctypes.c_int), ("stacks_dev", ctypes.c_void_p), ("planes_dev", ctypes.c_void_p),
-                ("estimate_dev", ctypes.c_void_p)]
+                ("estimate_dev", ctypes.c_void_p), ("variant", ctypes.c_int)]
 
 
 class Batch:
@@ -417,7 +437,8 @@ class Batch:
 def mvd_batch_create(volumes, boundary: str = "zero", eps: float = 1e-6, order: str = "simultaneous") -> Batch:
     """volumes: list of dicts with keys psfs ([V][K][K]), iters, estimate
     (CUDA float32 [P][H][W]) and either stacks (CUDA [V][H][P][W]) or planes
-    (CUDA [V][P][H][W]); all data of one dtype."""
+    (CUDA [V][P][H][W]); all data of one dtype; optional key variant (a key
+    of VARIANT, default "independent")."""
     descs = (_VolumeDesc * len(volumes))()
     keep, dtype = [], None
     for i, v in enumerate(volumes):
@@ -431,6 +452,7 @@ def mvd_batch_create(volumes, boundary: str = "zero", eps: float = 1e-6, order: 
         d.psfs_host = psfs.ctypes.data
         d.plane_h, d.plane_w, d.n_planes, d.iters = H, W, P, int(v["iters"])
         d.estimate_dev = est.data_ptr()
+        d.variant = VARIANT[v.get("variant", "independent")]
         src = v.get("stacks")
         if src is not None:
             _require_cuda(src)

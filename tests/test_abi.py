@@ -116,3 +116,30 @@ def test_rotated_gaussian_needs_several_terms():
     assert 1 < ranks[0] <= 17
     rec = _reconstruct(taps, ranks, 17, 1, [0])
     assert np.linalg.norm(rec[0] - psfs[0]) <= 1e-6 * np.linalg.norm(psfs[0])
+
+
+@pytest.mark.parametrize("variant", ["independent", "efficient_bayesian", "optimization_1", "optimization_2"])
+def test_variant_kernels_match_oracle(variant):
+    """The library's host-built X_v (FP64, rounded to FP32) equal the oracle's
+    on non-symmetric PSFs of three views and on oblique Gaussians."""
+    import oracle
+    rng = np.random.default_rng(21)
+    for psfs in (rng.random((3, 7, 7)).astype(np.float32) + 0.05,
+                 np.stack([synth.gaussian_psf(15, 3.0, 1.0, a) for a in (0, 60, 120)])):
+        got = mvd.mvd_variant_kernels(psfs, variant)
+        want = oracle.correlation_kernels(psfs.astype(np.float64), variant)
+        np.testing.assert_allclose(got, want, rtol=2e-6, atol=1e-7 * want.max())
+
+
+def test_variant_rejects_bad_arguments():
+    psfs = np.ones((2, 5, 5), np.float32)
+    with pytest.raises(KeyError):
+        mvd.mvd_variant_kernels(psfs, "nope")
+    bad = psfs.copy()
+    bad[0, 0, 0] = -1
+    with pytest.raises(mvd.MvdError):
+        mvd.mvd_variant_kernels(bad, "optimization_2")
+    out = np.zeros_like(psfs)
+    st = mvd.lib().mvd_variant_kernels(psfs.ctypes.data_as(ctypes.c_void_p), 2, 5, 7,
+                                       out.ctypes.data_as(ctypes.c_void_p))
+    assert st == mvd.MVD_ERR_ARG
