@@ -59,7 +59,7 @@ ALU_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 # scaled to the full workload (None until measured for the current kernels).
 # Taken on 128 of the 512 planes (--workload slab512) and scaled by 4; see
 # profiles/fused_kernels_volume512.md.
-NCU_TRAFFIC_PER_LAUNCH = {"blur_ratio": 1.9334e9, "correlate_update": 2.0165e9}
+NCU_TRAFFIC_PER_LAUNCH = {"blur_ratio": 1.9324e9, "correlate_update": 2.0041e9}
 
 
 def _peaks():
@@ -87,15 +87,32 @@ class ClockSampler:
         self.file = None
 
     def start(self):
+        """Start sampling every 50 ms and wait (at most 3 s) for the first row,
+        so that a short timed region that follows still gets samples."""
         try:
             self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
             self.proc = subprocess.Popen(
-                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200",
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "50",
                  "-i", str(self.index)], stdout=self.file, stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
+            return
+        t_end = time.time() + 3.0
+        while time.time() < t_end and self._rows() < 1 and self.proc.poll() is None:
+            time.sleep(0.01)
 
-    def stop(self):
+    def _rows(self) -> int:
+        try:
+            with open(self.file.name) as f:
+                return sum(1 for r in f if r.strip())
+        except OSError:
+            return 0
+
+    def mark(self) -> int:
+        """Rows written so far; stop(skip=mark()) keeps only later samples."""
+        return self._rows() if self.proc is not None else 0
+
+    def stop(self, skip: int = 0, upto=None):
         if self.proc is None:
             return None
         self.proc.terminate()
@@ -105,7 +122,7 @@ class ClockSampler:
             self.proc.kill()
         self.file.flush()
         with open(self.file.name) as f:
-            rows = [r.strip().split(", ") for r in f if r.strip()]
+            rows = [r.strip().split(", ") for r in f if r.strip()][skip:upto]
         os.unlink(self.file.name)
         sm, smax, reasons = [], 0.0, set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
@@ -272,17 +289,19 @@ def run_mvd(args, wl):
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
     barrier(world)
+    first_row = clocks.mark()
     ev0.record(stream)
     for _ in range(args.steps):
         step()
     ev1.record(stream)
     torch.cuda.synchronize()
+    last_row = max(clocks.mark(), first_row + 1)   # at least the first sample after the start
     barrier(world)
     ms = ev0.elapsed_time(ev1)
     launches = mvd.mvd_launch_count() - n0
     prof = mvd.mvd_profile_read(ctx)
     mvd.mvd_profile_enable(ctx, False)
-    clk = clocks.stop()
+    clk = clocks.stop(first_row, last_row)
     ms_max = reduce_max(ms, world)
     units_per_step = Y * Z * X * iters * V
     value = units_per_step * world * args.steps / (ms_max / 1e3)
@@ -292,7 +311,7 @@ def run_mvd(args, wl):
     vi_per_launch = Y * Z * X
     # 2K flop per output of each 1D pass, two passes per SVD term
     flops_a = 4 * K * info.blur_terms            # one blur per distinct PSF
-    flops_b = 4 * K * sum(info.rank[:V])         # one correlation per view
+    flops_b = 4 * K * sum(info.corr_rank[:V])    # one correlation per view
     es = 2 if stacks.dtype == torch.uint16 else 4
     kr = {
         "blur_ratio": kernel_roofline(prof, "blur_ratio", vi_per_launch, 4 + (es + 4) * V, flops_a, hbm_peak),
@@ -451,11 +470,14 @@ def run_batch(args):
     (U(1, 2), U(4, 12)) px, 5-20 iterations, blob density 5e-5, seeded per
     volume) run as one captured CUDA graph after autotuning."""
     import torch
-    dist_setup(args.gpus)
-    from paper_1503_07998_gb300 import mvd, synth
+    world, rank, _ = dist_setup(args.gpus)
+    from paper_1503_07998_gb300 import mvd, shard, synth
     dev = torch.device("cuda", torch.cuda.current_device())
     stream = torch.cuda.current_stream(dev)
-    vols = synth.uneven_volumes(64, seed=1000, device=dev)
+    # the same 64 volumes on every world size; each rank takes its share
+    mine = shard.volumes_of_rank(64, rank, world)
+    allv = synth.uneven_volumes(64, seed=1000, shapes_only=True)
+    vols = synth.uneven_volumes(64, seed=1000, device=dev, only=mine)
     ests = [torch.empty((v["P"], v["H"], v["W"]), device=dev) for v in vols]
     batch = mvd.mvd_batch_create([{"stacks": v["stacks"], "psfs": v["psfs"], "iters": v["iters"], "estimate": e}
                                   for v, e in zip(vols, ests)], order="sequential")
@@ -465,27 +487,39 @@ def run_batch(args):
     for _ in range(args.warmup):
         mvd.mvd_batch_run(batch)
     torch.cuda.synchronize()
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     n0 = mvd.mvd_launch_count()
+    barrier(world)
+    first_row = clocks.mark()
     e0.record(stream)
     for _ in range(args.steps):
         mvd.mvd_batch_run(batch)
     e1.record(stream)
     torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1) / args.steps
-    units = sum(v["P"] * v["H"] * v["W"] * v["iters"] * v["views"] for v in vols)
+    last_row = max(clocks.mark(), first_row + 1)
+    barrier(world)
+    clk = clocks.stop(first_row, last_row)
+    ms = reduce_max(e0.elapsed_time(e1) / args.steps, world)
+    units = sum(v["P"] * v["H"] * v["W"] * v["iters"] * v["views"] for v in allv)
     info = mvd.mvd_batch_info(batch)
-    line = {"metric": METRIC, "value": units / (ms / 1e3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+    line = {"metric": METRIC, "value": units / (ms / 1e3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "strong",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "64 uneven volumes in one captured CUDA graph (see run_batch)",
-                       "voxels": int(sum(v["P"] * v["H"] * v["W"] for v in vols)),
+            "config": {"workload": "64 uneven volumes in one captured CUDA graph per GPU (see run_batch)",
+                       "voxels": int(sum(v["P"] * v["H"] * v["W"] for v in allv)),
                        "voxel_view_iterations": int(units), "order": "sequential",
-                       "l2": "inputs larger than L2"},
-            "batch": info, "tune_s": tune_s,
+                       "l2": "inputs larger than L2",
+                       "parallelism": f"{world} GPU(s), volumes dealt round robin, no collective"},
+            "batch": info, "tune_s": tune_s, "clocks": clk,
             "gpu_launches": int(mvd.mvd_launch_count() - n0)}
     batch.close()
-    print(json.dumps(line))
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
     return 0
 
 

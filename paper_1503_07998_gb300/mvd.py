@@ -157,6 +157,8 @@ class Info:
     tile_h: int
     tile_w: int
     workspace_bytes: int
+    variant: int
+    corr_rank: list
 
 
 class Context:
@@ -253,7 +255,7 @@ def mvd_get_info(ctx: Context) -> Info:
     _check(lib().mvd_get_info(ctx.handle, ctypes.byref(inf)), "mvd_get_info")
     return Info(inf.views, inf.psf_size, inf.plane_h, inf.plane_w, inf.iters, inf.boundary, inf.algo, inf.order,
                 list(inf.rank)[:min(16, inf.views)], inf.blur_groups, inf.blur_terms, inf.tile_h, inf.tile_w,
-                int(inf.workspace_bytes))
+                int(inf.workspace_bytes), inf.variant, list(inf.corr_rank)[:min(16, inf.views)])
 
 
 def mvd_reslice(ctx: Context, stacks, planes, stream=None) -> None:

@@ -188,15 +188,18 @@ def volume_stacks(Z: int, Y: int, X: int, K: int, sigma_axial: float,
 
 def uneven_volumes(n: int, seed: int, side=(96, 768), planes=(16, 256), views=(2, 6), psf=(9, 41),
                    sigma_lateral=(1.0, 2.0), sigma_axial=(4.0, 12.0), iters=(5, 20), density=5e-5,
-                   device="cpu"):
+                   device="cpu", only=None, shapes_only=False):
     """Independent volumes of uneven shape for batched runs.
 
     Volume i uses seed + i: square planes of side U{side}, U{planes} planes,
     U{views} views at angles k*180/V degrees, an odd PSF side U{psf},
     Gaussian sigmas (U(lateral), U(axial)) px and U{iters} iterations.
     Returns a list of dicts (stacks [V][H][P][W] uint16 on `device`, psfs,
-    iters, shape)."""
+    iters, shape).  `only`: indices of the volumes to return (the others are
+    skipped; a volume depends on seed + i alone).  shapes_only: no data
+    (stacks and psfs None)."""
     out = []
+    keep = None if only is None else set(only)
     for i in range(n):
         rng = np.random.default_rng(seed + i)
         s = int(rng.integers(side[0], side[1] + 1))
@@ -207,6 +210,11 @@ def uneven_volumes(n: int, seed: int, side=(96, 768), planes=(16, 256), views=(2
         sa = float(rng.uniform(*sigma_axial))
         it = int(rng.integers(iters[0], iters[1] + 1))
         angles = tuple(180.0 * j / v for j in range(v))
-        stacks, psfs = volume_stacks(s, p, s, k, sa, sl, angles, density, seed=seed + i, device=device)
+        if keep is not None and i not in keep:
+            continue
+        if shapes_only:
+            stacks = psfs = None
+        else:
+            stacks, psfs = volume_stacks(s, p, s, k, sa, sl, angles, density, seed=seed + i, device=device)
         out.append({"stacks": stacks, "psfs": psfs, "iters": it, "H": s, "W": s, "P": p, "views": v, "K": k})
     return out
