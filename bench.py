@@ -369,6 +369,33 @@ def run_mvd(args, wl):
         finally:
             mvd.mvd_set_algo(ctx, "fused")
 
+    # the optional tensor-core route (BF16x3 tcgen05 passes) on the same planes
+    tensor_route = None
+    if not args.no_plain:
+        try:
+            mvd.mvd_set_algo(ctx, "tensor")
+            mvd.mvd_deconvolve_planes(ctx, planes, est)
+            torch.cuda.synchronize()
+            mvd.mvd_profile_enable(ctx, True)
+            f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            f0.record(stream)
+            mvd.mvd_deconvolve_planes(ctx, planes, est)
+            f1.record(stream)
+            torch.cuda.synchronize()
+            tprof = mvd.mvd_profile_read(ctx)
+            mvd.mvd_profile_enable(ctx, False)
+            tms = f0.elapsed_time(f1)
+            tk = {n: kernel_roofline(tprof, n, vi_per_launch, b, f, hbm_peak)
+                  for n, b, f in (("tc_blur_ratio", 4 + (es + 4) * V, flops_a),
+                                  ("tc_correlate_update", 4 * V + 8, flops_b))}
+            tensor_route = {"value": units_per_step / (tms / 1e3), "unit": UNIT, "ms": tms,
+                            "precision": "BF16x3 tcgen05 passes, FP32 accumulate; ratio and update FP32",
+                            "note": "deconvolution only (no reslice)", "kernels": tk}
+        except mvd.MvdError as e:
+            tensor_route = {"unavailable": str(e)}
+        finally:
+            mvd.mvd_set_algo(ctx, "fused")
+
     # PSF calibration gradient: 2 views, 64 planes of 256x256, free 31x31
     # PSFs started at sigma (1.2, 5) px on data made with (1.5, 7) px,
     # 10 unrolled iterations, checkpoint every 2
@@ -432,7 +459,7 @@ def run_mvd(args, wl):
                 "voxel_iterations_per_s": value / V,
                 "roofline": roof, "kernels": kr, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": int(launches), "clocks": clk, "plain_per_plane": plain,
-                "fft_route": fft_route, "psf_grad": grad,
+                "fft_route": fft_route, "tensor_route": tensor_route, "psf_grad": grad,
                 "paper_context": "GTX TITAN Black, 2 views, 1024^3 padded, 10 it: 21.1 s = 1.02e9 voxel-view-it/s "
                                  "(Supp. Table 1); another machine, not the target"}
         print(json.dumps(line))

@@ -86,7 +86,15 @@ typedef enum {
      * the plane itself (CIRCULAR, whose sides must then be such sizes);
      * padded sides <= 2048.  Its cost does not grow with K or with the PSFs'
      * separable rank (oblique views). */
-    MVD_ALGO_FFT = 3
+    MVD_ALGO_FFT = 3,
+    /* Optional tensor-core route: the fused kernels with every separable 1D
+     * pass run as a banded (Toeplitz) matrix product on the tcgen05 tensor
+     * cores in BF16x3 (each FP32 operand split into BF16 hi + lo, three
+     * products per multiply, FP32 accumulation: about 2^-16 relative error
+     * per product instead of 2^-24); the ratio, the product over views and
+     * the update stay FP32.  Odd K <= 47, any number of separable terms,
+     * both boundaries.  Never chosen by default or by mvd_autotune. */
+    MVD_ALGO_TENSOR = 4
 } mvd_algo;
 
 typedef enum {

@@ -268,7 +268,7 @@ cudaError_t prepare_workspace(mvd_ctx *c, int P) {
         e = c->fft.S0.ensure(rows * sizeof(float2));
         if (e == cudaSuccess) e = c->fft.T.ensure(rows * c->V * sizeof(float2));
     }
-    if (e == cudaSuccess && c->algo == MVD_ALGO_FUSED && mvd::fused_taps_fit(c->ft))
+    if (e == cudaSuccess && ((c->algo == MVD_ALGO_FUSED && mvd::fused_taps_fit(c->ft)) || c->algo == MVD_ALGO_TENSOR))
         e = c->ratio.ensure(static_cast<size_t>(c->V) * P * plane_px * sizeof(float));
     if (e == cudaSuccess) e = c->plain.ensure(4 * plane_px * sizeof(float));
     if (e == cudaSuccess) e = upload_psf_dev(c);
@@ -290,6 +290,7 @@ mvd_status run_fused(mvd_ctx *c, const void *data, mvd_dtype dt, float *est, int
     }
     // simultaneous: one launch pair over all views; sequential: one per view
     const int step = c->order == MVD_ORDER_SEQUENTIAL ? 1 : c->V;
+    const bool tc = c->algo == MVD_ALGO_TENSOR;
     bool first = init_mean != 0;
     for (int t = 0; t < c->iters; ++t) {
         for (int v0 = 0; v0 < c->V; v0 += step) {
@@ -297,11 +298,11 @@ mvd_status run_fused(mvd_ctx *c, const void *data, mvd_dtype dt, float *est, int
             a.view_hi = v0 + step;
             a.psi_in = first ? nullptr : est;
             first = false;
-            c->prof.mark(s, "blur_ratio");
-            e = mvd::launch_fused_blur_ratio(a, s);
+            c->prof.mark(s, tc ? "tc_blur_ratio" : "blur_ratio");
+            e = tc ? mvd::launch_tc_blur_ratio(a, s) : mvd::launch_fused_blur_ratio(a, s);
             if (e != cudaSuccess) return cuda_fail(e, "blur/ratio kernel");
-            c->prof.mark(s, "correlate_update");
-            e = mvd::launch_fused_correlate_update(a, s);
+            c->prof.mark(s, tc ? "tc_correlate_update" : "correlate_update");
+            e = tc ? mvd::launch_tc_correlate_update(a, s) : mvd::launch_fused_correlate_update(a, s);
             if (e != cudaSuccess) return cuda_fail(e, "correlate/update kernel");
         }
     }
@@ -844,8 +845,11 @@ mvd_status mvd_destroy(mvd_ctx *c) {
 
 mvd_status mvd_set_algo(mvd_ctx *c, mvd_algo algo) {
     if (!c) return fail(MVD_ERR_ARG, "ctx is NULL");
-    if (algo != MVD_ALGO_FUSED && algo != MVD_ALGO_PLAIN && algo != MVD_ALGO_DIRECT && algo != MVD_ALGO_FFT)
+    if (algo != MVD_ALGO_FUSED && algo != MVD_ALGO_PLAIN && algo != MVD_ALGO_DIRECT && algo != MVD_ALGO_FFT &&
+        algo != MVD_ALGO_TENSOR)
         return fail(MVD_ERR_ARG, "unknown algo %d", static_cast<int>(algo));
+    if (algo == MVD_ALGO_TENSOR && !mvd::tc_supported(c->K))
+        return fail(MVD_ERR_UNSUPPORTED, "tensor-core route takes odd K <= 47 (got %d)", c->K);
     if (algo == MVD_ALGO_FUSED && !(mvd::fused_supported(c->K) && mvd::fused_taps_fit(c->ft)))
         return fail(MVD_ERR_UNSUPPORTED, "fused path takes K <= %d (got %d)", mvd::kFusedMaxK, c->K);
     if (algo == MVD_ALGO_FFT) {
@@ -928,7 +932,10 @@ mvd_status mvd_get_info(const mvd_ctx *c, mvd_info *info) {
     info->variant = c->variant;
     info->blur_groups = c->ft.n_groups;
     info->blur_terms = c->ft.total_terms;
-    mvd::fused_tile_shape(c->K, &info->tile_h, &info->tile_w);
+    if (c->algo == MVD_ALGO_TENSOR)
+        mvd::tc_tile_shape(c->K, &info->tile_h, &info->tile_w);
+    else
+        mvd::fused_tile_shape(c->K, &info->tile_h, &info->tile_w);
     info->workspace_bytes = c->taps.bytes + c->psf_dev.bytes + c->means.bytes + c->ratio.bytes + c->plain.bytes +
                             c->run_stack[0].bytes + c->run_stack[1].bytes + c->run_planes.bytes +
                             c->run_est[0].bytes + c->run_est[1].bytes;
@@ -984,7 +991,7 @@ mvd_status mvd_deconvolve_planes(mvd_ctx *c, const void *data, mvd_dtype dt, flo
     }
     // the fused kernels carry the taps in their parameter block: PSFs that need
     // more separable terms than it holds run on the plain path
-    if (c->algo == MVD_ALGO_FUSED && mvd::fused_taps_fit(c->ft))
+    if ((c->algo == MVD_ALGO_FUSED && mvd::fused_taps_fit(c->ft)) || c->algo == MVD_ALGO_TENSOR)
         return run_fused(c, data, dt, est, n_planes, init_mean, s);
     if (c->algo == MVD_ALGO_FFT) return run_fft(c, data, dt, est, n_planes, init_mean, s);
     return run_plain(c, data, dt, est, n_planes, init_mean, c->algo == MVD_ALGO_DIRECT, s);

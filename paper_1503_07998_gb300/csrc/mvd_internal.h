@@ -91,6 +91,12 @@ void fused_tile_shape(int K, int *tile_h, int *tile_w);
 cudaError_t launch_fused_blur_ratio(const FusedArgs &a, cudaStream_t s);
 cudaError_t launch_fused_correlate_update(const FusedArgs &a, cudaStream_t s);
 
+// Tensor-core route (tc.cu): the same two kernels with BF16x3 tcgen05 passes.
+bool tc_supported(int K);
+void tc_tile_shape(int K, int *tile_h, int *tile_w);
+cudaError_t launch_tc_blur_ratio(const FusedArgs &a, cudaStream_t s);
+cudaError_t launch_tc_correlate_update(const FusedArgs &a, cudaStream_t s);
+
 // Fourier route (fft.cu).
 namespace fftr {
 constexpr int kMaxRadices = 16;
