@@ -15,24 +15,25 @@
 // product, against 2^-24 for FP32 arithmetic.
 //
 // Tile: TY x 128 outputs of one plane (TY = 96 for K <= 33, 64 above); the
-// input tile is 128 rows (TY + 2R of them used) x KA columns.
+// input tile is 128 rows (TY + 2R of them used) x KA columns.  An MMA costs
+// about the same issue time up to N = 128, so both passes use wide MMAs:
 //
-//   pass 1 (along x):  D1[y_in][x_out] = sum_k A1[y_in][k] T1[k][x_out]
-//       A1 = input tile (BF16 hi/lo, K-major), T1 = Toeplitz matrix of the
-//       horizontal taps, one 32-column output chunk per MMA group with a
-//       K window of 32 + 2R (+ alignment) input columns;  D1 in tensor memory
-//       (lanes = input rows, 128 columns).
-//   hand-over: each thread reads its lane (one input row) of D1, splits the
-//       values and stores them as A2 = D1^T (MN-major, x_out contiguous).
+//   pass 1 (along x):  D1[x_out][y_in] = sum_k T1[x_out][k] B1[k][y_in]
+//       T1 = Toeplitz matrix of the horizontal taps, built by the threads in
+//       tensor memory (A operand, one row per lane); B1 = input tile (BF16
+//       hi/lo, K-major in shared memory); N = 128 input rows, K = KA columns.
+//   split:  each thread reads its lane of D1 (one output column) and writes
+//       it back as BF16 hi/lo: A2 = D1, again an A operand in tensor memory.
 //   pass 2 (along y):  D2[x_out][y_out] = sum_k A2[x_out][k] T2[k][y_out]
-//       T2 = Toeplitz matrix of the vertical taps, 32-row output chunks;
-//       every SVD term accumulates into the same D2 (lanes = output columns).
+//       T2 = Toeplitz matrix of the vertical taps (shared memory), N = TY,
+//       K = 128 input rows; every SVD term accumulates into the same D2.
 //   epilogue: each thread reads its lane of D2, i.e. one output column, and
 //       walks its rows: coalesced loads of phi / psi and stores of r / psi.
 //
-// Shared memory: the FP32 staging tile (TMA destination, later reused for
-// A2), A1 hi/lo, and two buffers of Toeplitz operands built per term from
-// the factor taps.  One CTA per SM (about 195-217 KB), 512 threads.
+// The FP32 staging tile (TMA destination) is free once converted to B1, so
+// the next tile's copy overlaps all of the current tile's MMAs.  One CTA per
+// SM (about 194-215 KB of shared memory, all 512 tensor-memory columns),
+// 512 threads.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -52,7 +53,7 @@ namespace {
 
 constexpr int kThreads = 512;
 constexpr long long kDrainBudget = 4000000000LL;
-constexpr int kTmemCols = 256;
+constexpr int kTmemCols = 512;
 
 template <int K>
 struct Geo {
@@ -61,36 +62,31 @@ struct Geo {
     static constexpr int COL0 = R4 - R;           // input column of x0 - R within the staging tile
     static constexpr int TX = 128;
     static constexpr int TY = R == 0 ? 128 : (2 * R <= 32 ? 96 : 64);
-    static constexpr int ROWS = 128;              // input rows = MMA M of pass 1
-    static constexpr int WIN1 = (32 + COL0 + 2 * R + 15) / 16 * 16;
-    static constexpr int NKS1 = WIN1 / 16;
-    static constexpr int KA = 96 + WIN1;          // input columns
+    static constexpr int ROWS = 128;              // input rows = pass-1 N = pass-2 K
+    static constexpr int KA = (128 + COL0 + 2 * R + 15) / 16 * 16;   // input columns = pass-1 K
+    static constexpr int NKS1 = KA / 16;
     static constexpr int NKB = KA / 8;
-    static constexpr int WIN2 = (32 + 2 * R + 15) / 16 * 16;
-    static constexpr int NKS2 = WIN2 / 16;
-    static constexpr int NC2 = TY / 32;
+    static constexpr int NKS2 = ROWS / 16;
     static constexpr int NE = TY / 4;             // output rows per epilogue thread
+    static constexpr int QA = KA / 4;             // T1 columns (values) built per thread
+    // tensor-memory columns
+    static constexpr uint32_t C_T1 = 0, C_T1LO = KA / 2, C_D1 = KA, C_A2 = KA + 128, C_A2LO = KA + 192,
+                              C_D2 = KA + 256;
+    // shared memory
     static constexpr int STAGE_BYTES = ROWS * KA * 4;
-    static constexpr uint32_t A1_LBO = 128 * 16 + 16;   // k-group stride; +16 B spreads banks
-    static constexpr int A1_BYTES = NKB * A1_LBO;
-    static constexpr uint32_t A2_LBO = 128;              // k-group stride (8 rows x 16 B)
-    static constexpr uint32_t A2_SBO = 128 * 16;         // m-group stride (128 k rows x 16 B)
-    static constexpr int A2_BYTES = 16 * A2_SBO;
-    static constexpr uint32_t T_LBO = 32 * 16;           // k-group stride of a 32-column operand
-    static constexpr uint32_t T_SBO = 128;
-    static constexpr int T1_BYTES = WIN1 / 8 * T_LBO;
-    static constexpr int T2_BYTES = WIN2 / 8 * T_LBO;
-    static constexpr int TBUF_BYTES = 2 * (T1_BYTES + T2_BYTES);
+    static constexpr uint32_t B1_LBO = 128 * 16 + 16;   // k-group stride; +16 B spreads banks
+    static constexpr int B1_BYTES = NKB * B1_LBO;
+    static constexpr uint32_t T2_LBO = TY * 16;         // k-group stride (TY rows x 16 B)
+    static constexpr int T2_BYTES = ROWS / 8 * T2_LBO;
     static constexpr int OFF_STAGE = 1024;
-    static constexpr int OFF_A1 = OFF_STAGE + STAGE_BYTES;
-    static constexpr int OFF_T = OFF_A1 + 2 * A1_BYTES;
-    static constexpr int SMEM_USED = OFF_T + 2 * TBUF_BYTES;
+    static constexpr int OFF_B1 = OFF_STAGE + STAGE_BYTES;
+    static constexpr int OFF_T2 = OFF_B1 + 2 * B1_BYTES;
+    static constexpr int SMEM_USED = OFF_T2 + 2 * T2_BYTES;
     static constexpr int SMEM_BYTES = SMEM_USED + 128;   // room to align the dynamic base
-    static_assert(TY + 2 * R <= ROWS, "input rows fit the pass-1 M");
-    static_assert((NC2 - 1) * 32 + WIN2 <= ROWS, "pass-2 windows stay inside the input rows");
-    static_assert(96 + WIN1 == KA && KA % 16 == 0, "pass-1 windows");
-    static_assert(2 * A2_BYTES <= STAGE_BYTES, "A2 fits in the staging tile");
-    static_assert(128 + TY <= kTmemCols, "D1 + D2 columns");
+    static_assert(TY + 2 * R <= ROWS, "input rows fit pass 1's N");
+    static_assert(KA >= 128 + COL0 + 2 * R && KA % 16 == 0, "pass-1 K covers the halo");
+    static_assert(QA % 2 == 0, "T1 columns pair up");
+    static_assert(C_D2 + TY <= kTmemCols, "tensor-memory columns");
     static_assert(SMEM_BYTES <= 232448, "shared memory per CTA");
 };
 
@@ -104,21 +100,23 @@ __device__ __forceinline__ unsigned char *align128(unsigned char *p) {
     return reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(p) + 127) & ~static_cast<uintptr_t>(127));
 }
 
+// BF16 hi and lo parts of two FP32 values, packed (first value in the low half).
+__device__ __forceinline__ void split2(float x0, float x1, uint32_t &hi, uint32_t &lo) {
+    const __nv_bfloat162 hb = __floats2bfloat162_rn(x0, x1);
+    hi = *reinterpret_cast<const uint32_t *>(&hb);
+    const float h0 = __uint_as_float(hi << 16);
+    const float h1 = __uint_as_float(hi & 0xFFFF0000u);
+    const __nv_bfloat162 lb = __floats2bfloat162_rn(x0 - h0, x1 - h1);
+    lo = *reinterpret_cast<const uint32_t *>(&lb);
+}
+
 // Split 8 FP32 values into BF16 hi and lo parts (8 each, element 0 in the low
 // half of the first word).
 __device__ __forceinline__ void split8(const float (&x)[8], uint4 &hi, uint4 &lo) {
-    uint32_t h[4], l[4];
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        const __nv_bfloat162 hb = __floats2bfloat162_rn(x[2 * i], x[2 * i + 1]);
-        h[i] = *reinterpret_cast<const uint32_t *>(&hb);
-        const float h0 = __uint_as_float(h[i] << 16);
-        const float h1 = __uint_as_float(h[i] & 0xFFFF0000u);
-        const __nv_bfloat162 lb = __floats2bfloat162_rn(x[2 * i] - h0, x[2 * i + 1] - h1);
-        l[i] = *reinterpret_cast<const uint32_t *>(&lb);
-    }
-    hi = make_uint4(h[0], h[1], h[2], h[3]);
-    lo = make_uint4(l[0], l[1], l[2], l[3]);
+    split2(x[0], x[1], hi.x, lo.x);
+    split2(x[2], x[3], hi.y, lo.y);
+    split2(x[4], x[5], hi.z, lo.z);
+    split2(x[6], x[7], hi.w, lo.w);
 }
 
 __device__ __forceinline__ void sts128(unsigned char *p, const uint4 &v) { *reinterpret_cast<uint4 *>(p) = v; }
@@ -149,10 +147,11 @@ __device__ void load_stage_sw(float *__restrict__ stage, const float *__restrict
     }
 }
 
-// Staging tile (FP32, row-major) -> A1 hi/lo (K-major BF16).  Item = one
-// row and 8 consecutive columns.
+// Staging tile (FP32, row-major) -> B1 hi/lo (BF16, K-major: element
+// (input row n, column k) at n*16 + (k/8)*B1_LBO + (k%8)*2).  Item = one row
+// and 8 consecutive columns.
 template <int K>
-__device__ __forceinline__ void convert_a1(const float *__restrict__ stage, unsigned char *a1) {
+__device__ __forceinline__ void convert_b1(const float *__restrict__ stage, unsigned char *b1) {
     using G = Geo<K>;
     constexpr int ITEMS = G::ROWS * G::NKB;
     for (int it = threadIdx.x; it < ITEMS; it += kThreads) {
@@ -163,110 +162,106 @@ __device__ __forceinline__ void convert_a1(const float *__restrict__ stage, unsi
         const float x[8] = {p.x, p.y, p.z, p.w, q.x, q.y, q.z, q.w};
         uint4 hi, lo;
         split8(x, hi, lo);
-        const uint32_t off = static_cast<uint32_t>(m) * 16 + static_cast<uint32_t>(kb) * G::A1_LBO;
-        sts128(a1 + off, hi);
-        sts128(a1 + G::A1_BYTES + off, lo);
+        const uint32_t off = static_cast<uint32_t>(m) * 16 + static_cast<uint32_t>(kb) * G::B1_LBO;
+        sts128(b1 + off, hi);
+        sts128(b1 + G::B1_BYTES + off, lo);
     }
 }
 
-// Toeplitz operands of one term (correlation-form taps: out(i) = sum_j t[j]
-// in(i + j - R)): T1[k][n] = w[k - n - COL0] (horizontal), T2[k][n] = u[k - n]
-// (vertical), each K-major BF16 hi/lo.  Item = one column n and 8 rows k.
+// The Toeplitz operands of one term (correlation-form taps: out(i) = sum_j
+// t[j] in(i + j - R)):
+//   T1[x_out][k] = w[k - x_out - COL0]   (tensor memory, lane x_out; warp w
+//                                         writes columns QA*(w/4) .. of its lanes)
+//   T2[k][y_out] = u[k - y_out]          (shared memory, K-major, item = one
+//                                         output row and 8 consecutive k)
+// Callers make the writes visible (tcgen05 wait, proxy fence, barrier).
 template <int K>
-__device__ __forceinline__ void build_toeplitz(const float *__restrict__ u, const float *__restrict__ w,
-                                               unsigned char *tb) {
+__device__ __forceinline__ void build_toeplitz(const float *__restrict__ u, const float *__restrict__ w, uint32_t tmem,
+                                               unsigned char *t2) {
     using G = Geo<K>;
-    constexpr int I1 = 32 * (G::WIN1 / 8), I2 = 32 * (G::WIN2 / 8);
-    for (int it = threadIdx.x; it < I1 + I2; it += kThreads) {
-        const bool second = it >= I1;
-        const int i2 = second ? it - I1 : it;
-        const int n = i2 & 31, kg = i2 >> 5;
-        const float *t = second ? u : w;
-        const int off = second ? 0 : G::COL0;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int x_out = 32 * (warp & 3) + lane;
+    const int k0 = (warp >> 2) * G::QA;
+    uint32_t hi[G::QA / 2], lo[G::QA / 2];
+#pragma unroll
+    for (int c = 0; c < G::QA / 2; ++c) {
+        const int j0 = k0 + 2 * c - x_out - G::COL0;
+        const float a = (j0 >= 0 && j0 < K) ? __ldg(w + j0) : 0.0f;
+        const float b = (j0 + 1 >= 0 && j0 + 1 < K) ? __ldg(w + j0 + 1) : 0.0f;
+        split2(a, b, hi[c], lo[c]);
+    }
+    const uint32_t lane_off = static_cast<uint32_t>(32 * (warp & 3)) << 16;
+    tc5::st_cols<G::QA / 2>(tmem + lane_off + G::C_T1 + k0 / 2, hi);
+    tc5::st_cols<G::QA / 2>(tmem + lane_off + G::C_T1LO + k0 / 2, lo);
+    constexpr int ITEMS = G::TY * (G::ROWS / 8);
+    for (int it = threadIdx.x; it < ITEMS; it += kThreads) {
+        const int n = it % G::TY, kg = it / G::TY;
         float x[8];
 #pragma unroll
         for (int e = 0; e < 8; ++e) {
-            const int j = 8 * kg + e - n - off;
-            x[e] = (j >= 0 && j < K) ? __ldg(t + j) : 0.0f;
+            const int j = 8 * kg + e - n;
+            x[e] = (j >= 0 && j < K) ? __ldg(u + j) : 0.0f;
         }
-        uint4 hi, lo;
-        split8(x, hi, lo);
-        unsigned char *base = tb + (second ? 2 * G::T1_BYTES : 0);
-        const int bytes = second ? G::T2_BYTES : G::T1_BYTES;
-        const uint32_t addr = (n & 7) * 16 + (n >> 3) * G::T_SBO + kg * G::T_LBO;
-        sts128(base + addr, hi);
-        sts128(base + bytes + addr, lo);
+        uint4 h, l;
+        split8(x, h, l);
+        const uint32_t addr = (n & 7) * 16 + (n >> 3) * 128 + kg * G::T2_LBO;
+        sts128(t2 + addr, h);
+        sts128(t2 + G::T2_BYTES + addr, l);
+    }
+    tc5::wait_st();
+}
+
+// Pass 1 MMAs (one thread): D1 = T1 (tensor memory) x B1 (shared memory).
+template <int K>
+__device__ __forceinline__ void issue_pass1(uint32_t tmem, uint32_t b1) {
+    using G = Geo<K>;
+    constexpr uint32_t idesc = tc5::idesc_bf16(128, 128, false, false);
+    const uint32_t b1lo = b1 + G::B1_BYTES;
+#pragma unroll 1
+    for (int s = 0; s < G::NKS1; ++s) {
+        const uint32_t bo = static_cast<uint32_t>(2 * s) * G::B1_LBO;
+        const uint64_t bh = tc5::sdesc(b1 + bo, G::B1_LBO, 128), bl = tc5::sdesc(b1lo + bo, G::B1_LBO, 128);
+        const uint32_t ah = tmem + G::C_T1 + 8 * s, al = tmem + G::C_T1LO + 8 * s;
+        tc5::mma_bf16_ta(tmem + G::C_D1, al, bh, idesc, s > 0);
+        tc5::mma_bf16_ta(tmem + G::C_D1, ah, bl, idesc, 1);
+        tc5::mma_bf16_ta(tmem + G::C_D1, ah, bh, idesc, 1);
     }
 }
 
-// Pass 1 MMAs (one thread): D1 columns [32c, 32c+32) for c = 0..3.
+// Pass 2 MMAs (one thread): D2 (+)= A2 (tensor memory) x T2 (shared memory).
 template <int K>
-__device__ __forceinline__ void issue_pass1(uint32_t tmem, uint32_t a1, uint32_t tb) {
+__device__ __forceinline__ void issue_pass2(uint32_t tmem, uint32_t t2, bool accumulate) {
     using G = Geo<K>;
-    constexpr uint32_t idesc = tc5::idesc_bf16(128, 32, false, false);
-    const uint32_t a1lo = a1 + G::A1_BYTES, t1lo = tb + G::T1_BYTES;
+    constexpr uint32_t idesc = tc5::idesc_bf16(128, G::TY, false, false);
+    const uint32_t t2lo = t2 + G::T2_BYTES;
 #pragma unroll 1
-    for (int c = 0; c < 4; ++c) {
-#pragma unroll 1
-        for (int s = 0; s < G::NKS1; ++s) {
-            const uint32_t ao = static_cast<uint32_t>(4 * c + 2 * s) * G::A1_LBO;
-            const uint32_t bo = static_cast<uint32_t>(2 * s) * G::T_LBO;
-            const uint64_t ah = tc5::sdesc(a1 + ao, G::A1_LBO, 128), al = tc5::sdesc(a1lo + ao, G::A1_LBO, 128);
-            const uint64_t bh = tc5::sdesc(tb + bo, G::T_LBO, G::T_SBO), bl = tc5::sdesc(t1lo + bo, G::T_LBO, G::T_SBO);
-            const uint32_t d = tmem + 32 * c;
-            tc5::mma_bf16(d, al, bh, idesc, s > 0);
-            tc5::mma_bf16(d, ah, bl, idesc, 1);
-            tc5::mma_bf16(d, ah, bh, idesc, 1);
-        }
+    for (int s = 0; s < G::NKS2; ++s) {
+        const uint32_t bo = static_cast<uint32_t>(2 * s) * G::T2_LBO;
+        const uint64_t bh = tc5::sdesc(t2 + bo, G::T2_LBO, 128), bl = tc5::sdesc(t2lo + bo, G::T2_LBO, 128);
+        const uint32_t ah = tmem + G::C_A2 + 8 * s, al = tmem + G::C_A2LO + 8 * s;
+        tc5::mma_bf16_ta(tmem + G::C_D2, al, bh, idesc, (accumulate || s > 0) ? 1u : 0u);
+        tc5::mma_bf16_ta(tmem + G::C_D2, ah, bl, idesc, 1);
+        tc5::mma_bf16_ta(tmem + G::C_D2, ah, bh, idesc, 1);
     }
 }
 
-// Pass 2 MMAs (one thread): D2 columns [128 + 32c, +32) for c < NC2.
+// D1 -> A2 in place per lane: warp w reads input rows 32*(w/4).. of its
+// lanes' D1 and writes them back as BF16 hi/lo pairs.
 template <int K>
-__device__ __forceinline__ void issue_pass2(uint32_t tmem, uint32_t a2, uint32_t tb, bool accumulate) {
+__device__ __forceinline__ void split_d1(uint32_t tmem) {
     using G = Geo<K>;
-    constexpr uint32_t idesc = tc5::idesc_bf16(128, 32, true, false);
-    const uint32_t a2lo = a2 + G::A2_BYTES;
-    const uint32_t t2 = tb + 2 * G::T1_BYTES, t2lo = t2 + G::T2_BYTES;
-#pragma unroll 1
-    for (int c = 0; c < G::NC2; ++c) {
-#pragma unroll 1
-        for (int s = 0; s < G::NKS2; ++s) {
-            const uint32_t ao = static_cast<uint32_t>(4 * c + 2 * s) * G::A2_LBO;
-            const uint32_t bo = static_cast<uint32_t>(2 * s) * G::T_LBO;
-            const uint64_t ah = tc5::sdesc(a2 + ao, G::A2_LBO, G::A2_SBO), al = tc5::sdesc(a2lo + ao, G::A2_LBO, G::A2_SBO);
-            const uint64_t bh = tc5::sdesc(t2 + bo, G::T_LBO, G::T_SBO), bl = tc5::sdesc(t2lo + bo, G::T_LBO, G::T_SBO);
-            const uint32_t d = tmem + 128 + 32 * c;
-            tc5::mma_bf16(d, al, bh, idesc, (accumulate || s > 0) ? 1u : 0u);
-            tc5::mma_bf16(d, ah, bl, idesc, 1);
-            tc5::mma_bf16(d, ah, bh, idesc, 1);
-        }
-    }
-}
-
-// D1 -> A2: warp w reads lanes 32*(w%4).. (input rows) x columns 32*(w/4)..
-// (one output chunk) and stores them transposed, BF16 hi/lo, MN-major.
-template <int K>
-__device__ __forceinline__ void handover(uint32_t tmem, unsigned char *a2) {
-    using G = Geo<K>;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int qd = warp & 3, c = warp >> 2;
+    const int warp = threadIdx.x >> 5;
+    const uint32_t lane_off = static_cast<uint32_t>(32 * (warp & 3)) << 16;
+    const int cg = warp >> 2;
     uint32_t r[32];
-    tc5::ld32(tmem + (static_cast<uint32_t>(32 * qd) << 16) + 32 * c, r);
+    tc5::ld32(tmem + lane_off + G::C_D1 + 32 * cg, r);
     tc5::wait_ld();
-    const uint32_t row = 32 * qd + lane;   // k index of A2
+    uint32_t hi[16], lo[16];
 #pragma unroll
-    for (int v = 0; v < 4; ++v) {
-        const float x[8] = {__uint_as_float(r[8 * v]),     __uint_as_float(r[8 * v + 1]),
-                            __uint_as_float(r[8 * v + 2]), __uint_as_float(r[8 * v + 3]),
-                            __uint_as_float(r[8 * v + 4]), __uint_as_float(r[8 * v + 5]),
-                            __uint_as_float(r[8 * v + 6]), __uint_as_float(r[8 * v + 7])};
-        uint4 hi, lo;
-        split8(x, hi, lo);
-        const uint32_t off = static_cast<uint32_t>(4 * c + v) * G::A2_SBO + row * 16;
-        sts128(a2 + off, hi);
-        sts128(a2 + G::A2_BYTES + off, lo);
-    }
+    for (int c = 0; c < 16; ++c) split2(__uint_as_float(r[2 * c]), __uint_as_float(r[2 * c + 1]), hi[c], lo[c]);
+    tc5::st16(tmem + lane_off + G::C_A2 + 16 * cg, hi);
+    tc5::st16(tmem + lane_off + G::C_A2LO + 16 * cg, lo);
+    tc5::wait_st();
 }
 
 // This thread's column of D2: NE consecutive output rows.
@@ -275,7 +270,7 @@ __device__ __forceinline__ void read_d2(uint32_t tmem, float (&d)[Geo<K>::NE]) {
     using G = Geo<K>;
     const int warp = threadIdx.x >> 5;
     const int qd = warp & 3, cg = warp >> 2;
-    const uint32_t base = tmem + (static_cast<uint32_t>(32 * qd) << 16) + 128 + cg * G::NE;
+    const uint32_t base = tmem + (static_cast<uint32_t>(32 * qd) << 16) + G::C_D2 + cg * G::NE;
 #pragma unroll
     for (int j = 0; j < G::NE / 8; ++j) tc5::ld8(base + 8 * j, reinterpret_cast<uint32_t *>(d) + 8 * j);
     tc5::wait_ld();
@@ -347,61 +342,45 @@ __device__ __forceinline__ void teardown(uint32_t tmem) {
     if (threadIdx.x < 32) tc5::dealloc(tmem, kTmemCols);
 }
 
-// The Toeplitz operands of every term a launch uses stay resident (built once
-// per CTA) when there are at most this many; otherwise two buffers alternate
-// and each term's operands are built before its MMAs.
-constexpr int kResidentTerms = 2;
-
 // One group of SVD terms (a PSF's blur, or a view's correlation) on the input
-// tile in A1: D2 = sum over the terms.  Returns with every MMA issued and
-// their completion committed to bar_mma (the caller waits).  With
-// `a2_last_in_a1` the last term's A2 goes to the A1 region (A1 is not read
-// again), so the staging tile is free early: thread 0 calls `stage_free()`
-// as soon as nothing can read it any more.  resident_slot >= 0: the terms'
-// operands are resident from that slot on.  False if a wait timed out.
-template <int K, typename F>
+// tile in B1: D2 = sum over the terms.  Enter with every earlier MMA complete;
+// returns with the last MMAs issued and committed to bar_mma (the caller
+// waits, then reads D2).  False if a wait timed out.
+template <int K>
 __device__ bool run_terms(const FusedArgs &a, const Smem &s, uint32_t tmem, unsigned char *smem, int term0,
-                          int n_terms, int kind_u, int kind_w, int resident_slot, bool a2_last_in_a1,
-                          F &&stage_free, uint32_t &ph_mma, int &tbuf) {
+                          int n_terms, int kind_u, int kind_w, uint32_t &ph_mma) {
     using G = Geo<K>;
-    unsigned char *a1 = smem + G::OFF_A1;
+    unsigned char *b1 = smem + G::OFF_B1;
+    unsigned char *t2 = smem + G::OFF_T2;
     for (int q = 0; q < n_terms; ++q) {
-        const bool last = q == n_terms - 1;
-        unsigned char *tb;
-        if (resident_slot >= 0) {
-            tb = smem + G::OFF_T + (resident_slot + q) * G::TBUF_BYTES;
-        } else {
-            tb = smem + G::OFF_T + tbuf * G::TBUF_BYTES;
-            tbuf ^= 1;
-            const float *tq = a.taps + static_cast<long long>(term0 + q) * 4 * K;
-            build_toeplitz<K>(tq + kind_u * K, tq + kind_w * K, tb);
-            tma::fence_proxy_async_smem();
-        }
-        tc5::fence_before();
-        __syncthreads();
-        if (threadIdx.x == 0) {
+        if (q > 0) {
+            // the previous term's pass 2 still reads T2 and A2
+            if (!wait_bar(s.bar_mma, ph_mma, a, s.abort_flag)) return false;
+            ph_mma ^= 1;
             tc5::fence_after();
-            issue_pass1<K>(tmem, tc5::smem_u32(a1), tc5::smem_u32(tb));
-            tc5::commit(s.bar_mma);
-            // one term: the staging tile was last read by the conversion
-            if (last && a2_last_in_a1 && n_terms == 1) stage_free();
         }
-        // pass 1 done, and with it every earlier MMA (D1 and the previous A2 are free)
-        if (!wait_bar(s.bar_mma, ph_mma, a, s.abort_flag)) return false;
-        ph_mma ^= 1;
-        tc5::fence_after();
-        if (threadIdx.x == 0 && last && a2_last_in_a1 && n_terms > 1) stage_free();
-        unsigned char *a2 = (last && a2_last_in_a1) ? a1 : smem + G::OFF_STAGE;
-        handover<K>(tmem, a2);
+        const float *tq = a.taps + static_cast<long long>(term0 + q) * 4 * K;
+        build_toeplitz<K>(tq + kind_u * K, tq + kind_w * K, tmem, t2);
         tma::fence_proxy_async_smem();
         tc5::fence_before();
         __syncthreads();
         if (threadIdx.x == 0) {
             tc5::fence_after();
-            issue_pass2<K>(tmem, tc5::smem_u32(a2), tc5::smem_u32(tb), q > 0);
+            issue_pass1<K>(tmem, tc5::smem_u32(b1));
+            tc5::commit(s.bar_mma);
+        }
+        if (!wait_bar(s.bar_mma, ph_mma, a, s.abort_flag)) return false;
+        ph_mma ^= 1;
+        tc5::fence_after();
+        split_d1<K>(tmem);
+        tc5::fence_before();
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            tc5::fence_after();
+            issue_pass2<K>(tmem, tc5::smem_u32(t2), q > 0);
+            tc5::commit(s.bar_mma);
         }
     }
-    if (threadIdx.x == 0) tc5::commit(s.bar_mma);
     return true;
 }
 
@@ -411,18 +390,6 @@ __device__ __forceinline__ bool finish_terms(const FusedArgs &a, const Smem &s, 
     ph_mma ^= 1;
     tc5::fence_after();
     return true;
-}
-
-// Build the operands of up to kResidentTerms terms once (slots 0, 1, ...).
-template <int K>
-__device__ __forceinline__ void build_resident(const FusedArgs &a, const int *terms, int n, int kind_u, int kind_w,
-                                               unsigned char *smem) {
-    using G = Geo<K>;
-    for (int i = 0; i < n; ++i) {
-        const float *tq = a.taps + static_cast<long long>(terms[i]) * 4 * K;
-        build_toeplitz<K>(tq + kind_u * K, tq + kind_w * K, smem + G::OFF_T + i * G::TBUF_BYTES);
-    }
-    tma::fence_proxy_async_smem();
 }
 
 // Raw data of view v at this thread's output column and rows (NE values,
@@ -460,6 +427,38 @@ __device__ __forceinline__ void store_ratio(const FusedArgs &a, int v, int p, in
     }
 }
 
+// Input tile of (tile t, z) into B1, then the staging tile is released: thread
+// 0 requests the next copy (plane index nz of tile nt) if there is one.
+// Returns false if the tile's copy timed out.
+template <int K>
+__device__ __forceinline__ bool take_tile(const TcParams &kp, const Smem &s, unsigned char *smem, bool use_tma,
+                                          const float *sw_src, float sw_fill, const Tile &c, bool next, const Tile &c2,
+                                          int nz, uint32_t &ph_tma, bool &tma_pending) {
+    using G = Geo<K>;
+    const FusedArgs &a = kp.a;
+    float *stage = reinterpret_cast<float *>(smem + G::OFF_STAGE);
+    if (use_tma) {
+        if (!wait_bar(s.bar_tma, ph_tma, a, s.abort_flag)) {
+            tma_pending = false;   // drained by the wait
+            return false;
+        }
+        ph_tma ^= 1;
+        tma_pending = false;
+    } else {
+        load_stage_sw<K>(stage, sw_src, sw_fill, c.y0, c.x0, a.H, a.W, a.circular);
+        __syncthreads();
+    }
+    convert_b1<K>(stage, smem + G::OFF_B1);
+    tma::fence_proxy_async_smem();
+    __syncthreads();
+    if (use_tma && next && threadIdx.x == 0) {
+        tma::mbar_arrive_expect_tx(s.bar_tma, G::STAGE_BYTES);
+        tma::load_3d(stage, &kp.map, s.bar_tma, c2.x0 - G::R4, c2.y0 - G::R, nz);
+        tma_pending = true;   // thread 0's copy of the flag is the one used
+    }
+    return true;
+}
+
 // Persistent kernel A: blur of every PSF group in use, then the ratios.
 template <int K>
 __global__ void __launch_bounds__(kThreads, 1) tc_blur_ratio_kernel(const __grid_constant__ TcParams kp) {
@@ -477,29 +476,19 @@ __global__ void __launch_bounds__(kThreads, 1) tc_blur_ratio_kernel(const __grid
     const long long plane_px = static_cast<long long>(a.H) * a.W;
     const bool use_tma = kp.use_tma && a.psi_in != nullptr;
     uint32_t ph_tma = 0, ph_mma = 0;
-    int tbuf = 0;
     bool tma_pending = false;
 
-    // groups in use, the last of them, and the terms they need
-    int last_g = -1, n_terms = 0, terms[kResidentTerms] = {0, 0};
-    for (int g = 0; g < a.ft.n_groups; ++g) {
-        bool used = false;
-        for (int v = a.view_lo; v < a.view_hi; ++v) used |= (a.ft.group[v] == g);
-        if (!used) continue;
-        last_g = g;
-        const int lead = a.ft.group_leader[g];
-        for (int q = 0; q < a.ft.rank[lead]; ++q, ++n_terms)
-            if (n_terms < kResidentTerms) terms[n_terms] = a.ft.tap_off[lead] + q;
-    }
-    const bool resident = n_terms <= kResidentTerms;
-    if (resident) build_resident<K>(a, terms, n_terms, 0, 1, smem);
+    int last_g = -1;
+    for (int g = 0; g < a.ft.n_groups; ++g)
+        for (int v = a.view_lo; v < a.view_hi; ++v)
+            if (a.ft.group[v] == g) last_g = g;
 
     if (use_tma && threadIdx.x == 0 && static_cast<int>(blockIdx.x) < n_tiles) {
         const Tile c = tile_of<K>(blockIdx.x, tiles_x, tiles_y);
         tma::mbar_arrive_expect_tx(s.bar_tma, G::STAGE_BYTES);
         tma::load_3d(stage, &kp.map, s.bar_tma, c.x0 - G::R4, c.y0 - G::R, c.p);
+        tma_pending = true;
     }
-    tma_pending = use_tma && static_cast<int>(blockIdx.x) < n_tiles;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int x_out = 32 * (warp & 3) + lane;
     const int row0 = (warp >> 2) * G::NE;
@@ -507,42 +496,19 @@ __global__ void __launch_bounds__(kThreads, 1) tc_blur_ratio_kernel(const __grid
 
     for (int t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
         const Tile c = tile_of<K>(t, tiles_x, tiles_y);
-        if (use_tma) {
-            if (!wait_bar(s.bar_tma, ph_tma, a, s.abort_flag)) {
-                tma_pending = false;   // drained by the wait
-                break;
-            }
-            ph_tma ^= 1;
-            tma_pending = false;
-        } else {
-            const float mean = a.psi_in ? 0.0f : __ldg(a.means + c.p);
-            load_stage_sw<K>(stage, a.psi_in ? a.psi_in + c.p * plane_px : nullptr, mean, c.y0, c.x0, a.H, a.W,
-                             a.circular);
-            __syncthreads();
-        }
-        convert_a1<K>(stage, smem + G::OFF_A1);
-        auto stage_free = [&]() {
-            const int nt = t + gridDim.x;
-            if (use_tma && nt < n_tiles) {
-                const Tile c2 = tile_of<K>(nt, tiles_x, tiles_y);
-                tma::fence_proxy_async_smem();
-                tma::mbar_arrive_expect_tx(s.bar_tma, G::STAGE_BYTES);
-                tma::load_3d(stage, &kp.map, s.bar_tma, c2.x0 - G::R4, c2.y0 - G::R, c2.p);
-                tma_pending = true;   // thread 0's copy of the flag is the one used
-            }
-        };
+        const int nt = t + gridDim.x;
+        const Tile c2 = tile_of<K>(nt < n_tiles ? nt : t, tiles_x, tiles_y);
+        const float mean = a.psi_in ? 0.0f : __ldg(a.means + c.p);
+        ok = take_tile<K>(kp, s, smem, use_tma, a.psi_in ? a.psi_in + c.p * plane_px : nullptr, mean, c,
+                          nt < n_tiles, c2, c2.p, ph_tma, tma_pending);
         const int x = c.x0 + x_out;
-        int slot = 0;
         for (int g = 0; g <= last_g && ok; ++g) {
             int v0 = -1;
             for (int v = a.view_lo; v < a.view_hi; ++v)
                 if (a.ft.group[v] == g && v0 < 0) v0 = v;
             if (v0 < 0) continue;
             const int lead = a.ft.group_leader[g];
-            const int rank = a.ft.rank[lead];
-            ok = run_terms<K>(a, s, tmem, smem, a.ft.tap_off[lead], rank, 0, 1, resident ? slot : -1, g == last_g,
-                              stage_free, ph_mma, tbuf);
-            slot += rank;
+            ok = run_terms<K>(a, s, tmem, smem, a.ft.tap_off[lead], a.ft.rank[lead], 0, 1, ph_mma);
             if (!ok) break;
             // the first view's data load overlaps the MMAs
             uint32_t phi[G::NE];
@@ -585,22 +551,14 @@ __global__ void __launch_bounds__(kThreads, 1) tc_correlate_update_kernel(const 
     const long long plane_px = static_cast<long long>(a.H) * a.W;
     const bool use_tma = kp.use_tma != 0;
     uint32_t ph_tma = 0, ph_mma = 0;
-    int tbuf = 0;
     bool tma_pending = false;
-
-    int n_terms = 0, terms[kResidentTerms] = {0, 0};
-    for (int v = a.view_lo; v < a.view_hi; ++v)
-        for (int q = 0; q < a.ft.crank[v]; ++q, ++n_terms)
-            if (n_terms < kResidentTerms) terms[n_terms] = a.ft.ctap_off[v] + q;
-    const bool resident = n_terms <= kResidentTerms;
-    if (resident) build_resident<K>(a, terms, n_terms, 2, 3, smem);
 
     if (use_tma && threadIdx.x == 0 && static_cast<int>(blockIdx.x) < n_tiles) {
         const Tile c = tile_of<K>(blockIdx.x, tiles_x, tiles_y);
         tma::mbar_arrive_expect_tx(s.bar_tma, G::STAGE_BYTES);
         tma::load_3d(stage, &kp.map, s.bar_tma, c.x0 - G::R4, c.y0 - G::R, a.view_lo * a.P + c.p);
+        tma_pending = true;
     }
-    tma_pending = use_tma && static_cast<int>(blockIdx.x) < n_tiles;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int x_out = 32 * (warp & 3) + lane;
     const int row0 = (warp >> 2) * G::NE;
@@ -611,40 +569,17 @@ __global__ void __launch_bounds__(kThreads, 1) tc_correlate_update_kernel(const 
         float prod[G::NE];
 #pragma unroll
         for (int j = 0; j < G::NE; ++j) prod[j] = 1.0f;
-        int slot = 0;
-        for (int v = a.view_lo; v < a.view_hi; ++v) {
-            if (use_tma) {
-                if (!wait_bar(s.bar_tma, ph_tma, a, s.abort_flag)) {
-                    tma_pending = false;
-                    ok = false;
-                    break;
-                }
-                ph_tma ^= 1;
-                tma_pending = false;
-            } else {
-                load_stage_sw<K>(stage, a.ratio + (static_cast<long long>(v) * a.P + c.p) * plane_px, 0.0f, c.y0,
-                                 c.x0, a.H, a.W, a.circular);
-                __syncthreads();
-            }
-            convert_a1<K>(stage, smem + G::OFF_A1);
-            // the staging tile is free early: request the next (view, tile)
+        for (int v = a.view_lo; v < a.view_hi && ok; ++v) {
             int nv = v + 1, nt = t;
             if (nv >= a.view_hi) {
                 nv = a.view_lo;
                 nt = t + gridDim.x;
             }
-            auto stage_free = [&]() {
-                if (use_tma && nt < n_tiles) {
-                    const Tile c2 = tile_of<K>(nt, tiles_x, tiles_y);
-                    tma::fence_proxy_async_smem();
-                    tma::mbar_arrive_expect_tx(s.bar_tma, G::STAGE_BYTES);
-                    tma::load_3d(stage, &kp.map, s.bar_tma, c2.x0 - G::R4, c2.y0 - G::R, nv * a.P + c2.p);
-                    tma_pending = true;   // thread 0's copy of the flag is the one used
-                }
-            };
-            ok = run_terms<K>(a, s, tmem, smem, a.ft.ctap_off[v], a.ft.crank[v], 2, 3, resident ? slot : -1, true,
-                              stage_free, ph_mma, tbuf);
-            slot += a.ft.crank[v];
+            const Tile c2 = tile_of<K>(nt < n_tiles ? nt : t, tiles_x, tiles_y);
+            ok = take_tile<K>(kp, s, smem, use_tma, a.ratio + (static_cast<long long>(v) * a.P + c.p) * plane_px,
+                              0.0f, c, nt < n_tiles, c2, nv * a.P + c2.p, ph_tma, tma_pending);
+            if (!ok) break;
+            ok = run_terms<K>(a, s, tmem, smem, a.ft.ctap_off[v], a.ft.crank[v], 2, 3, ph_mma);
             if (!ok) break;
             ok = finish_terms(a, s, ph_mma);
             if (!ok) break;

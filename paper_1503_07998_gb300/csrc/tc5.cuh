@@ -107,5 +107,61 @@ __device__ __forceinline__ void ld8(uint32_t taddr, uint32_t *r) {
 
 __device__ __forceinline__ void wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
+// One thread: D (tensor memory) = A * B (+ D), A from tensor memory (BF16,
+// column c of a row holding k = 2c in its low and 2c+1 in its high half), B
+// from shared memory.
+__device__ __forceinline__ void mma_bf16_ta(uint32_t d_tmem, uint32_t a_tmem, uint64_t b, uint32_t idesc,
+                                            uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "r"(a_tmem), "l"(b), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+// Warp: write N consecutive columns of each thread's lane (N = 16, 8, 4, 2, 1).
+__device__ __forceinline__ void st16(uint32_t taddr, const uint32_t *w) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};" ::"r"(
+            taddr),
+        "r"(w[0]), "r"(w[1]), "r"(w[2]), "r"(w[3]), "r"(w[4]), "r"(w[5]), "r"(w[6]), "r"(w[7]), "r"(w[8]), "r"(w[9]),
+        "r"(w[10]), "r"(w[11]), "r"(w[12]), "r"(w[13]), "r"(w[14]), "r"(w[15])
+        : "memory");
+}
+__device__ __forceinline__ void st8(uint32_t taddr, const uint32_t *w) {
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"r"(taddr), "r"(w[0]),
+                 "r"(w[1]), "r"(w[2]), "r"(w[3]), "r"(w[4]), "r"(w[5]), "r"(w[6]), "r"(w[7])
+                 : "memory");
+}
+__device__ __forceinline__ void st4(uint32_t taddr, const uint32_t *w) {
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1,%2,%3,%4};" ::"r"(taddr), "r"(w[0]), "r"(w[1]),
+                 "r"(w[2]), "r"(w[3])
+                 : "memory");
+}
+__device__ __forceinline__ void st2(uint32_t taddr, const uint32_t *w) {
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x2.b32 [%0], {%1,%2};" ::"r"(taddr), "r"(w[0]), "r"(w[1]) : "memory");
+}
+
+// N (compile time, even) consecutive columns from w[0..N).
+template <int N>
+__device__ __forceinline__ void st_cols(uint32_t taddr, const uint32_t *w) {
+    static_assert(N % 2 == 0, "even column counts");
+    int c = 0;
+#pragma unroll
+    for (; c + 16 <= N; c += 16) st16(taddr + c, w + c);
+    if constexpr (N % 16 >= 8) {
+        st8(taddr + c, w + c);
+        c += 8;
+    }
+    if constexpr (N % 8 >= 4) {
+        st4(taddr + c, w + c);
+        c += 4;
+    }
+    if constexpr (N % 4 >= 2) st2(taddr + c, w + c);
+}
+
+__device__ __forceinline__ void wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+
 }  // namespace tc5
 }  // namespace mvd
