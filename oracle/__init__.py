@@ -8,7 +8,8 @@ shares no code with it.
 
 Modules
 -------
-rl       the forward method (Supp. Note 1, update equation; Fig. 1a reslicing)
+rl       the forward method (Supp. Note 1, update equation; Fig. 1a reslicing),
+         with optional per-pixel view weights and the padded-domain estimate
 adjoint  reverse-mode gradient of a Poisson data fit through unrolled
          iterations with respect to the PSFs (PSF calibration)
 variants correlation kernels X_v of the MV-RL variants (Supp. Note 2 sec. 1)
@@ -27,6 +28,9 @@ from .rl import (  # noqa: F401
     rl_step,
     rl_planes,
     reslice,
+    embed_padded,
+    crop_padded,
+    NORM_FLOOR,
 )
 from .adjoint import poisson_nll, rl_loss, rl_loss_and_psf_grad  # noqa: F401
 from .variants import VARIANTS, correlation_kernels  # noqa: F401

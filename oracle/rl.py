@@ -38,6 +38,10 @@ import numpy as np
 ZERO = "zero"
 CIRCULAR = "circular"
 
+# Weighted MV-RL: where a view's weighted footprint n_v = w_v (*) P_v is below
+# this floor the view leaves psi unchanged (its factor is 1).
+NORM_FLOOR = 1e-6
+
 
 def _check_psf(P: np.ndarray) -> int:
     P = np.asarray(P)
@@ -150,10 +154,19 @@ def init_mean(phi: np.ndarray) -> np.ndarray:
 
 
 def rl_step(psi, phi_planes, psfs, boundary=ZERO, eps=1e-6, route="direct",
-            order="simultaneous", corr_kernels=None):
+            order="simultaneous", corr_kernels=None, weights=None):
     """One MV-RL update of one plane (Supp. Note 1, update equation).
 
     psi: [H][W]; phi_planes: [V][H][W]; psfs: [V][K][K].
+
+    weights: optional [V][H][W] per-pixel view weights (the "weights" array
+    of the memory table in Supp. Note 1).  The paper gives no formula for
+    them; the reading taken is the EM update of a Poisson likelihood whose
+    pixels count with weight w_v: each view's factor becomes
+        c_v = ((w_v phi_v / (psi * P_v)) (*) P_v^*) / n_v,   n_v = w_v (*) P_v^*,
+    and c_v = 1 where n_v < NORM_FLOOR (no weighted pixel in reach).  Unit
+    weights with normalised PSFs under the circular boundary give n_v = 1,
+    i.e. the unweighted update.
 
     order="simultaneous": every view's ratio uses the same psi and the
     views' corrections are multiplied, as the equation is printed.
@@ -172,24 +185,31 @@ def rl_step(psi, phi_planes, psfs, boundary=ZERO, eps=1e-6, route="direct",
     else:
         corr_of = lambda img, v, b: corr(img, psfs[v], b)  # noqa: E731
     psi = np.asarray(psi, dtype=np.float64)
+
+    def factor(v, psi_now):
+        blur = conv(psi_now, psfs[v], boundary)
+        data = np.asarray(phi_planes[v], dtype=np.float64)
+        if weights is None:
+            return corr_of(data / np.maximum(blur, eps), v, boundary)
+        w = np.asarray(weights[v], dtype=np.float64)
+        n = corr_of(w, v, boundary)
+        c = corr_of(w * data / np.maximum(blur, eps), v, boundary)
+        return np.where(n >= NORM_FLOOR, c / np.where(n >= NORM_FLOOR, n, 1.0), 1.0)
+
     if order == "sequential":
         for v in range(len(psfs)):
-            blur = conv(psi, psfs[v], boundary)
-            ratio = np.asarray(phi_planes[v], dtype=np.float64) / np.maximum(blur, eps)
-            psi = psi * corr_of(ratio, v, boundary)
+            psi = psi * factor(v, psi)
         return psi
     if order != "simultaneous":
         raise ValueError(f"unknown update order {order!r}")
     update = np.ones_like(psi)
     for v in range(len(psfs)):
-        blur = conv(psi, psfs[v], boundary)
-        ratio = np.asarray(phi_planes[v], dtype=np.float64) / np.maximum(blur, eps)
-        update *= corr_of(ratio, v, boundary)
+        update *= factor(v, psi)
     return psi * update
 
 
 def rl_planes(phi, psfs, iters, boundary=ZERO, eps=1e-6, psi0=None,
-              route="direct", planes=None, order="simultaneous", corr_kernels=None):
+              route="direct", planes=None, order="simultaneous", corr_kernels=None, weights=None):
     """Plane-wise MV-RL over a stack of planes.
 
     phi:  [V][P][H][W] data (any real dtype; used as FP64)
@@ -201,6 +221,7 @@ def rl_planes(phi, psfs, iters, boundary=ZERO, eps=1e-6, psi0=None,
     corr_kernels: optional [V][K][K] kernels X_v of a variant (oracle.variants);
             the ratio of view v is then convolved with X_v instead of being
             correlated with P_v
+    weights: optional [V][P][H][W] per-pixel view weights (see rl_step)
     Returns the estimate after ``iters`` updates, FP64 [n][H][W].
     """
     phi = np.asarray(phi)
@@ -217,7 +238,8 @@ def rl_planes(phi, psfs, iters, boundary=ZERO, eps=1e-6, psi0=None,
         else:
             psi = np.asarray(psi0[p], dtype=np.float64).copy()
         for _ in range(iters):
-            psi = rl_step(psi, phi[:, p], psfs, boundary, eps, route, order, corr_kernels)
+            psi = rl_step(psi, phi[:, p], psfs, boundary, eps, route, order, corr_kernels,
+                          None if weights is None else np.asarray(weights)[:, p])
         out[n] = psi
     return out
 
@@ -226,3 +248,22 @@ def reslice(stack: np.ndarray) -> np.ndarray:
     """Reslice a registered view stack into planes orthogonal to the
     rotation axis (Abstract; Fig. 1a).  [Z][Y][X] -> [Y][Z][X]."""
     return np.ascontiguousarray(np.transpose(np.asarray(stack), (1, 0, 2)))
+
+
+def embed_padded(phi, pad):
+    """Padded-domain estimate (Supp. Table 1 caption: data padded by the PSF
+    size): planes [V][P][H][W] -> zero-padded planes [V][P][H+2pad][W+2pad]
+    and weights that are 1 on the data and 0 in the padding."""
+    phi = np.asarray(phi)
+    V, P, H, W = phi.shape
+    out = np.zeros((V, P, H + 2 * pad, W + 2 * pad), dtype=phi.dtype)
+    out[:, :, pad:pad + H, pad:pad + W] = phi
+    w = np.zeros(out.shape, dtype=np.float64)
+    w[:, :, pad:pad + H, pad:pad + W] = 1.0
+    return out, w
+
+
+def crop_padded(est, pad):
+    """[P][H+2pad][W+2pad] -> [P][H][W] (the data region of the estimate)."""
+    est = np.asarray(est)
+    return est[:, pad:est.shape[1] - pad, pad:est.shape[2] - pad].copy()

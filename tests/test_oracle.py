@@ -386,3 +386,98 @@ def test_variants_single_view_delta_and_fixed_point(variant):
     for order in ("simultaneous", "sequential"):
         out = oracle.rl_planes(phi, psfs, 4, boundary="circular", psi0=psi_true[None], order=order, corr_kernels=X)
         np.testing.assert_allclose(out[0], psi_true, rtol=1e-11)
+
+
+def weighted_textbook(phi, psfs, w, iters, boundary, order):
+    """psi <- psi * prod_v A_v^T(w_v phi_v / max(A_v psi, eps)) / A_v^T w_v,
+    factor 1 where A_v^T w_v < floor; A_v built entry by entry."""
+    V, _, H, W = phi.shape
+    A = [conv_matrix(psfs[v], H, W, boundary) for v in range(V)]
+    psi = np.full(H * W, phi.mean())
+    for _ in range(iters):
+        fac = []
+        for v in range(V):
+            wv, pv = w[v, 0].ravel(), phi[v, 0].ravel()
+            n = A[v].T @ wv
+
+            def f(ps, v=v, wv=wv, pv=pv, n=n):
+                c = A[v].T @ (wv * pv / np.maximum(A[v] @ ps, 1e-6))
+                out = np.ones_like(ps)
+                ok = n >= oracle.NORM_FLOOR
+                out[ok] = c[ok] / n[ok]
+                return out
+            fac.append(f)
+        if order == "sequential":
+            for v in range(V):
+                psi = psi * fac[v](psi)
+        else:
+            upd = np.ones_like(psi)
+            for v in range(V):
+                upd *= fac[v](psi)
+            psi = psi * upd
+    return psi
+
+
+@pytest.mark.parametrize("boundary", ["zero", "circular"])
+@pytest.mark.parametrize("order", ["simultaneous", "sequential"])
+def test_weighted_matches_textbook_em(boundary, order):
+    """Weighted MV-RL against the matrix-form EM update with the footprint
+    normaliser, on random weights with a zero block wide enough that the
+    guard (factor 1 where no weighted pixel is in reach) is exercised."""
+    rng = np.random.default_rng(15)
+    H, W, V, K = 9, 10, 2, 3
+    psfs = rng.random((V, K, K)) + 0.1
+    phi = rng.uniform(1, 20, size=(V, 1, H, W))
+    w = rng.uniform(0.2, 1.0, size=(V, 1, H, W))
+    w[0, 0, 1:6, 2:7] = 0.0                      # interior 3x3 block has n_0 = 0
+    out = oracle.rl_planes(phi, psfs, 3, boundary=boundary, order=order, weights=w)
+    want = weighted_textbook(phi, psfs, w, 3, boundary, order)
+    np.testing.assert_allclose(out[0].ravel(), want, rtol=1e-12)
+
+
+@pytest.mark.parametrize("boundary", ["zero", "circular"])
+def test_weighted_em_invariant_single_view(boundary):
+    """One view, weights > 0: sum_x (P (*) w)(x) psi'(x) = sum_x w(x) phi(x)
+    after every update (any PSF, either boundary)."""
+    rng = np.random.default_rng(16)
+    phi = rng.uniform(1, 30, size=(1, 1, 11, 13))
+    P = rng.random((1, 5, 5)) + 0.05
+    w = rng.uniform(0.1, 1.0, size=phi.shape)
+    n = oracle.correlate(w[0, 0], P[0], boundary)
+    for it in (1, 2, 3):
+        psi = oracle.rl_planes(phi, P, it, boundary=boundary, weights=w)[0]
+        assert abs((n * psi).sum() - (w * phi).sum()) <= 1e-11 * (w * phi).sum()
+
+
+def test_weighted_unit_weights_and_zero_weight_view():
+    """Unit weights with normalised PSFs under the circular boundary give the
+    unweighted update; a view with all-zero weights changes nothing."""
+    rng = np.random.default_rng(17)
+    phi = rng.uniform(1, 30, size=(2, 2, 12, 9))
+    psfs = rng.random((2, 5, 5)) + 0.1
+    psfs /= psfs.sum(axis=(1, 2), keepdims=True)
+    ones = np.ones(phi.shape)
+    np.testing.assert_allclose(oracle.rl_planes(phi, psfs, 3, boundary="circular", weights=ones),
+                               oracle.rl_planes(phi, psfs, 3, boundary="circular"), rtol=1e-12)
+    w = ones.copy()
+    w[1] = 0.0
+    psi0 = rng.uniform(5, 10, size=(2, 12, 9))
+    np.testing.assert_allclose(oracle.rl_planes(phi, psfs, 3, psi0=psi0, weights=w),
+                               oracle.rl_planes(phi[:1], psfs[:1], 3, psi0=psi0, weights=w[:1]), rtol=1e-13)
+
+
+def test_padded_domain_fixed_point_and_embedding():
+    """The estimate on the data+PSF-padded domain (Supp. Table 1 caption):
+    noise-free data phi_v = (P_v * psi_true) seen only on the data region,
+    embedded with zero weights in the padding, leave psi_true fixed (any V,
+    zero boundary); embed/crop are each other's inverse on the data."""
+    rng = np.random.default_rng(18)
+    K, R, H, W = 7, 3, 14, 11
+    psfs = np.stack([synth.gaussian_psf(K, 2.0, 0.8, a).astype(np.float64) for a in (0, 90, 45)])
+    psi_true = rng.uniform(10, 100, size=(H + 2 * R, W + 2 * R))
+    phi = np.stack([oracle.convolve(psi_true, P, "zero")[R:R + H, R:R + W] for P in psfs])[:, None]
+    pphi, w = oracle.embed_padded(phi, R)
+    assert pphi.shape == (3, 1, H + 2 * R, W + 2 * R) and w.sum() == 3 * H * W
+    np.testing.assert_array_equal(oracle.crop_padded(pphi[0], R), phi[0])
+    out = oracle.rl_planes(pphi, psfs, 4, boundary="zero", psi0=psi_true[None], weights=w, order="sequential")
+    np.testing.assert_allclose(out[0], psi_true, rtol=1e-11)
