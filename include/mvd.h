@@ -308,6 +308,40 @@ mvd_status mvd_psf_grad(mvd_ctx *ctx, const void *data_dev, mvd_dtype dt, int n_
                         int checkpoint_every, double *loss_host, float *grad_dev,
                         float *estimate_dev, void *stream);
 
+/* Weighted MV-RL (the "weights" array of Supp. Note 1's memory table, 4 B
+ * per pixel and view; the paper gives no formula for them).  weights_dev
+ * [V][n_planes][H][W] FP32 (device memory, kept by pointer, not copied; it
+ * must stay valid while deconvolutions use it) holds one weight per view and
+ * pixel of the planes later passed to mvd_deconvolve_planes, which must then
+ * have exactly n_planes planes; n_planes = 1 gives one weight plane per view
+ * that serves every plane of any call.  Each view's factor of the update becomes
+ *     c_v = ((w_v phi_v / max(psi * P_v, eps)) (*) P_v^*) / n_v,
+ *     n_v = w_v (*) P_v^*  (recomputed at every call),
+ * the EM update of a Poisson likelihood whose pixels count with weight w_v,
+ * and c_v = 1 where n_v < 1e-6 (no weighted pixel in reach).  Unit weights,
+ * normalised PSFs and the circular boundary give the unweighted update.
+ * Zero weights mark pixels without data: with mvd_embed_padded this is the
+ * estimate on the data + PSF padded domain (Supp. Table 1 caption).  Runs on
+ * the fused, plain and direct routes (MVD_ERR_UNSUPPORTED on the Fourier and
+ * tensor-core routes, mvd_run_host and mvd_psf_grad).  NULL clears. */
+mvd_status mvd_set_weights(mvd_ctx *ctx, const float *weights_dev, int n_planes);
+
+/* Padded domain: src [V][n_planes][H][W] (dt, device) -> dst
+ * [V][n_planes][H+2pad][W+2pad] with the planes in the centre and zeros
+ * around; weights (FP32 [V][weight_planes][H+2pad][W+2pad], weight_planes 1
+ * or n_planes, may be NULL) 1 on the data, 0 in the padding.  pad >= R gives
+ * the estimate room for the PSF; a padded width that is a multiple of 4 (16)
+ * keeps the fused kernels on TMA (vector) loads.  Buffers must not overlap.
+ * Asynchronous on `stream`. */
+mvd_status mvd_embed_padded(const void *src_dev, mvd_dtype dt, int views, int n_planes, int plane_h,
+                            int plane_w, int pad, void *dst_dev, float *weights_dev, int weight_planes,
+                            void *stream);
+
+/* src [n_planes][padded_h][padded_w] FP32 -> dst [n_planes][padded_h-2pad]
+ * [padded_w-2pad], the centre of each plane.  Asynchronous on `stream`. */
+mvd_status mvd_crop_planes(const float *src_dev, int n_planes, int padded_h, int padded_w, int pad,
+                           float *dst_dev, void *stream);
+
 /* Replace the context's PSFs (same views and size), e.g. after an optimiser
  * step of PSF calibration; same checks as mvd_create. */
 mvd_status mvd_set_psfs(mvd_ctx *ctx, const float *psfs_host);

@@ -161,6 +161,9 @@ struct mvd_ctx {
     std::vector<float> psfs;
     std::vector<float> corr_psfs;        // a variant's flip(X_v), [V][K][K]; empty for plain MV-RL
     bool psf_dev_fresh = false;          // psf_dev holds the current psfs (+ corr_psfs)
+    const float *weights = nullptr;      // caller's [V][P][H][W] per-pixel view weights, or none
+    int weight_planes = 0;               // P, or 1: one plane per view used for every plane
+    DevBuf wnorm, wtmp;                  // 1 / footprint per view and plane; scratch planes
     std::vector<float> taps_host;
     mvd::FactorTable ft;
     DevBuf taps, psf_dev, means, ratio, plain;
@@ -250,6 +253,9 @@ mvd::FusedArgs fused_args(const mvd_ctx *c, const void *data, mvd_dtype dt, floa
     a.circular = c->boundary == MVD_BOUNDARY_CIRCULAR;
     a.eps = c->eps;
     a.err = c->status.as<int>();
+    a.weights = c->weights;
+    a.wnorm = c->weights ? c->wnorm.as<float>() : nullptr;
+    a.weights_bcast = c->weight_planes == 1;
     a.wait_budget = c->wait_budget;
     a.max_ctas = c->max_ctas;
     return a;
@@ -425,6 +431,26 @@ mvd_status run_fft(mvd_ctx *c, const void *data, mvd_dtype dt, float *est, int P
     return MVD_OK;
 }
 
+// Weighted MV-RL: 1 / (w_v (*) P_v^*) for every view and plane, before the iterations.
+mvd_status prepare_weights(mvd_ctx *c, int P, cudaStream_t s) {
+    const size_t n = static_cast<size_t>(c->H) * c->W * P;
+    cudaError_t e;
+    if ((e = c->wnorm.ensure(n * c->V * sizeof(float))) != cudaSuccess ||
+        (e = c->wtmp.ensure(n * sizeof(float))) != cudaSuccess)
+        return fail(MVD_ERR_NOMEM, "weight workspace: %s", cudaGetErrorString(e));
+    mvd::PlainArgs a{};
+    a.taps = c->taps.as<float>();
+    a.ft = c->ft;
+    a.H = c->H;
+    a.W = c->W;
+    a.circular = c->boundary == MVD_BOUNDARY_CIRCULAR;
+    c->prof.mark(s, "weight_norms");
+    if ((e = mvd::weight_norms(a, c->weights, P, c->wtmp.as<float>(), c->wnorm.as<float>(), s)) != cudaSuccess)
+        return cuda_fail(e, "weight normaliser");
+    c->prof.end(s);
+    return MVD_OK;
+}
+
 mvd_status run_plain(mvd_ctx *c, const void *data, mvd_dtype dt, float *est, int P, int init_mean,
                      int direct, cudaStream_t s) {
     const size_t n = static_cast<size_t>(c->H) * c->W;
@@ -453,10 +479,15 @@ mvd_status run_plain(mvd_ctx *c, const void *data, mvd_dtype dt, float *est, int
         for (int t = 0; t < c->iters; ++t) {
             c->prof.mark(s, direct ? "direct_iteration" : "plain_iteration");
             for (int v = 0; v < c->V; ++v) {
-                const char *phi = static_cast<const char *>(data) + (static_cast<size_t>(v) * P + p) * n * esz;
+                const size_t vp = (static_cast<size_t>(v) * P + p) * n;
+                const char *phi = static_cast<const char *>(data) + vp * esz;
+                const size_t wp = c->weight_planes == 1 ? static_cast<size_t>(v) * n : vp;
+                const float *w = c->weights ? c->weights + wp : nullptr;
                 if ((e = mvd::plain_convolve(a, v, 0, direct, psi, tmp, b, s)) != cudaSuccess) return cuda_fail(e, "blur");
-                if ((e = mvd::plain_ratio(phi, u16, b, b, n, c->eps, s)) != cudaSuccess) return cuda_fail(e, "ratio");
+                if ((e = mvd::plain_ratio(phi, u16, w, b, b, n, c->eps, s)) != cudaSuccess) return cuda_fail(e, "ratio");
                 if ((e = mvd::plain_convolve(a, v, 1, direct, b, tmp, cv, s)) != cudaSuccess) return cuda_fail(e, "correlate");
+                if (w && (e = mvd::plain_apply_norm(cv, c->wnorm.as<float>() + wp, n, s)) != cudaSuccess)
+                    return cuda_fail(e, "weight normaliser");
                 if (sequential) {
                     if ((e = mvd::plain_update(psi, cv, n, s)) != cudaSuccess) return cuda_fail(e, "update");
                 } else if ((e = mvd::plain_multiply(prod, cv, n, v == 0, s)) != cudaSuccess) {
@@ -521,8 +552,8 @@ mvd_status mvd_psf_grad(mvd_ctx *c, const void *data, mvd_dtype dt, int P, int c
     if (dt != MVD_U16 && dt != MVD_F32) return fail(MVD_ERR_ARG, "unknown dtype");
     if (P < 1 || P > 65535 || ckpt < 1) return fail(MVD_ERR_ARG, "need 1 <= n_planes <= 65535 and checkpoint_every >= 1");
     if (c->order != MVD_ORDER_SIMULTANEOUS) return fail(MVD_ERR_UNSUPPORTED, "the gradient follows the simultaneous order");
-    if (c->variant != MVD_VARIANT_INDEPENDENT)
-        return fail(MVD_ERR_UNSUPPORTED, "the gradient follows plain MV-RL (variant INDEPENDENT)");
+    if (c->variant != MVD_VARIANT_INDEPENDENT || c->weights)
+        return fail(MVD_ERR_UNSUPPORTED, "the gradient follows plain MV-RL (variant INDEPENDENT, no weights)");
     if (c->K > mvd::adj::kMaxK) return fail(MVD_ERR_UNSUPPORTED, "the gradient takes K <= %d", mvd::adj::kMaxK);
     DeviceGuard g(c->device);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -747,9 +778,9 @@ mvd_status mvd_autotune(mvd_ctx *c, const void *data, mvd_dtype dt, int n_planes
     if (n_planes < 1) return fail(MVD_ERR_ARG, "n_planes must be >= 1");
     DeviceGuard g(c->device);
     char key[256];
-    std::snprintf(key, sizeof key, "route_v%d_k%d_%dx%d_t%d_b%d_o%d_r%d_x%d", c->V, c->K, c->H, c->W, c->iters,
+    std::snprintf(key, sizeof key, "route_v%d_k%d_%dx%d_t%d_b%d_o%d_r%d_x%d_w%d", c->V, c->K, c->H, c->W, c->iters,
                   static_cast<int>(c->boundary), static_cast<int>(c->order), c->ft.total_terms,
-                  static_cast<int>(c->variant));
+                  static_cast<int>(c->variant), c->weights ? 1 : 0);
     int cached = -1, unused = 0;
     if (tune_cache_lookup(key, &cached, &unused) && cached >= 0) {
         c->algo = static_cast<mvd_algo>(cached);
@@ -758,7 +789,7 @@ mvd_status mvd_autotune(mvd_ctx *c, const void *data, mvd_dtype dt, int n_planes
     int ly, lx;
     std::vector<mvd_algo> cand;
     if (mvd::fused_supported(c->K) && mvd::fused_taps_fit(c->ft)) cand.push_back(MVD_ALGO_FUSED);
-    if (fft_grid(c, &ly, &lx)) cand.push_back(MVD_ALGO_FFT);
+    if (fft_grid(c, &ly, &lx) && !c->weights) cand.push_back(MVD_ALGO_FFT);
     if (cand.empty()) cand.push_back(MVD_ALGO_PLAIN);
     if (cand.size() == 1) {
         c->algo = cand[0];
@@ -887,6 +918,57 @@ mvd_status mvd_set_variant(mvd_ctx *c, mvd_variant variant) {
     return MVD_OK;
 }
 
+mvd_status mvd_set_weights(mvd_ctx *c, const float *weights_dev, int n_planes) {
+    t_last_error.clear();
+    if (!c) return fail(MVD_ERR_ARG, "ctx is NULL");
+    if (!weights_dev) {
+        c->weights = nullptr;
+        c->weight_planes = 0;
+        return MVD_OK;
+    }
+    if (n_planes < 1 || n_planes > 65535) return fail(MVD_ERR_ARG, "need 1 <= n_planes <= 65535");
+    c->weights = weights_dev;
+    c->weight_planes = n_planes;
+    return MVD_OK;
+}
+
+mvd_status mvd_embed_padded(const void *src, mvd_dtype dt, int views, int n_planes, int plane_h, int plane_w,
+                            int pad, void *dst, float *weights, int weight_planes, void *stream) {
+    t_last_error.clear();
+    if (!src || !dst) return fail(MVD_ERR_ARG, "NULL buffer");
+    if (dt != MVD_U16 && dt != MVD_F32) return fail(MVD_ERR_ARG, "unknown dtype");
+    if (views < 1 || n_planes < 1 || plane_h < 1 || plane_w < 1 || pad < 0)
+        return fail(MVD_ERR_ARG, "need views, planes, plane sides >= 1 and pad >= 0");
+    if (weights && weight_planes != 1 && weight_planes != n_planes)
+        return fail(MVD_ERR_ARG, "weight_planes must be 1 or n_planes");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaError_t e = mvd::launch_embed_padded(src, dt == MVD_U16 ? 2 : 4, static_cast<long long>(views) * n_planes,
+                                             plane_h, plane_w, pad, dst, weight_planes == n_planes ? weights : nullptr,
+                                             s);
+    if (e == cudaSuccess && weights && weight_planes != n_planes) {
+        // one weight plane per view: embed the first plane of each view once more, keeping its mask
+        const size_t pin = static_cast<size_t>(plane_h) * plane_w * (dt == MVD_U16 ? 2 : 4);
+        const size_t pout = static_cast<size_t>(plane_h + 2 * pad) * (plane_w + 2 * pad);
+        for (int v = 0; v < views && e == cudaSuccess; ++v) {
+            const char *sv = static_cast<const char *>(src) + static_cast<size_t>(v) * n_planes * pin;
+            char *dv = static_cast<char *>(dst) + static_cast<size_t>(v) * n_planes * pout * (dt == MVD_U16 ? 2 : 4);
+            e = mvd::launch_embed_padded(sv, dt == MVD_U16 ? 2 : 4, 1, plane_h, plane_w, pad, dv, weights + v * pout, s);
+        }
+    }
+    return e == cudaSuccess ? MVD_OK : cuda_fail(e, "embed kernel");
+}
+
+mvd_status mvd_crop_planes(const float *src, int n_planes, int padded_h, int padded_w, int pad, float *dst,
+                           void *stream) {
+    t_last_error.clear();
+    if (!src || !dst) return fail(MVD_ERR_ARG, "NULL buffer");
+    if (n_planes < 1 || pad < 0 || padded_h <= 2 * pad || padded_w <= 2 * pad)
+        return fail(MVD_ERR_ARG, "need planes >= 1 and padded sides > 2 pad");
+    const cudaError_t e = mvd::launch_crop_planes(src, n_planes, padded_h, padded_w, pad, dst,
+                                                  static_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? MVD_OK : cuda_fail(e, "crop kernel");
+}
+
 mvd_status mvd_variant_kernels(const float *psfs, int views, int K, mvd_variant variant, float *x_out) {
     t_last_error.clear();
     if (!psfs || !x_out) return fail(MVD_ERR_ARG, "NULL argument");
@@ -989,6 +1071,14 @@ mvd_status mvd_deconvolve_planes(mvd_ctx *c, const void *data, mvd_dtype dt, flo
             return cuda_fail(e, "plane means kernel");
         c->prof.end(s);
     }
+    if (c->weights) {
+        if (c->weight_planes != 1 && n_planes != c->weight_planes)
+            return fail(MVD_ERR_ARG, "weights were set for %d planes, the data have %d", c->weight_planes, n_planes);
+        if (c->algo == MVD_ALGO_FFT || c->algo == MVD_ALGO_TENSOR)
+            return fail(MVD_ERR_UNSUPPORTED, "weights run on the fused, plain and direct routes");
+        mvd_status st = prepare_weights(c, c->weight_planes, s);
+        if (st != MVD_OK) return st;
+    }
     // the fused kernels carry the taps in their parameter block: PSFs that need
     // more separable terms than it holds run on the plain path
     if ((c->algo == MVD_ALGO_FUSED && mvd::fused_taps_fit(c->ft)) || c->algo == MVD_ALGO_TENSOR)
@@ -1004,6 +1094,7 @@ mvd_status mvd_run_host(mvd_ctx *c, const void *stacks_host, mvd_dtype dt, int n
     if (!stacks_host || !out_host) return fail(MVD_ERR_ARG, "NULL buffer");
     if (dt != MVD_U16 && dt != MVD_F32) return fail(MVD_ERR_ARG, "unknown dtype");
     if (nz != c->H || nx != c->W) return fail(MVD_ERR_ARG, "stack (nz, nx) must equal the context's plane (H, W)");
+    if (c->weights) return fail(MVD_ERR_UNSUPPORTED, "host pipeline without weights");
     if (ny < 1) return fail(MVD_ERR_ARG, "ny must be >= 1");
     if (chunk_planes < 0) return fail(MVD_ERR_ARG, "chunk_planes must be >= 0");
     DeviceGuard g(c->device);

@@ -301,6 +301,17 @@ blur_ratio_kernel(const __grid_constant__ KParams kp) {
                             for (int e = 0; e < 4; ++e) ph[4 * q4 + e] = f[e];
                         }
                     }
+                    if (a.weights) {   // weighted MV-RL: w_v phi_v / blur
+                        const long long woff = (a.weights_bcast ? v * plane_px : vplane) +
+                                               static_cast<long long>(y) * a.W + x;
+#pragma unroll
+                        for (int q4 = 0; q4 < kNC / 4; ++q4) {
+                            float f[4];
+                            load4(a.weights, 0, woff + 4 * q4, kp.vec_ok && n == kNC, max(0, min(4, n - 4 * q4)), f);
+#pragma unroll
+                            for (int e = 0; e < 4; ++e) ph[4 * q4 + e] *= f[e];
+                        }
+                    }
 #pragma unroll
                     for (int q4 = 0; q4 < kNC / 4; ++q4) {
                         float r[4];
@@ -382,7 +393,7 @@ correlate_update_kernel(const __grid_constant__ KParams kp) {
                     tma::load_3d(tile, &kp.map, bar, c2.x0 - G::R4, c2.y0 - G::R, nv * a.P + c2.p);
                 }
             };
-            if (a.ft.crank[v] == 1) {
+            if (a.ft.crank[v] == 1 && !a.wnorm) {
                 const float *tq = kp.taps + a.ft.ctap_off[v] * 2 * K;
                 vertical_pass<K>(tile, stage, tq);
                 __syncthreads();
@@ -402,6 +413,26 @@ correlate_update_kernel(const __grid_constant__ KParams kp) {
                     if (q == a.ft.crank[v] - 1) prefetch_next();
                     horizontal_pass<K>(stage, tq + K, c);
                     __syncthreads();
+                }
+                if (a.wnorm) {   // weighted MV-RL: c / n_v, or 1 where no weighted pixel is in reach
+                    const long long vplane =
+                        a.weights_bcast ? v * plane_px : (static_cast<long long>(v) * a.P + p) * plane_px;
+#pragma unroll
+                    for (int h = 0; h < G::H_PER_THREAD; ++h) {
+                        int y, x;
+                        item_origin<K>(h, y0, x0, y, x);
+                        if (y >= a.H || x >= a.W) continue;
+                        const int n = min(kNC, a.W - x);
+                        const long long off = vplane + static_cast<long long>(y) * a.W + x;
+#pragma unroll
+                        for (int q4 = 0; q4 < kNC / 4; ++q4) {
+                            float m[4];
+                            load4(a.wnorm, 0, off + 4 * q4, kp.vec_ok && n == kNC, max(0, min(4, n - 4 * q4)), m);
+#pragma unroll
+                            for (int e = 0; e < 4; ++e)
+                                c[h][4 * q4 + e] = m[e] >= 0.0f ? c[h][4 * q4 + e] * m[e] : 1.0f;
+                        }
+                    }
                 }
 #pragma unroll
                 for (int h = 0; h < G::H_PER_THREAD; ++h)
@@ -493,6 +524,7 @@ cudaError_t launch_pair(const FusedArgs &a, int which, cudaStream_t s) {
         std::memcpy(kp.taps + tt * 2 * K, a.taps_host + (static_cast<size_t>(tt) * 4 + (which == 0 ? 0 : 2)) * K,
                     2 * K * sizeof(float));
     const bool aligned = aligned16(a.phi) && aligned16(a.ratio) && aligned16(a.psi_out) &&
+                         (a.weights == nullptr || aligned16(a.weights)) && (a.wnorm == nullptr || aligned16(a.wnorm)) &&
                          (a.psi_in == nullptr || aligned16(a.psi_in));
     kp.vec_ok = aligned && (a.W % 4 == 0);
     kp.vec16 = aligned && (a.W % 16 == 0);

@@ -58,6 +58,14 @@ void variant_kernels(const float *psfs, int views, int K, int variant, double *X
 cudaError_t launch_reslice(const void *src, void *dst, int elem_bytes, int views,
                            int nz, int ny, int nx, cudaStream_t s);
 
+// [planes][H][W] -> [planes][H+2pad][W+2pad] with zeros around; weights
+// (optional) 1 on the data and 0 in the padding.
+cudaError_t launch_embed_padded(const void *src, int elem_bytes, long long planes, int H, int W, int pad, void *dst,
+                                float *weights, cudaStream_t s);
+// [planes][Hp][Wp] -> [planes][Hp-2pad][Wp-2pad] (the centre).
+cudaError_t launch_crop_planes(const float *src, long long planes, int Hp, int Wp, int pad, float *dst,
+                               cudaStream_t s);
+
 // means[p] = (sum over views and pixels of plane p) / (V*H*W), FP64 sum.
 cudaError_t launch_plane_means(const void *data, int u16, int views, int planes, int H,
                                int W, float *means, cudaStream_t s);
@@ -76,12 +84,16 @@ struct FusedArgs {
     int circular;
     float eps;
     int view_lo, view_hi;    // views [lo, hi) take part in this launch
+    const float *weights;    // [V][P][H][W] per-pixel view weights, or nullptr (plain MV-RL)
+    const float *wnorm;      // [V][P][H][W] 1 / (w_v (*) P_v^*), negative where that is below the floor
+    int weights_bcast;       // weights and wnorm hold one plane per view, used for every plane
     int *err;                // device status word (kDevTimeout set on an expired wait)
     long long wait_budget;   // clock cycles a tile wait may spin before it reports a timeout
     int max_ctas;            // cap on the persistent grid (0: one resident wave)
 };
 
 constexpr int kDevTimeout = 1;
+constexpr float kNormFloor = 1e-6f;      // weighted MV-RL: a view leaves psi unchanged below this footprint
 constexpr long long kDefaultWaitBudget = 2000000000LL;   // about one second at 2 GHz
 
 bool fused_supported(int K);
@@ -156,8 +168,14 @@ struct PlainArgs {
 cudaError_t plain_convolve(const PlainArgs &a, int v, int correlate, int direct,
                            const float *in, float *tmp, float *out, cudaStream_t s);
 cudaError_t plain_fill(float *dst, const float *means, int plane, size_t n, cudaStream_t s);
-cudaError_t plain_ratio(const void *phi, int u16, const float *blur, float *ratio, size_t n,
-                        float eps, cudaStream_t s);
+cudaError_t plain_ratio(const void *phi, int u16, const float *weights, const float *blur, float *ratio,
+                        size_t n, float eps, cudaStream_t s);
+// Weighted MV-RL: c = c * m where m >= 0, else 1 (m = 1 / n_v from weight_norms).
+cudaError_t plain_apply_norm(float *c, const float *wnorm, size_t n, cudaStream_t s);
+// m_v = 1 / (w_v (*) P_v^*) (correlation factors of view v), or -1 below
+// kNormFloor, for the P planes of every view: weights and wnorm [V][P][H][W];
+// tmp holds P planes.
+cudaError_t weight_norms(const PlainArgs &a, const float *weights, int P, float *tmp, float *wnorm, cudaStream_t s);
 cudaError_t plain_multiply(float *acc, const float *c, size_t n, int first, cudaStream_t s);
 cudaError_t plain_update(float *psi, const float *prod, size_t n, cudaStream_t s);
 

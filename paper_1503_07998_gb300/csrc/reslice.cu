@@ -180,4 +180,60 @@ cudaError_t launch_plane_means(const void *data, int u16, int views, int planes,
     return cudaGetLastError();
 }
 
+namespace {
+
+// Padded-domain estimate: plane (v, p) of H x W -> centre of a (H+2pad) x
+// (W+2pad) plane, zeros around; weights 1 on the data, 0 in the padding.
+template <typename T>
+__global__ void embed_padded_kernel(const T *__restrict__ src, T *__restrict__ dst, float *__restrict__ w, int H,
+                                    int W, int pad, long long n_out) {
+    const long long i = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i >= n_out) return;
+    const int Hp = H + 2 * pad, Wp = W + 2 * pad;
+    const long long plane = i / (static_cast<long long>(Hp) * Wp);
+    const long long r = i - plane * Hp * Wp;
+    const int y = static_cast<int>(r / Wp) - pad;
+    const int x = static_cast<int>(r % Wp) - pad;
+    const bool in = y >= 0 && y < H && x >= 0 && x < W;
+    dst[i] = in ? src[plane * H * W + static_cast<long long>(y) * W + x] : T(0);
+    if (w) w[i] = in ? 1.0f : 0.0f;
+}
+
+__global__ void crop_planes_kernel(const float *__restrict__ src, float *__restrict__ dst, int Hp, int Wp, int pad,
+                                   long long n_out) {
+    const long long i = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i >= n_out) return;
+    const int H = Hp - 2 * pad, W = Wp - 2 * pad;
+    const long long plane = i / (static_cast<long long>(H) * W);
+    const long long r = i - plane * H * W;
+    const int y = static_cast<int>(r / W), x = static_cast<int>(r % W);
+    dst[i] = src[plane * Hp * Wp + static_cast<long long>(y + pad) * Wp + x + pad];
+}
+
+}  // namespace
+
+cudaError_t launch_embed_padded(const void *src, int elem_bytes, long long planes, int H, int W, int pad, void *dst,
+                                float *weights, cudaStream_t s) {
+    const long long n = planes * (H + 2LL * pad) * (W + 2LL * pad);
+    if (n == 0) return cudaSuccess;
+    const unsigned blocks = static_cast<unsigned>((n + 255) / 256);
+    if (elem_bytes == 2)
+        embed_padded_kernel<uint16_t><<<blocks, 256, 0, s>>>(static_cast<const uint16_t *>(src),
+                                                             static_cast<uint16_t *>(dst), weights, H, W, pad, n);
+    else
+        embed_padded_kernel<float><<<blocks, 256, 0, s>>>(static_cast<const float *>(src), static_cast<float *>(dst),
+                                                          weights, H, W, pad, n);
+    count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_crop_planes(const float *src, long long planes, int Hp, int Wp, int pad, float *dst,
+                               cudaStream_t s) {
+    const long long n = planes * (Hp - 2LL * pad) * (Wp - 2LL * pad);
+    if (n == 0) return cudaSuccess;
+    crop_planes_kernel<<<static_cast<unsigned>((n + 255) / 256), 256, 0, s>>>(src, dst, Hp, Wp, pad, n);
+    count_launch();
+    return cudaGetLastError();
+}
+
 }  // namespace mvd

@@ -69,6 +69,9 @@ def lib() -> ctypes.CDLL:
     L.mvd_set_rank_tolerance.argtypes = [vp, d]
     L.mvd_set_update_order.argtypes = [vp, i]
     L.mvd_set_variant.argtypes = [vp, i]
+    L.mvd_set_weights.argtypes = [vp, vp, i]
+    L.mvd_embed_padded.argtypes = [vp, i, i, i, i, i, i, vp, vp, i, vp]
+    L.mvd_crop_planes.argtypes = [vp, i, i, i, i, vp, vp]
     L.mvd_variant_kernels.argtypes = [vp, i, i, i, vp]
     L.mvd_device_status.argtypes = [vp, vp]
     L.mvd_psf_grad.argtypes = [vp, vp, i, i, i, ctypes.POINTER(d), vp, vp, vp]
@@ -95,7 +98,8 @@ def lib() -> ctypes.CDLL:
     L.mvd_launch_count.argtypes = []
     L.mvd_launch_count.restype = ctypes.c_uint64
     for name in ("mvd_create", "mvd_destroy", "mvd_set_algo", "mvd_set_rank_tolerance", "mvd_get_info",
-                 "mvd_set_update_order", "mvd_set_variant", "mvd_variant_kernels", "mvd_device_status", "mvd_set_wait_budget",
+                 "mvd_set_update_order", "mvd_set_variant", "mvd_variant_kernels", "mvd_device_status",
+                 "mvd_set_weights", "mvd_embed_padded", "mvd_crop_planes", "mvd_set_wait_budget",
                  "mvd_deconvolve_planes_static", "mvd_psf_grad", "mvd_set_psfs", "mvd_autotune",
                  "mvd_batch_create", "mvd_batch_tune", "mvd_batch_run", "mvd_batch_info", "mvd_batch_destroy",
                  "mvd_reslice", "mvd_deconvolve_planes", "mvd_run_host", "mvd_psf_factors",
@@ -222,6 +226,52 @@ def mvd_set_update_order(ctx: Context, order: str) -> None:
 def mvd_set_variant(ctx: Context, variant: str) -> None:
     """Select the MV-RL variant (keys of VARIANT; default "independent")."""
     _check(lib().mvd_set_variant(ctx.handle, VARIANT[variant]), "mvd_set_variant")
+
+
+def mvd_set_weights(ctx: Context, weights) -> None:
+    """Per-pixel view weights [V][P][H][W] (CUDA float32 tensor, kept by
+    reference on the context; P = 1: one plane per view for every plane) or
+    None to clear."""
+    if weights is None:
+        _check(lib().mvd_set_weights(ctx.handle, None, 0), "mvd_set_weights")
+        ctx._weights = None
+        return
+    _require_cuda(weights)
+    import torch
+    if weights.dtype != torch.float32 or not weights.is_contiguous():
+        raise ValueError("weights must be contiguous float32")
+    V, P, H, W = weights.shape
+    if V != ctx.views or (H, W) != (ctx.H, ctx.W):
+        raise ValueError("weights must be [V][P][H][W] of the context's views and plane")
+    _check(lib().mvd_set_weights(ctx.handle, ctypes.c_void_p(weights.data_ptr()), P), "mvd_set_weights")
+    ctx._weights = weights
+
+
+def mvd_embed_padded(planes, pad: int, per_plane_weights: bool = False, stream=None):
+    """planes [V][P][H][W] (CUDA uint16/float32) -> (padded planes
+    [V][P][H+2pad][W+2pad], float32 weights 1 on the data: [V][1][..] shared
+    by every plane, or [V][P][..] with per_plane_weights)."""
+    import torch
+    _require_cuda(planes)
+    V, P, H, W = planes.shape
+    dst = torch.empty((V, P, H + 2 * pad, W + 2 * pad), dtype=planes.dtype, device=planes.device)
+    wp = P if per_plane_weights else 1
+    w = torch.empty((V, wp, H + 2 * pad, W + 2 * pad), dtype=torch.float32, device=planes.device)
+    _check(lib().mvd_embed_padded(ctypes.c_void_p(planes.data_ptr()), _dtype_code(planes), V, P, H, W, int(pad),
+                                  ctypes.c_void_p(dst.data_ptr()), ctypes.c_void_p(w.data_ptr()), wp,
+                                  _stream_of(planes, stream)), "mvd_embed_padded")
+    return dst, w
+
+
+def mvd_crop_planes(est, pad: int, stream=None):
+    """est [P][Hp][Wp] (CUDA float32) -> [P][Hp-2pad][Wp-2pad]."""
+    import torch
+    _require_cuda(est)
+    P, Hp, Wp = est.shape
+    out = torch.empty((P, Hp - 2 * pad, Wp - 2 * pad), dtype=torch.float32, device=est.device)
+    _check(lib().mvd_crop_planes(ctypes.c_void_p(est.data_ptr()), P, Hp, Wp, int(pad), ctypes.c_void_p(out.data_ptr()),
+                                 _stream_of(est, stream)), "mvd_crop_planes")
+    return out
 
 
 def mvd_variant_kernels(psfs, variant: str) -> np.ndarray:
