@@ -13,6 +13,8 @@ rl       the forward method (Supp. Note 1, update equation; Fig. 1a reslicing),
 adjoint  reverse-mode gradient of a Poisson data fit through unrolled
          iterations with respect to the PSFs (PSF calibration)
 variants correlation kernels X_v of the MV-RL variants (Supp. Note 2 sec. 1)
+volume3d 3D MV-RL with PSFs a_v(y) P_v(z, x) (views turned about the axis),
+         against which the plane-wise approximation is measured
 
 Every function is pinned by ``tests/test_oracle.py`` against brute force,
 library routines, closed forms and invariants; none is "parity unpinned".
@@ -34,3 +36,4 @@ from .rl import (  # noqa: F401
 )
 from .adjoint import poisson_nll, rl_loss, rl_loss_and_psf_grad  # noqa: F401
 from .variants import VARIANTS, correlation_kernels  # noqa: F401
+from .volume3d import convolve3d, correlate3d, rl3d  # noqa: F401

@@ -481,3 +481,67 @@ def test_padded_domain_fixed_point_and_embedding():
     np.testing.assert_array_equal(oracle.crop_padded(pphi[0], R), phi[0])
     out = oracle.rl_planes(pphi, psfs, 4, boundary="zero", psi0=psi_true[None], weights=w, order="sequential")
     np.testing.assert_allclose(out[0], psi_true, rtol=1e-11)
+
+
+def brute3d(vol, P, a, boundary, corr):
+    Y, Z, X = vol.shape
+    K, Ka = P.shape[0], a.shape[0]
+    R, Ra = (K - 1) // 2, (Ka - 1) // 2
+    out = np.zeros_like(vol)
+    sg = 1 if corr else -1
+    for y in range(Y):
+        for z in range(Z):
+            for x in range(X):
+                s = 0.0
+                for i in range(Ka):
+                    for j in range(K):
+                        for k in range(K):
+                            yy, zz, xx = y + sg * (i - Ra), z + sg * (j - R), x + sg * (k - R)
+                            if boundary == "circular":
+                                yy, zz, xx = yy % Y, zz % Z, xx % X
+                            elif not (0 <= yy < Y and 0 <= zz < Z and 0 <= xx < X):
+                                continue
+                            s += a[i] * P[j, k] * vol[yy, zz, xx]
+                out[y, z, x] = s
+    return out
+
+
+@pytest.mark.parametrize("boundary", ["zero", "circular"])
+def test_convolve3d_brute_force_scipy_and_adjoint(boundary):
+    """3D convolution with a(y) P(z, x) against a sextuple loop and (zero
+    boundary) scipy's 3D convolution; correlation is its adjoint."""
+    from scipy.signal import convolve as sconv
+    rng = np.random.default_rng(19)
+    vol = rng.random((5, 6, 7))
+    P = rng.random((3, 3))
+    a = rng.random(5)
+    np.testing.assert_allclose(oracle.convolve3d(vol, P, a, boundary), brute3d(vol, P, a, boundary, False),
+                               rtol=1e-12)
+    np.testing.assert_allclose(oracle.correlate3d(vol, P, a, boundary), brute3d(vol, P, a, boundary, True),
+                               rtol=1e-12)
+    if boundary == "zero":
+        k3 = a[:, None, None] * P[None]
+        np.testing.assert_allclose(oracle.convolve3d(vol, P, a, "zero"), sconv(vol, k3, mode="same"), rtol=1e-12)
+    u = rng.random(vol.shape)
+    lhs = (oracle.convolve3d(vol, P, a, boundary) * u).sum()
+    rhs = (vol * oracle.correlate3d(u, P, a, boundary)).sum()
+    assert abs(lhs - rhs) <= 1e-12 * abs(lhs)
+
+
+def test_rl3d_reduces_to_planewise_and_conserves_flux():
+    """A delta axial profile gives the plane-wise result on every plane; one
+    view with normalised kernels under the circular boundary conserves flux."""
+    rng = np.random.default_rng(20)
+    phi = rng.uniform(1, 30, size=(2, 4, 9, 8))
+    psfs = rng.random((2, 5, 5)) + 0.1
+    delta = np.zeros((2, 3))
+    delta[:, 1] = 1.0
+    for order in ("simultaneous", "sequential"):
+        np.testing.assert_allclose(oracle.rl3d(phi, psfs, delta, 3, order=order),
+                                   oracle.rl_planes(phi, psfs, 3, order=order), rtol=1e-13)
+    P = psfs[:1] / psfs[:1].sum()
+    a = rng.random((1, 5))
+    a /= a.sum()
+    for it in (1, 2, 3):
+        psi = oracle.rl3d(phi[:1], P, a, it, boundary="circular")
+        assert abs(psi.sum() - phi[0].sum()) <= 1e-11 * phi[0].sum()
