@@ -429,6 +429,52 @@ def run_mvd(args, wl):
         finally:
             pctx.close()
 
+    # 3D MV-RL (PSF a_v(y) P_v(z, x), axial sigma 1.5 px = the lateral width)
+    # on the same planes, and what the plane-wise approximation loses against
+    # it on 3D-blurred synthetic volumes with known truth
+    vol3d = None
+    if not args.no_plain and rank == 0:
+        from paper_1503_07998_gb300 import synth
+        ax = synth.gaussian_1d(11, 1.5).astype(np.float32)
+        mvd.mvd_set_axial_psfs(ctx, np.stack([ax] * V))
+        try:
+            mvd.mvd_deconvolve_planes(ctx, planes, est)
+            torch.cuda.synchronize()
+            mvd.mvd_profile_enable(ctx, True)
+            v0, v1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            v0.record(stream)
+            mvd.mvd_deconvolve_planes(ctx, planes, est)
+            v1.record(stream)
+            torch.cuda.synchronize()
+            vprof = mvd.mvd_profile_read(ctx)
+            mvd.mvd_profile_enable(ctx, False)
+            vms = v0.elapsed_time(v1)
+        finally:
+            mvd.mvd_set_axial_psfs(ctx, None)
+        study = []
+        for sy in (1.5, 3.0, 6.0):
+            cs = synth.volume3d_case(48, 128, 128, 31, 8.0, 1.5, sy, n_blobs=200, seed=7)
+            sctx = mvd.mvd_create(V, cs["psfs"], 31, 128, 128, iters, "zero", 1e-6)
+            try:
+                d = torch.from_numpy(cs["phi"]).to(dev)
+                e = torch.empty((48, 128, 128), device=dev)
+                errs = {}
+                for name, axial in (("planewise", None), ("3d", cs["axial"])):
+                    mvd.mvd_set_axial_psfs(sctx, axial)
+                    mvd.mvd_deconvolve_planes(sctx, d, e)
+                    torch.cuda.synchronize()
+                    errs[name] = float(np.linalg.norm(e.cpu().numpy() - cs["truth"]) / np.linalg.norm(cs["truth"]))
+                study.append({"sigma_y": sy, "rel_l2_to_truth": errs})
+            finally:
+                sctx.close()
+        vol3d = {"value": units_per_step / (vms / 1e3), "unit": UNIT, "ms": vms,
+                 "note": "3D route on the same planes (axial Gaussian sigma 1.5, 11 taps): fused in-plane passes "
+                         "+ axial passes; deconvolution only",
+                 "kernels": {k: {"total_ms": v[0], "launches": v[1]} for k, v in vprof.items()},
+                 "study": {"config": "2 views, 48 planes of 128x128, 200 blobs, K=31 sigma (1.5, 8), 10 iterations, "
+                                     "data blurred in 3D with an axial Gaussian of sigma_y, Poisson noise",
+                           "results": study}}
+
     # PSF calibration gradient: 2 views, 64 planes of 256x256, free 31x31
     # PSFs started at sigma (1.2, 5) px on data made with (1.5, 7) px,
     # 10 unrolled iterations, checkpoint every 2
@@ -492,7 +538,7 @@ def run_mvd(args, wl):
                 "voxel_iterations_per_s": value / V,
                 "roofline": roof, "kernels": kr, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": int(launches), "clocks": clk, "plain_per_plane": plain,
-                "fft_route": fft_route, "tensor_route": tensor_route, "weighted_padded": weighted, "psf_grad": grad,
+                "fft_route": fft_route, "tensor_route": tensor_route, "weighted_padded": weighted, "vol3d": vol3d, "psf_grad": grad,
                 "paper_context": "GTX TITAN Black, 2 views, 1024^3 padded, 10 it: 21.1 s = 1.02e9 voxel-view-it/s "
                                  "(Supp. Table 1); another machine, not the target"}
         print(json.dumps(line))

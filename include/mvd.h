@@ -308,6 +308,20 @@ mvd_status mvd_psf_grad(mvd_ctx *ctx, const void *data_dev, mvd_dtype dt, int n_
                         int checkpoint_every, double *loss_host, float *grad_dev,
                         float *estimate_dev, void *stream);
 
+/* 3D MV-RL for views turned about the rotation axis, against which the
+ * plane-wise approximation (Results; Fig. 1a; compared with 3D deconvolution
+ * in Supp. Figs. 3-4) can be measured: view v's PSF becomes
+ * a_v(y) P_v(z, x), the in-plane PSF times a profile along the axis, and
+ * the planes of one mvd_deconvolve_planes call are consecutive positions on
+ * the axis (planes outside the call are zero, or wrapped for the circular
+ * boundary).  axial_host [V][axial_size] FP32 (copied), odd length 1..127,
+ * entries >= 0 with a positive sum; NULL or 0 clears (plane-wise, the
+ * default; a centred delta profile gives the plane-wise result).  The
+ * in-plane passes run in the fused kernels and the axial passes in their
+ * own kernels; other routes, weights, mvd_run_host, mvd_psf_grad and a given
+ * initial estimate return MVD_ERR_UNSUPPORTED. */
+mvd_status mvd_set_axial_psfs(mvd_ctx *ctx, const float *axial_host, int axial_size);
+
 /* Weighted MV-RL (the "weights" array of Supp. Note 1's memory table, 4 B
  * per pixel and view; the paper gives no formula for them).  weights_dev
  * [V][n_planes][H][W] FP32 (device memory, kept by pointer, not copied; it

@@ -164,6 +164,9 @@ struct mvd_ctx {
     const float *weights = nullptr;      // caller's [V][P][H][W] per-pixel view weights, or none
     int weight_planes = 0;               // P, or 1: one plane per view used for every plane
     DevBuf wnorm, wtmp;                  // 1 / footprint per view and plane; scratch planes
+    std::vector<float> axial;            // 3D route: [V][Ka] profiles along the rotation axis
+    int Ka = 0;
+    DevBuf axial_dev, tmp3d;
     std::vector<float> taps_host;
     mvd::FactorTable ft;
     DevBuf taps, psf_dev, means, ratio, plain;
@@ -431,6 +434,52 @@ mvd_status run_fft(mvd_ctx *c, const void *data, mvd_dtype dt, float *est, int P
     return MVD_OK;
 }
 
+// 3D route: in-plane blur (kernel A, blur only), the passes along the plane
+// axis per view, then kernel B on the axially correlated ratios.
+mvd_status run_fused3d(mvd_ctx *c, const void *data, mvd_dtype dt, float *est, int P, cudaStream_t s) {
+    const size_t n = static_cast<size_t>(c->H) * c->W;
+    cudaError_t e;
+    if ((e = c->ratio.ensure(static_cast<size_t>(c->V) * P * n * sizeof(float))) != cudaSuccess ||
+        (e = c->tmp3d.ensure(static_cast<size_t>(P) * n * sizeof(float))) != cudaSuccess)
+        return fail(MVD_ERR_NOMEM, "3D workspace: %s", cudaGetErrorString(e));
+    if ((e = c->axial_dev.ensure(c->axial.size() * sizeof(float))) != cudaSuccess)
+        return fail(MVD_ERR_NOMEM, "axial profiles: %s", cudaGetErrorString(e));
+    if ((e = cudaMemcpyAsync(c->axial_dev.ptr, c->axial.data(), c->axial.size() * sizeof(float),
+                             cudaMemcpyHostToDevice, s)) != cudaSuccess)
+        return cuda_fail(e, "upload axial profiles");
+    mvd::FusedArgs a = fused_args(c, data, dt, est, P);
+    const int step = c->order == MVD_ORDER_SEQUENTIAL ? 1 : c->V;
+    const int circ = c->boundary == MVD_BOUNDARY_CIRCULAR;
+    const size_t es = dt == MVD_U16 ? 2 : 4;
+    bool first = true;
+    for (int t = 0; t < c->iters; ++t) {
+        for (int v0 = 0; v0 < c->V; v0 += step) {
+            a.view_lo = v0;
+            a.view_hi = v0 + step;
+            a.psi_in = first ? nullptr : est;
+            first = false;
+            a.store_blur = 1;
+            c->prof.mark(s, "blur_ratio");
+            if ((e = mvd::launch_fused_blur_ratio(a, s)) != cudaSuccess) return cuda_fail(e, "blur kernel");
+            c->prof.mark(s, "axial");
+            for (int v = v0; v < v0 + step; ++v) {
+                float *rv = c->ratio.as<float>() + static_cast<size_t>(v) * P * n;
+                const char *phi = static_cast<const char *>(data) + static_cast<size_t>(v) * P * n * es;
+                const float *av = c->axial_dev.as<float>() + static_cast<size_t>(v) * c->Ka;
+                if ((e = mvd::launch_axial_ratio(rv, phi, dt == MVD_U16, av, c->Ka, P, n, circ, c->eps,
+                                                 c->tmp3d.as<float>(), s)) != cudaSuccess ||
+                    (e = mvd::launch_axial_corr(c->tmp3d.as<float>(), av, c->Ka, P, n, circ, rv, s)) != cudaSuccess)
+                    return cuda_fail(e, "axial kernels");
+            }
+            a.store_blur = 0;
+            c->prof.mark(s, "correlate_update");
+            if ((e = mvd::launch_fused_correlate_update(a, s)) != cudaSuccess) return cuda_fail(e, "correlate kernel");
+        }
+    }
+    c->prof.end(s);
+    return MVD_OK;
+}
+
 // Weighted MV-RL: 1 / (w_v (*) P_v^*) for every view and plane, before the iterations.
 mvd_status prepare_weights(mvd_ctx *c, int P, cudaStream_t s) {
     const size_t n = static_cast<size_t>(c->H) * c->W * P;
@@ -552,7 +601,7 @@ mvd_status mvd_psf_grad(mvd_ctx *c, const void *data, mvd_dtype dt, int P, int c
     if (dt != MVD_U16 && dt != MVD_F32) return fail(MVD_ERR_ARG, "unknown dtype");
     if (P < 1 || P > 65535 || ckpt < 1) return fail(MVD_ERR_ARG, "need 1 <= n_planes <= 65535 and checkpoint_every >= 1");
     if (c->order != MVD_ORDER_SIMULTANEOUS) return fail(MVD_ERR_UNSUPPORTED, "the gradient follows the simultaneous order");
-    if (c->variant != MVD_VARIANT_INDEPENDENT || c->weights)
+    if (c->variant != MVD_VARIANT_INDEPENDENT || c->weights || c->Ka > 0)
         return fail(MVD_ERR_UNSUPPORTED, "the gradient follows plain MV-RL (variant INDEPENDENT, no weights)");
     if (c->K > mvd::adj::kMaxK) return fail(MVD_ERR_UNSUPPORTED, "the gradient takes K <= %d", mvd::adj::kMaxK);
     DeviceGuard g(c->device);
@@ -789,7 +838,7 @@ mvd_status mvd_autotune(mvd_ctx *c, const void *data, mvd_dtype dt, int n_planes
     int ly, lx;
     std::vector<mvd_algo> cand;
     if (mvd::fused_supported(c->K) && mvd::fused_taps_fit(c->ft)) cand.push_back(MVD_ALGO_FUSED);
-    if (fft_grid(c, &ly, &lx) && !c->weights) cand.push_back(MVD_ALGO_FFT);
+    if (fft_grid(c, &ly, &lx) && !c->weights && c->Ka == 0) cand.push_back(MVD_ALGO_FFT);
     if (cand.empty()) cand.push_back(MVD_ALGO_PLAIN);
     if (cand.size() == 1) {
         c->algo = cand[0];
@@ -915,6 +964,30 @@ mvd_status mvd_set_variant(mvd_ctx *c, mvd_variant variant) {
         cudaError_t e = upload_psf_dev(c);
         if (e != cudaSuccess) return cuda_fail(e, "upload psfs");
     }
+    return MVD_OK;
+}
+
+mvd_status mvd_set_axial_psfs(mvd_ctx *c, const float *axial_host, int axial_size) {
+    t_last_error.clear();
+    if (!c) return fail(MVD_ERR_ARG, "ctx is NULL");
+    if (!axial_host || axial_size == 0) {
+        c->axial.clear();
+        c->Ka = 0;
+        return MVD_OK;
+    }
+    if (axial_size < 1 || axial_size > 127 || axial_size % 2 == 0)
+        return fail(MVD_ERR_ARG, "axial profile length must be odd, 1..127");
+    for (int v = 0; v < c->V; ++v) {
+        double sum = 0;
+        for (int i = 0; i < axial_size; ++i) {
+            const float x = axial_host[v * axial_size + i];
+            if (!std::isfinite(x) || x < 0) return fail(MVD_ERR_ARG, "axial profile %d has a negative or non-finite entry", v);
+            sum += x;
+        }
+        if (!(sum > 0)) return fail(MVD_ERR_ARG, "axial profile %d sums to zero", v);
+    }
+    c->axial.assign(axial_host, axial_host + static_cast<size_t>(c->V) * axial_size);
+    c->Ka = axial_size;
     return MVD_OK;
 }
 
@@ -1071,6 +1144,18 @@ mvd_status mvd_deconvolve_planes(mvd_ctx *c, const void *data, mvd_dtype dt, flo
             return cuda_fail(e, "plane means kernel");
         c->prof.end(s);
     }
+    if (c->Ka > 0) {
+        if (c->weights || !(c->algo == MVD_ALGO_FUSED && mvd::fused_taps_fit(c->ft)))
+            return fail(MVD_ERR_UNSUPPORTED, "the 3D route runs on the fused kernels, without weights");
+        if (c->iters == 0) {
+            for (int p = 0; p < n_planes; ++p)
+                if ((e = mvd::plain_fill(est + p * n, c->means.as<float>(), p, n, s)) != cudaSuccess)
+                    return cuda_fail(e, "fill");
+            return MVD_OK;
+        }
+        if (!init_mean) return fail(MVD_ERR_UNSUPPORTED, "the 3D route starts from the plane means");
+        return run_fused3d(c, data, dt, est, n_planes, s);
+    }
     if (c->weights) {
         if (c->weight_planes != 1 && n_planes != c->weight_planes)
             return fail(MVD_ERR_ARG, "weights were set for %d planes, the data have %d", c->weight_planes, n_planes);
@@ -1094,7 +1179,7 @@ mvd_status mvd_run_host(mvd_ctx *c, const void *stacks_host, mvd_dtype dt, int n
     if (!stacks_host || !out_host) return fail(MVD_ERR_ARG, "NULL buffer");
     if (dt != MVD_U16 && dt != MVD_F32) return fail(MVD_ERR_ARG, "unknown dtype");
     if (nz != c->H || nx != c->W) return fail(MVD_ERR_ARG, "stack (nz, nx) must equal the context's plane (H, W)");
-    if (c->weights) return fail(MVD_ERR_UNSUPPORTED, "host pipeline without weights");
+    if (c->weights || c->Ka > 0) return fail(MVD_ERR_UNSUPPORTED, "host pipeline without weights or axial profiles");
     if (ny < 1) return fail(MVD_ERR_ARG, "ny must be >= 1");
     if (chunk_planes < 0) return fail(MVD_ERR_ARG, "chunk_planes must be >= 0");
     DeviceGuard g(c->device);

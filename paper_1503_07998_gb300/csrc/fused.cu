@@ -317,7 +317,8 @@ blur_ratio_kernel(const __grid_constant__ KParams kp) {
                         float r[4];
 #pragma unroll
                         for (int e = 0; e < 4; ++e)
-                            r[e] = __fdividef(ph[4 * q4 + e], fmaxf(acc[h][4 * q4 + e], a.eps));
+                            r[e] = a.store_blur ? acc[h][4 * q4 + e]
+                                                : __fdividef(ph[4 * q4 + e], fmaxf(acc[h][4 * q4 + e], a.eps));
                         store4(a.ratio + off + 4 * q4, kp.vec_ok && n == kNC, max(0, min(4, n - 4 * q4)), r);
                     }
                 }

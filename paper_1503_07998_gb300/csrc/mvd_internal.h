@@ -87,6 +87,7 @@ struct FusedArgs {
     const float *weights;    // [V][P][H][W] per-pixel view weights, or nullptr (plain MV-RL)
     const float *wnorm;      // [V][P][H][W] 1 / (w_v (*) P_v^*), negative where that is below the floor
     int weights_bcast;       // weights and wnorm hold one plane per view, used for every plane
+    int store_blur;          // kernel A writes the in-plane blur instead of the ratio (3D route)
     int *err;                // device status word (kDevTimeout set on an expired wait)
     long long wait_budget;   // clock cycles a tile wait may spin before it reports a timeout
     int max_ctas;            // cap on the persistent grid (0: one resident wave)
@@ -102,6 +103,13 @@ bool fused_taps_fit(const FactorTable &ft);
 void fused_tile_shape(int K, int *tile_h, int *tile_w);
 cudaError_t launch_fused_blur_ratio(const FusedArgs &a, cudaStream_t s);
 cudaError_t launch_fused_correlate_update(const FusedArgs &a, cudaStream_t s);
+
+// 3D route (vol3d.cu): passes along the plane axis with the profile a [Ka].
+// blur, phi, r, c: one view's [P][plane] planes.
+cudaError_t launch_axial_ratio(const float *blur, const void *phi, int u16, const float *a, int Ka, int P,
+                               long long plane, int circular, float eps, float *r, cudaStream_t s);
+cudaError_t launch_axial_corr(const float *r, const float *a, int Ka, int P, long long plane, int circular, float *c,
+                              cudaStream_t s);
 
 // Tensor-core route (tc.cu): the same two kernels with BF16x3 tcgen05 passes.
 bool tc_supported(int K);

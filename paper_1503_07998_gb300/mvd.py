@@ -70,6 +70,7 @@ def lib() -> ctypes.CDLL:
     L.mvd_set_update_order.argtypes = [vp, i]
     L.mvd_set_variant.argtypes = [vp, i]
     L.mvd_set_weights.argtypes = [vp, vp, i]
+    L.mvd_set_axial_psfs.argtypes = [vp, vp, i]
     L.mvd_embed_padded.argtypes = [vp, i, i, i, i, i, i, vp, vp, i, vp]
     L.mvd_crop_planes.argtypes = [vp, i, i, i, i, vp, vp]
     L.mvd_variant_kernels.argtypes = [vp, i, i, i, vp]
@@ -99,7 +100,7 @@ def lib() -> ctypes.CDLL:
     L.mvd_launch_count.restype = ctypes.c_uint64
     for name in ("mvd_create", "mvd_destroy", "mvd_set_algo", "mvd_set_rank_tolerance", "mvd_get_info",
                  "mvd_set_update_order", "mvd_set_variant", "mvd_variant_kernels", "mvd_device_status",
-                 "mvd_set_weights", "mvd_embed_padded", "mvd_crop_planes", "mvd_set_wait_budget",
+                 "mvd_set_weights", "mvd_embed_padded", "mvd_crop_planes", "mvd_set_axial_psfs", "mvd_set_wait_budget",
                  "mvd_deconvolve_planes_static", "mvd_psf_grad", "mvd_set_psfs", "mvd_autotune",
                  "mvd_batch_create", "mvd_batch_tune", "mvd_batch_run", "mvd_batch_info", "mvd_batch_destroy",
                  "mvd_reslice", "mvd_deconvolve_planes", "mvd_run_host", "mvd_psf_factors",
@@ -226,6 +227,18 @@ def mvd_set_update_order(ctx: Context, order: str) -> None:
 def mvd_set_variant(ctx: Context, variant: str) -> None:
     """Select the MV-RL variant (keys of VARIANT; default "independent")."""
     _check(lib().mvd_set_variant(ctx.handle, VARIANT[variant]), "mvd_set_variant")
+
+
+def mvd_set_axial_psfs(ctx: Context, axial) -> None:
+    """3D route: [V][Ka] profiles along the rotation axis (host array), or
+    None for the plane-wise method."""
+    if axial is None:
+        _check(lib().mvd_set_axial_psfs(ctx.handle, None, 0), "mvd_set_axial_psfs")
+        return
+    a = np.ascontiguousarray(np.asarray(axial, dtype=np.float32))
+    if a.ndim != 2 or a.shape[0] != ctx.views:
+        raise ValueError("axial profiles must be [V][Ka]")
+    _check(lib().mvd_set_axial_psfs(ctx.handle, a.ctypes.data_as(ctypes.c_void_p), a.shape[1]), "mvd_set_axial_psfs")
 
 
 def mvd_set_weights(ctx: Context, weights) -> None:

@@ -218,3 +218,37 @@ def uneven_volumes(n: int, seed: int, side=(96, 768), planes=(16, 256), views=(2
             stacks, psfs = volume_stacks(s, p, s, k, sa, sl, angles, density, seed=seed + i, device=device)
         out.append({"stacks": stacks, "psfs": psfs, "iters": it, "H": s, "W": s, "P": p, "views": v, "K": k})
     return out
+
+
+def volume3d_case(Y: int, Z: int, X: int, K: int, sigma_axial: float, sigma_lateral: float, sigma_y: float,
+                  angles=(0.0, 90.0), n_blobs: int = 100, seed: int = 0, background: float = 10.0,
+                  noise: bool = True):
+    """Views of a 3D blob volume blurred in 3D: view v's PSF is
+    a(y) P_v(z, x) with P_v the in-plane Gaussian PSF (sigma_axial,
+    sigma_lateral, turned by the view's angle) and a a Gaussian of sigma_y
+    along the rotation axis y (the plane index), odd length covering
+    +-3 sigma_y; Poisson noise.  Plane layout.  Returns a dict with truth
+    [Y][Z][X] (FP64), phi [V][Y][Z][X] (uint16), psfs [V][K][K] (FP32),
+    axial [V][Ka] (FP32)."""
+    from scipy.ndimage import convolve1d
+    from scipy.signal import fftconvolve
+
+    rng = np.random.default_rng(seed)
+    truth = np.full((Y, Z, X), background, dtype=np.float64)
+    cy, cz, cx = rng.uniform(0, Y, n_blobs), rng.uniform(0, Z, n_blobs), rng.uniform(0, X, n_blobs)
+    A = rng.uniform(100.0, 1000.0, n_blobs)
+    yy, zz, xx = np.meshgrid(np.arange(Y), np.arange(Z), np.arange(X), indexing="ij")
+    for y0, z0, x0, a in zip(cy, cz, cx, A):
+        truth += a * np.exp(-((yy - y0) ** 2 + (zz - z0) ** 2 + (xx - x0) ** 2) / 2.0)
+    Ra = max(1, int(math.ceil(3 * sigma_y)))
+    axial = gaussian_1d(2 * Ra + 1, sigma_y)
+    psfs, phis = [], []
+    for ang in angles:
+        P = gaussian_psf(K, sigma_axial, sigma_lateral, ang)
+        psfs.append(P)
+        planes = np.stack([fftconvolve(truth[y], P.astype(np.float64), mode="same") for y in range(Y)])
+        blurred = convolve1d(planes, axial, axis=0, mode="constant", cval=0.0)
+        img = rng.poisson(np.maximum(blurred, 0)) if noise else np.round(blurred)
+        phis.append(np.clip(img, 0, 65535).astype(np.uint16))
+    return {"truth": truth, "phi": np.stack(phis), "psfs": np.stack(psfs).astype(np.float32),
+            "axial": np.stack([axial] * len(angles)).astype(np.float32)}
