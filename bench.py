@@ -59,7 +59,7 @@ ALU_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 # scaled to the full workload (None until measured for the current kernels).
 # Taken on 128 of the 512 planes (--workload slab512) and scaled by 4; see
 # profiles/fused_kernels_volume512.md.
-NCU_TRAFFIC_PER_LAUNCH = {"blur_ratio": 1.9324e9, "correlate_update": 2.0041e9}
+NCU_TRAFFIC_PER_LAUNCH = {}
 
 
 def _peaks():
@@ -310,8 +310,11 @@ def run_mvd(args, wl):
     hbm_peak, hbm_src = _peaks()
     vi_per_launch = Y * Z * X
     # 2K flop per output of each 1D pass, two passes per SVD term
-    flops_a = 4 * K * info.blur_terms            # one blur per distinct PSF
-    flops_b = 4 * K * sum(info.corr_rank[:V])    # one correlation per view
+    # 2 FLOP per tap of every 1D pass the fused kernels run (narrow factors
+    # run with their 17 central taps): one blur per distinct PSF, one
+    # correlation per view
+    flops_a = info.flops_blur
+    flops_b = info.flops_corr
     es = 2 if stacks.dtype == torch.uint16 else 4
     kr = {
         "blur_ratio": kernel_roofline(prof, "blur_ratio", vi_per_launch, 4 + (es + 4) * V, flops_a, hbm_peak),

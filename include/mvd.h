@@ -146,6 +146,13 @@ typedef struct {
     int variant;                /* mvd_variant in use                       */
     int corr_rank[16];          /* SVD terms of the correlation kernel per
                                    view (= rank for INDEPENDENT)            */
+    int flops_blur;             /* fused kernels, FLOP per voxel and launch:
+                                   2 per tap of every 1D pass run, blur of
+                                   every distinct PSF (narrow factors run
+                                   with their 17 central taps when the rest
+                                   is below the rank tolerance; full taps
+                                   with weights set)                        */
+    int flops_corr;             /* the same for the correlation of all views */
 } mvd_info;
 
 /* Create a context for `views` views with K x K PSFs psfs_host[V][K][K]

@@ -1084,6 +1084,14 @@ mvd_status mvd_get_info(const mvd_ctx *c, mvd_info *info) {
     info->order = c->order;
     for (int v = 0; v < c->V && v < 16; ++v) info->rank[v] = c->ft.rank[v];
     for (int v = 0; v < c->V && v < 16; ++v) info->corr_rank[v] = c->ft.crank[v];
+    auto taps = [&](int v, unsigned bit) {
+        return (!c->weights && (c->ft.short_mask[v] & bit)) ? mvd::kShortTaps : c->K;
+    };
+    for (int g = 0; g < c->ft.n_groups; ++g) {
+        const int lead = c->ft.group_leader[g];
+        info->flops_blur += 2 * c->ft.rank[lead] * (taps(lead, 1u) + taps(lead, 2u));
+    }
+    for (int v = 0; v < c->V; ++v) info->flops_corr += 2 * c->ft.crank[v] * (taps(v, 4u) + taps(v, 8u));
     info->variant = c->variant;
     info->blur_groups = c->ft.n_groups;
     info->blur_terms = c->ft.total_terms;

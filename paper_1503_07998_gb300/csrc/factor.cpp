@@ -205,6 +205,30 @@ bool factorise_psfs(const float *psfs, int views, int K, double rank_tol, Factor
         off += r;
     }
     ft.total_terms = off;
+    // short factors: the mass outside the kShortTaps central taps is within the tolerance
+    if (K > kShortTaps && rank_tol > 0) {
+        const int OFF = (K - kShortTaps) / 2;
+        auto trimmable = [&](int term, int kind) {
+            const float *t = taps_out + static_cast<size_t>(term) * 4 * K + static_cast<size_t>(kind) * K;
+            double all = 0, tail = 0;
+            for (int m = 0; m < K; ++m) {
+                all += std::fabs(t[m]);
+                if (m < OFF || m >= OFF + kShortTaps) tail += std::fabs(t[m]);
+            }
+            return all > 0 && tail <= rank_tol * all;
+        };
+        for (int v = 0; v < views; ++v) {
+            unsigned char mask = 0;
+            for (int kind = 0; kind < 4; ++kind) {
+                const int n = kind < 2 ? ft.rank[v] : ft.crank[v];
+                const int t0 = kind < 2 ? ft.tap_off[v] : ft.ctap_off[v];
+                bool ok = n > 0;
+                for (int q = 0; q < n && ok; ++q) ok = trimmable(t0 + q, kind);
+                if (ok) mask |= static_cast<unsigned char>(1u << kind);
+            }
+            ft.short_mask[v] = mask;
+        }
+    }
     return true;
 }
 

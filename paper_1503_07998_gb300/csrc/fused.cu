@@ -244,10 +244,16 @@ blur_ratio_kernel(const __grid_constant__ KParams kp) {
             for (int v = a.view_hi - 1; v >= a.view_lo; --v)
                 if (a.ft.group[v] == g) v_first = v;
             const bool pre = kp.vec16 && a.phi_u16;
+            // weighted runs have zero-weight regions whose only signal comes
+            // through the factors' tails: full taps there
+            const unsigned sm = a.weights ? 0u : a.ft.short_mask[lead];
             uint4 pf[G::H_PER_THREAD][2];
             for (int q = 0; q < a.ft.rank[lead]; ++q) {
                 const float *tq = kp.taps + (a.ft.tap_off[lead] + q) * 2 * K;
-                vertical_pass<K>(tile, stage, tq);
+                if (sm & 1u)
+                    vertical_pass<K, short_taps<K>()>(tile, stage, tq);
+                else
+                    vertical_pass<K>(tile, stage, tq);
                 __syncthreads();
                 if (--left == 0 && use_tma && threadIdx.x == 0 && t_next < n_tiles) {
                     const TileCoord c = tile_coord<K>(t_next, tiles_x, tiles_y);
@@ -269,7 +275,10 @@ blur_ratio_kernel(const __grid_constant__ KParams kp) {
                         }
                     }
                 }
-                horizontal_pass<K>(stage, tq + K, acc);
+                if (sm & 2u)
+                    horizontal_pass<K, short_taps<K>()>(stage, tq + K, acc);
+                else
+                    horizontal_pass<K>(stage, tq + K, acc);
                 __syncthreads();
             }
             // ratio epilogue per item (16 consecutive pixels of one row)
@@ -394,12 +403,19 @@ correlate_update_kernel(const __grid_constant__ KParams kp) {
                     tma::load_3d(tile, &kp.map, bar, c2.x0 - G::R4, c2.y0 - G::R, nv * a.P + c2.p);
                 }
             };
+            const unsigned sm = a.weights ? 0u : a.ft.short_mask[v];
             if (a.ft.crank[v] == 1 && !a.wnorm) {
                 const float *tq = kp.taps + a.ft.ctap_off[v] * 2 * K;
-                vertical_pass<K>(tile, stage, tq);
+                if (sm & 4u)
+                    vertical_pass<K, short_taps<K>()>(tile, stage, tq);
+                else
+                    vertical_pass<K>(tile, stage, tq);
                 __syncthreads();
                 prefetch_next();
-                horizontal_pass_mul<K>(stage, tq + K, prod);
+                if (sm & 8u)
+                    horizontal_pass_mul<K, short_taps<K>()>(stage, tq + K, prod);
+                else
+                    horizontal_pass_mul<K>(stage, tq + K, prod);
                 __syncthreads();
             } else {
                 float c[G::H_PER_THREAD][kNC];
@@ -409,10 +425,16 @@ correlate_update_kernel(const __grid_constant__ KParams kp) {
                     for (int j = 0; j < kNC; ++j) c[h][j] = 0.0f;
                 for (int q = 0; q < a.ft.crank[v]; ++q) {
                     const float *tq = kp.taps + (a.ft.ctap_off[v] + q) * 2 * K;
-                    vertical_pass<K>(tile, stage, tq);
+                    if (sm & 4u)
+                        vertical_pass<K, short_taps<K>()>(tile, stage, tq);
+                    else
+                        vertical_pass<K>(tile, stage, tq);
                     __syncthreads();
                     if (q == a.ft.crank[v] - 1) prefetch_next();
-                    horizontal_pass<K>(stage, tq + K, c);
+                    if (sm & 8u)
+                        horizontal_pass<K, short_taps<K>()>(stage, tq + K, c);
+                    else
+                        horizontal_pass<K>(stage, tq + K, c);
                     __syncthreads();
                 }
                 if (a.wnorm) {   // weighted MV-RL: c / n_v, or 1 where no weighted pixel is in reach

@@ -34,6 +34,8 @@ namespace mvd {
 namespace fused {
 
 constexpr int kThreads = 256;
+template <int K>
+__host__ __device__ constexpr int short_taps() { return K > kShortTaps ? kShortTaps : K; }
 constexpr int kNR = 16;      // rows per vertical item
 constexpr int kNC = 16;      // columns per horizontal item
 constexpr int kTX = 128;     // output tile width
@@ -101,22 +103,24 @@ __device__ __forceinline__ void load_tile_sw(float *__restrict__ tile, const flo
     }
 }
 
-// One vertical item: NR consecutive output rows r0.. of column c.
-template <int K, int NR>
+// One vertical item: NR consecutive output rows r0.. of column c, with the
+// KP central taps of the K-tap factor (KP = K: all of them).
+template <int K, int NR, int KP>
 __device__ __forceinline__ void vertical_item(const float *__restrict__ tile, float *__restrict__ stage,
-                                              const float (&t)[K], int c, int r0) {
+                                              const float (&t)[KP], int c, int r0) {
     using G = Geo<K>;
-    const float *col = tile + r0 * G::BOX_W + G::COL0 + c;
+    constexpr int OFF = (K - KP) / 2;
+    const float *col = tile + (r0 + OFF) * G::BOX_W + G::COL0 + c;
     float acc[NR];
 #pragma unroll
     for (int i = 0; i < NR; ++i) acc[i] = 0.0f;
 #pragma unroll
-    for (int m = 0; m < NR + K - 1; ++m) {
+    for (int m = 0; m < NR + KP - 1; ++m) {
         const float x = col[m * G::BOX_W];
 #pragma unroll
         for (int i = 0; i < NR; ++i) {
             const int j = m - i;
-            if (j >= 0 && j < K) acc[i] = fmaf(t[j], x, acc[i]);
+            if (j >= 0 && j < KP) acc[i] = fmaf(t[j], x, acc[i]);
         }
     }
     float *dst = stage + r0 * G::VB_LD + c;
@@ -129,23 +133,24 @@ __device__ __forceinline__ void vertical_item(const float *__restrict__ tile, fl
 // 16-row items (TX*TY/16 = a whole number of rounds of the CTA), the 2R halo
 // columns as 8-row items (one more round), so that no warp idles for long
 // at the barrier that follows.
-template <int K>
+template <int K, int KP = K>
 __device__ __forceinline__ void vertical_pass(const float *__restrict__ tile, float *__restrict__ stage,
                                               const float *__restrict__ taps_s) {
     using G = Geo<K>;
     static_assert((G::TX * (G::TY / kNR)) % kThreads == 0, "main vertical items must tile the CTA");
-    float t[K];
+    constexpr int OFF = (K - KP) / 2;
+    float t[KP];
 #pragma unroll
-    for (int m = 0; m < K; ++m) t[m] = taps_s[m];
+    for (int m = 0; m < KP; ++m) t[m] = taps_s[OFF + m];
     for (int it = threadIdx.x; it < G::TX * (G::TY / kNR); it += kThreads) {
         const int rb = it / G::TX;
-        vertical_item<K, kNR>(tile, stage, t, it - rb * G::TX, rb * kNR);
+        vertical_item<K, kNR, KP>(tile, stage, t, it - rb * G::TX, rb * kNR);
     }
     if (G::R > 0) {
         constexpr int HC = G::R > 0 ? 2 * G::R : 1;   // halo columns TX .. TX+2R-1
         for (int it = threadIdx.x; it < HC * (G::TY / 8); it += kThreads) {
             const int r8 = it / HC;
-            vertical_item<K, 8>(tile, stage, t, G::TX + (it - r8 * HC), r8 * 8);
+            vertical_item<K, 8, KP>(tile, stage, t, G::TX + (it - r8 * HC), r8 * 8);
         }
     }
 }
@@ -154,32 +159,35 @@ __device__ __forceinline__ void vertical_pass(const float *__restrict__ tile, fl
 // Inputs stream through registers four at a time (one 16-byte load), each
 // feeding every output it reaches, so only the 16 accumulators, the taps
 // and one quad are live.
-template <int K>
+// With KP < K only the KP central taps run: inputs start at the quad
+// boundary S <= OFF below the first one used, D = OFF - S places them.
+template <int K, int KP = K>
 __device__ __forceinline__ void horizontal_pass(const float *__restrict__ stage,
                                                 const float *__restrict__ taps_s,
                                                 float (&acc)[Geo<K>::H_PER_THREAD][kNC]) {
     using G = Geo<K>;
-    constexpr int NIN = kNC + K - 1;      // inputs actually used
-    float t[K];
+    constexpr int OFF = (K - KP) / 2, S = OFF & ~3, D = OFF - S;
+    constexpr int NIN = kNC + KP - 1 + D;      // inputs read from S on
+    float t[KP];
 #pragma unroll
-    for (int m = 0; m < K; ++m) t[m] = taps_s[m];
+    for (int m = 0; m < KP; ++m) t[m] = taps_s[OFF + m];
 #pragma unroll
     for (int h = 0; h < G::H_PER_THREAD; ++h) {
         const int it = threadIdx.x + h * kThreads;
         const int row = it % G::TY;
         const int g = it / G::TY;
-        const float4 *src = reinterpret_cast<const float4 *>(stage + row * G::VB_LD + g * kNC);
+        const float4 *src = reinterpret_cast<const float4 *>(stage + row * G::VB_LD + g * kNC + S);
 #pragma unroll
         for (int q = 0; q < (NIN + 3) / 4; ++q) {
             const float4 v = src[q];
             const float x4[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
-                const int i = 4 * q + e;          // input index
+                const int i = 4 * q + e;          // input index from S
 #pragma unroll
                 for (int j = 0; j < kNC; ++j) {
-                    const int m = i - j;
-                    if (i < NIN && m >= 0 && m < K) acc[h][j] = fmaf(t[m], x4[e], acc[h][j]);
+                    const int m = i - j - D;
+                    if (i < NIN && m >= 0 && m < KP) acc[h][j] = fmaf(t[m], x4[e], acc[h][j]);
                 }
             }
         }
@@ -189,19 +197,21 @@ __device__ __forceinline__ void horizontal_pass(const float *__restrict__ stage,
 // Horizontal pass of a one-term factorisation whose result multiplies into
 // `prod` item by item (the running product over views of kernel B), so no
 // second set of accumulators stays live.
-template <int K>
+template <int K, int KP = K>
 __device__ __forceinline__ void horizontal_pass_mul(const float *__restrict__ stage,
                                                     const float *__restrict__ taps_s,
                                                     float (&prod)[Geo<K>::H_PER_THREAD][kNC]) {
     using G = Geo<K>;
-    constexpr int NIN = kNC + K - 1;
-    float t[K];
+    constexpr int OFF = (K - KP) / 2, S = OFF & ~3, D = OFF - S;
+    constexpr int NIN = kNC + KP - 1 + D;
+    float t[KP];
 #pragma unroll
-    for (int m = 0; m < K; ++m) t[m] = taps_s[m];
+    for (int m = 0; m < KP; ++m) t[m] = taps_s[OFF + m];
 #pragma unroll
     for (int h = 0; h < G::H_PER_THREAD; ++h) {
         const int it = threadIdx.x + h * kThreads;
-        const float4 *src = reinterpret_cast<const float4 *>(stage + (it % G::TY) * G::VB_LD + (it / G::TY) * kNC);
+        const float4 *src =
+            reinterpret_cast<const float4 *>(stage + (it % G::TY) * G::VB_LD + (it / G::TY) * kNC + S);
         float acc[kNC];
 #pragma unroll
         for (int j = 0; j < kNC; ++j) acc[j] = 0.0f;
@@ -214,8 +224,8 @@ __device__ __forceinline__ void horizontal_pass_mul(const float *__restrict__ st
                 const int i = 4 * q + e;
 #pragma unroll
                 for (int j = 0; j < kNC; ++j) {
-                    const int m = i - j;
-                    if (i < NIN && m >= 0 && m < K) acc[j] = fmaf(t[m], x4[e], acc[j]);
+                    const int m = i - j - D;
+                    if (i < NIN && m >= 0 && m < KP) acc[j] = fmaf(t[m], x4[e], acc[j]);
                 }
             }
         }

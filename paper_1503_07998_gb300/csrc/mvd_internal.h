@@ -10,6 +10,9 @@
 namespace mvd {
 
 constexpr int kMaxViews = 64;
+// 1D factors whose taps beyond +-8 of the centre carry no mass above the
+// rank tolerance (narrow Gaussians) run with this many taps on the fused path.
+constexpr int kShortTaps = 17;
 constexpr int kFusedMaxK = 47;   // largest PSF side with a fused-kernel instance
 
 // Launch accounting (mvd_launch_count).
@@ -31,6 +34,10 @@ struct FactorTable {
     int rank[kMaxViews] = {};
     int tap_off[kMaxViews] = {};     // in units of terms
     int crank[kMaxViews] = {};       // terms of the correlation step (= rank for plain MV-RL)
+    // per view, the 1D factor kinds (bit k: blur vertical, blur horizontal,
+    // correlation vertical, correlation horizontal) whose every term keeps
+    // all but a rank-tolerance share of its mass in the kShortTaps central taps
+    unsigned char short_mask[kMaxViews] = {};
     int ctap_off[kMaxViews] = {};    // their offset (= tap_off for plain MV-RL)
     int group[kMaxViews] = {};       // blur group (views with identical PSFs)
     int n_groups = 0;

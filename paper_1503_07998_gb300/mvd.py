@@ -48,6 +48,7 @@ class _Info(ctypes.Structure):
         ("tile_h", ctypes.c_int), ("tile_w", ctypes.c_int),
         ("workspace_bytes", ctypes.c_size_t),
         ("variant", ctypes.c_int), ("corr_rank", ctypes.c_int * 16),
+        ("flops_blur", ctypes.c_int), ("flops_corr", ctypes.c_int),
     ]
 
 
@@ -164,6 +165,8 @@ class Info:
     workspace_bytes: int
     variant: int
     corr_rank: list
+    flops_blur: int
+    flops_corr: int
 
 
 class Context:
@@ -318,7 +321,8 @@ def mvd_get_info(ctx: Context) -> Info:
     _check(lib().mvd_get_info(ctx.handle, ctypes.byref(inf)), "mvd_get_info")
     return Info(inf.views, inf.psf_size, inf.plane_h, inf.plane_w, inf.iters, inf.boundary, inf.algo, inf.order,
                 list(inf.rank)[:min(16, inf.views)], inf.blur_groups, inf.blur_terms, inf.tile_h, inf.tile_w,
-                int(inf.workspace_bytes), inf.variant, list(inf.corr_rank)[:min(16, inf.views)])
+                int(inf.workspace_bytes), inf.variant, list(inf.corr_rank)[:min(16, inf.views)], inf.flops_blur,
+                inf.flops_corr)
 
 
 def mvd_reslice(ctx: Context, stacks, planes, stream=None) -> None:

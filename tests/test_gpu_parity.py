@@ -292,3 +292,41 @@ def test_volume_512_cubed_two_views_sampled_planes(mvd):
     phi = np.stack([planes[:, i].cpu().numpy() for i in sample], axis=1)
     ref = oracle.rl_planes(phi, psfs, 10, eps=1e-6, route="fft")
     assert_parity(est[sample].cpu().numpy(), ref, what="512^3 sampled planes")
+
+
+def test_narrow_factors_run_with_central_taps(mvd):
+    """31x31 PSFs sigma (1.5, 8) turned by 90 degrees: the lateral factors
+    keep all but ~1e-8 of their mass in their 17 central taps, so the fused
+    kernels run those passes short (info.flops_* count the taps run); the
+    result still matches the oracle.  Weighted runs keep every tap (a
+    zero-weight region's only signal comes through the tails): checked with
+    weights through kernel B's general path."""
+    c = synth.plane_case(seed=61, H=200, W=300, n_planes=2, n_blobs=80, K=31, sigma_axial=8.0,
+                         sigma_lateral=1.5, iters=5, dtype=np.uint16)
+    V, P, H, W = c.phi.shape
+    ctx = mvd.mvd_create(V, c.psfs, 31, H, W, 5, "zero", 1e-6)
+    try:
+        info = mvd.mvd_get_info(ctx)
+        assert info.flops_blur == 2 * 2 * (31 + 17) and info.flops_corr == 2 * 2 * (31 + 17)
+        mvd.mvd_set_rank_tolerance(ctx, 0.0)          # exact factors (every term kept): no short passes
+        info0 = mvd.mvd_get_info(ctx)
+        assert info0.flops_blur == 2 * info0.blur_terms * 62
+    finally:
+        ctx.close()
+    ref = oracle.rl_planes(c.phi, c.psfs, 5, eps=1e-6, route="fft")
+    assert_parity(run_gpu(mvd, c.phi, c.psfs, 5), ref, what="short factors")
+    w = np.random.default_rng(61).uniform(0.3, 1.0, size=c.phi.shape).astype(np.float32)
+    ctx = mvd.mvd_create(V, c.psfs, 31, H, W, 5, "zero", 1e-6)
+    try:
+        wt = torch.from_numpy(w).to(DEV)
+        mvd.mvd_set_weights(ctx, wt)
+        assert mvd.mvd_get_info(ctx).flops_blur == 2 * 2 * 62
+        d = torch.from_numpy(c.phi).to(DEV)
+        est = torch.empty((P, H, W), device=DEV)
+        mvd.mvd_deconvolve_planes(ctx, d, est)
+        torch.cuda.synchronize()
+        got = est.cpu().numpy()
+    finally:
+        ctx.close()
+    refw = oracle.rl_planes(c.phi, c.psfs, 5, eps=1e-6, weights=w.astype(np.float64))
+    assert_parity(got, refw, what="short factors, weighted")
