@@ -372,11 +372,16 @@ def run_mvd(args, wl):
         finally:
             mvd.mvd_set_algo(ctx, "fused")
 
-    # the optional tensor-core route (BF16x3 tcgen05 passes) on the same planes
-    tensor_route = None
-    if not args.no_plain:
+    # the optional tensor-core routes (BF16x3 and TF32 tcgen05 passes) on the
+    # same planes
+    tc_routes = {}
+    for algo, prefix, precision in (
+            ("tensor", "tc", "BF16x3 tcgen05 passes, FP32 accumulate; ratio and update FP32"),
+            ("tf32", "tf32", "TF32 tcgen05 passes (operands rounded to TF32), FP32 accumulate; ratio and update FP32")):
+        if args.no_plain:
+            break
         try:
-            mvd.mvd_set_algo(ctx, "tensor")
+            mvd.mvd_set_algo(ctx, algo)
             mvd.mvd_deconvolve_planes(ctx, planes, est)
             torch.cuda.synchronize()
             mvd.mvd_profile_enable(ctx, True)
@@ -389,15 +394,16 @@ def run_mvd(args, wl):
             mvd.mvd_profile_enable(ctx, False)
             tms = f0.elapsed_time(f1)
             tk = {n: kernel_roofline(tprof, n, vi_per_launch, b, f, hbm_peak)
-                  for n, b, f in (("tc_blur_ratio", 4 + (es + 4) * V, flops_a),
-                                  ("tc_correlate_update", 4 * V + 8, flops_b))}
-            tensor_route = {"value": units_per_step / (tms / 1e3), "unit": UNIT, "ms": tms,
-                            "precision": "BF16x3 tcgen05 passes, FP32 accumulate; ratio and update FP32",
-                            "note": "deconvolution only (no reslice)", "kernels": tk}
+                  for n, b, f in ((prefix + "_blur_ratio", 4 + (es + 4) * V, flops_a),
+                                  (prefix + "_correlate_update", 4 * V + 8, flops_b))}
+            tc_routes[algo] = {"value": units_per_step / (tms / 1e3), "unit": UNIT, "ms": tms,
+                               "precision": precision, "note": "deconvolution only (no reslice)", "kernels": tk}
         except mvd.MvdError as e:
-            tensor_route = {"unavailable": str(e)}
+            tc_routes[algo] = {"unavailable": str(e)}
         finally:
             mvd.mvd_set_algo(ctx, "fused")
+    tensor_route = tc_routes.get("tensor")
+    tf32_route = tc_routes.get("tf32")
 
     # weighted MV-RL on the padded domain: the planes embedded with zero
     # weights in an R-wide border (data + PSF size), deconvolved there, cropped
@@ -541,7 +547,7 @@ def run_mvd(args, wl):
                 "voxel_iterations_per_s": value / V,
                 "roofline": roof, "kernels": kr, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": int(launches), "clocks": clk, "plain_per_plane": plain,
-                "fft_route": fft_route, "tensor_route": tensor_route, "weighted_padded": weighted, "vol3d": vol3d, "psf_grad": grad,
+                "fft_route": fft_route, "tensor_route": tensor_route, "tf32_route": tf32_route, "weighted_padded": weighted, "vol3d": vol3d, "psf_grad": grad,
                 "paper_context": "GTX TITAN Black, 2 views, 1024^3 padded, 10 it: 21.1 s = 1.02e9 voxel-view-it/s "
                                  "(Supp. Table 1); another machine, not the target"}
         print(json.dumps(line))
@@ -579,9 +585,9 @@ def run_precision(args):
     """The precision configuration: 4 views of 1024^3 uint16 blobs (density
     5e-5) at 0/90/180/270 degrees, 41x41 PSFs sigma (1.8, 10) px, views in
     sequence, 10 iterations over all 1024 planes, on the FP32 fused route and
-    on the BF16x3 tensor-core route; `value` is the FP32 route's throughput,
-    the tensor route's difference to it is measured on the GPU (the error
-    against the FP64 oracle is stated by the parity tests)."""
+    on the BF16x3 and TF32 tensor-core routes; `value` is the FP32 route's
+    throughput, the tensor routes' differences to it are measured on the GPU
+    (their errors against the FP64 oracle are stated by the parity tests)."""
     import torch
     world, rank, _ = dist_setup(args.gpus)
     from paper_1503_07998_gb300 import mvd, synth
@@ -602,7 +608,7 @@ def run_precision(args):
     clocks.start()
     n0 = mvd.mvd_launch_count()
     clk = None
-    for route in ("fused", "tensor"):
+    for route in ("fused", "tensor", "tf32"):
         mvd.mvd_set_algo(ctx, route)
         est = torch.empty((Y, Z, X), device=dev)
         for _ in range(args.warmup):
@@ -624,8 +630,9 @@ def run_precision(args):
         ests[route] = est
     clk = clocks.stop(*clk)
     launches = mvd.mvd_launch_count() - n0
-    diff = float((torch.linalg.vector_norm(ests["tensor"] - ests["fused"]) /
-                  torch.linalg.vector_norm(ests["fused"])).item())
+    ref_norm = torch.linalg.vector_norm(ests["fused"])
+    diff = {r: float((torch.linalg.vector_norm(ests[r] - ests["fused"]) / ref_norm).item())
+            for r in ("tensor", "tf32")}
     ctx.close()
     if rank == 0:
         line = {"metric": METRIC, "value": routes["fused"]["value"], "unit": UNIT, "n_gpus": world,
@@ -637,7 +644,7 @@ def run_precision(args):
                            "l2": "inputs larger than L2",
                            "parallelism": f"{world} GPU(s), one independent volume per GPU, no collective"},
                 "routes": routes,
-                "tensor_rel_l2_vs_fp32": diff,
+                "tensor_rel_l2_vs_fp32": diff["tensor"], "tf32_rel_l2_vs_fp32": diff["tf32"],
                 "clocks": clk, "gpu_launches": int(launches)}
         print(json.dumps(line))
     if world > 1:

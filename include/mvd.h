@@ -94,7 +94,16 @@ typedef enum {
      * per product instead of 2^-24); the ratio, the product over views and
      * the update stay FP32.  Odd K <= 47, any number of separable terms,
      * both boundaries.  Never chosen by default or by mvd_autotune. */
-    MVD_ALGO_TENSOR = 4
+    MVD_ALGO_TENSOR = 4,
+    /* Optional reduced-precision tensor-core route: the same banded matrix
+     * products in TF32 (operands rounded to 10 explicit mantissa bits, round
+     * to nearest; FP32 accumulation: about 2^-11 relative error per product),
+     * one MMA per product.  The ratio, the product over views and the update
+     * stay FP32.  Odd K <= 47, any number of separable terms, both
+     * boundaries.  Its error against the exact result is larger than the
+     * FP32 routes' and is reported, not bounded by their tolerance.  Never
+     * chosen by default or by mvd_autotune. */
+    MVD_ALGO_TF32 = 5
 } mvd_algo;
 
 typedef enum {

@@ -266,6 +266,9 @@ mvd::FusedArgs fused_args(const mvd_ctx *c, const void *data, mvd_dtype dt, floa
 
 mvd_status fft_plan(mvd_ctx *c);
 
+// The tensor-core routes (BF16x3, TF32): the fused kernels' schedule.
+inline bool tensor_algo(mvd_algo a) { return a == MVD_ALGO_TENSOR || a == MVD_ALGO_TF32; }
+
 // Allocate everything a deconvolution of P planes needs, so that the call
 // itself allocates nothing (required while a stream is being captured).
 cudaError_t prepare_workspace(mvd_ctx *c, int P) {
@@ -277,7 +280,7 @@ cudaError_t prepare_workspace(mvd_ctx *c, int P) {
         e = c->fft.S0.ensure(rows * sizeof(float2));
         if (e == cudaSuccess) e = c->fft.T.ensure(rows * c->V * sizeof(float2));
     }
-    if (e == cudaSuccess && ((c->algo == MVD_ALGO_FUSED && mvd::fused_taps_fit(c->ft)) || c->algo == MVD_ALGO_TENSOR))
+    if (e == cudaSuccess && ((c->algo == MVD_ALGO_FUSED && mvd::fused_taps_fit(c->ft)) || tensor_algo(c->algo)))
         e = c->ratio.ensure(static_cast<size_t>(c->V) * P * plane_px * sizeof(float));
     if (e == cudaSuccess) e = c->plain.ensure(4 * plane_px * sizeof(float));
     if (e == cudaSuccess) e = upload_psf_dev(c);
@@ -299,7 +302,21 @@ mvd_status run_fused(mvd_ctx *c, const void *data, mvd_dtype dt, float *est, int
     }
     // simultaneous: one launch pair over all views; sequential: one per view
     const int step = c->order == MVD_ORDER_SEQUENTIAL ? 1 : c->V;
-    const bool tc = c->algo == MVD_ALGO_TENSOR;
+    // kernel A / kernel B of the selected route, with their profile names
+    cudaError_t (*blur)(const mvd::FusedArgs &, cudaStream_t) = mvd::launch_fused_blur_ratio;
+    cudaError_t (*corr)(const mvd::FusedArgs &, cudaStream_t) = mvd::launch_fused_correlate_update;
+    const char *blur_name = "blur_ratio", *corr_name = "correlate_update";
+    if (c->algo == MVD_ALGO_TENSOR) {
+        blur = mvd::launch_tc_blur_ratio;
+        corr = mvd::launch_tc_correlate_update;
+        blur_name = "tc_blur_ratio";
+        corr_name = "tc_correlate_update";
+    } else if (c->algo == MVD_ALGO_TF32) {
+        blur = mvd::launch_tf32_blur_ratio;
+        corr = mvd::launch_tf32_correlate_update;
+        blur_name = "tf32_blur_ratio";
+        corr_name = "tf32_correlate_update";
+    }
     bool first = init_mean != 0;
     for (int t = 0; t < c->iters; ++t) {
         for (int v0 = 0; v0 < c->V; v0 += step) {
@@ -307,11 +324,11 @@ mvd_status run_fused(mvd_ctx *c, const void *data, mvd_dtype dt, float *est, int
             a.view_hi = v0 + step;
             a.psi_in = first ? nullptr : est;
             first = false;
-            c->prof.mark(s, tc ? "tc_blur_ratio" : "blur_ratio");
-            e = tc ? mvd::launch_tc_blur_ratio(a, s) : mvd::launch_fused_blur_ratio(a, s);
+            c->prof.mark(s, blur_name);
+            e = blur(a, s);
             if (e != cudaSuccess) return cuda_fail(e, "blur/ratio kernel");
-            c->prof.mark(s, tc ? "tc_correlate_update" : "correlate_update");
-            e = tc ? mvd::launch_tc_correlate_update(a, s) : mvd::launch_fused_correlate_update(a, s);
+            c->prof.mark(s, corr_name);
+            e = corr(a, s);
             if (e != cudaSuccess) return cuda_fail(e, "correlate/update kernel");
         }
     }
@@ -926,9 +943,9 @@ mvd_status mvd_destroy(mvd_ctx *c) {
 mvd_status mvd_set_algo(mvd_ctx *c, mvd_algo algo) {
     if (!c) return fail(MVD_ERR_ARG, "ctx is NULL");
     if (algo != MVD_ALGO_FUSED && algo != MVD_ALGO_PLAIN && algo != MVD_ALGO_DIRECT && algo != MVD_ALGO_FFT &&
-        algo != MVD_ALGO_TENSOR)
+        !tensor_algo(algo))
         return fail(MVD_ERR_ARG, "unknown algo %d", static_cast<int>(algo));
-    if (algo == MVD_ALGO_TENSOR && !mvd::tc_supported(c->K))
+    if (tensor_algo(algo) && !mvd::tc_supported(c->K))
         return fail(MVD_ERR_UNSUPPORTED, "tensor-core route takes odd K <= 47 (got %d)", c->K);
     if (algo == MVD_ALGO_FUSED && !(mvd::fused_supported(c->K) && mvd::fused_taps_fit(c->ft)))
         return fail(MVD_ERR_UNSUPPORTED, "fused path takes K <= %d (got %d)", mvd::kFusedMaxK, c->K);
@@ -1097,6 +1114,8 @@ mvd_status mvd_get_info(const mvd_ctx *c, mvd_info *info) {
     info->blur_terms = c->ft.total_terms;
     if (c->algo == MVD_ALGO_TENSOR)
         mvd::tc_tile_shape(c->K, &info->tile_h, &info->tile_w);
+    else if (c->algo == MVD_ALGO_TF32)
+        mvd::tf32_tile_shape(c->K, &info->tile_h, &info->tile_w);
     else
         mvd::fused_tile_shape(c->K, &info->tile_h, &info->tile_w);
     info->workspace_bytes = c->taps.bytes + c->psf_dev.bytes + c->means.bytes + c->ratio.bytes + c->plain.bytes +
@@ -1167,14 +1186,14 @@ mvd_status mvd_deconvolve_planes(mvd_ctx *c, const void *data, mvd_dtype dt, flo
     if (c->weights) {
         if (c->weight_planes != 1 && n_planes != c->weight_planes)
             return fail(MVD_ERR_ARG, "weights were set for %d planes, the data have %d", c->weight_planes, n_planes);
-        if (c->algo == MVD_ALGO_FFT || c->algo == MVD_ALGO_TENSOR)
+        if (c->algo == MVD_ALGO_FFT || tensor_algo(c->algo))
             return fail(MVD_ERR_UNSUPPORTED, "weights run on the fused, plain and direct routes");
         mvd_status st = prepare_weights(c, c->weight_planes, s);
         if (st != MVD_OK) return st;
     }
     // the fused kernels carry the taps in their parameter block: PSFs that need
     // more separable terms than it holds run on the plain path
-    if ((c->algo == MVD_ALGO_FUSED && mvd::fused_taps_fit(c->ft)) || c->algo == MVD_ALGO_TENSOR)
+    if ((c->algo == MVD_ALGO_FUSED && mvd::fused_taps_fit(c->ft)) || tensor_algo(c->algo))
         return run_fused(c, data, dt, est, n_planes, init_mean, s);
     if (c->algo == MVD_ALGO_FFT) return run_fft(c, data, dt, est, n_planes, init_mean, s);
     return run_plain(c, data, dt, est, n_planes, init_mean, c->algo == MVD_ALGO_DIRECT, s);

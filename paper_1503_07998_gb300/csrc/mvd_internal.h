@@ -123,6 +123,10 @@ bool tc_supported(int K);
 void tc_tile_shape(int K, int *tile_h, int *tile_w);
 cudaError_t launch_tc_blur_ratio(const FusedArgs &a, cudaStream_t s);
 cudaError_t launch_tc_correlate_update(const FusedArgs &a, cudaStream_t s);
+// TF32 variant of the tensor-core kernels (same K range and tile rule).
+void tf32_tile_shape(int K, int *tile_h, int *tile_w);
+cudaError_t launch_tf32_blur_ratio(const FusedArgs &a, cudaStream_t s);
+cudaError_t launch_tf32_correlate_update(const FusedArgs &a, cudaStream_t s);
 
 // Fourier route (fft.cu).
 namespace fftr {

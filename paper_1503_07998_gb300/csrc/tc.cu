@@ -42,18 +42,25 @@
 #include <cstdint>
 #include <cstring>
 
-#include "mvd_internal.h"
-#include "tc5.cuh"
-#include "tma.cuh"
+#include "tc_common.cuh"
 
 namespace mvd {
 namespace tcr {
 
 namespace {
 
-constexpr int kThreads = 512;
-constexpr long long kDrainBudget = 4000000000LL;
-constexpr int kTmemCols = 512;
+using tcc::kDrainBudget;
+using tcc::kThreads;
+using tcc::kTmemCols;
+using tcc::Smem;
+using tcc::TcParams;
+using tcc::Tile;
+using tcc::align128;
+using tcc::load_phi;
+using tcc::setup;
+using tcc::store_ratio;
+using tcc::teardown;
+using tcc::wait_bar;
 
 template <int K>
 struct Geo {
@@ -89,16 +96,6 @@ struct Geo {
     static_assert(C_D2 + TY <= kTmemCols, "tensor-memory columns");
     static_assert(SMEM_BYTES <= 232448, "shared memory per CTA");
 };
-
-struct TcParams {
-    CUtensorMap map;   // psi (kernel A) or the ratio planes (kernel B); valid if use_tma
-    FusedArgs a;
-    int use_tma;
-};
-
-__device__ __forceinline__ unsigned char *align128(unsigned char *p) {
-    return reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(p) + 127) & ~static_cast<uintptr_t>(127));
-}
 
 // BF16 hi and lo parts of two FP32 values, packed (first value in the low half).
 __device__ __forceinline__ void split2(float x0, float x1, uint32_t &hi, uint32_t &lo) {
@@ -276,70 +273,9 @@ __device__ __forceinline__ void read_d2(uint32_t tmem, float (&d)[Geo<K>::NE]) {
     tc5::wait_ld();
 }
 
-// Bounded wait on `bar`: thread 0 polls while the others park at the CTA
-// barrier (spinning warps would take issue slots from the MMA-issuing
-// thread); on a timeout flag the status, drain once more and make the CTA
-// leave.
-__device__ __forceinline__ bool wait_bar(uint64_t *bar, uint32_t parity, const FusedArgs &a,
-                                         volatile int *abort_flag) {
-    if (threadIdx.x == 0) {
-        if (a.wait_budget < 0 || !tma::mbar_wait_bounded(bar, parity, a.wait_budget)) {
-            atomicOr(a.err, kDevTimeout);
-            tma::mbar_wait_bounded(bar, parity, kDrainBudget);
-            *abort_flag = 1;
-        }
-    }
-    __syncthreads();
-    return *abort_flag == 0;
-}
-
-struct Tile {
-    int p, y0, x0;
-};
-
 template <int K>
 __device__ __forceinline__ Tile tile_of(int t, int tiles_x, int tiles_y) {
-    using G = Geo<K>;
-    const int per_plane = tiles_x * tiles_y;
-    const int p = t / per_plane;
-    const int r = t - p * per_plane;
-    const int ty = r / tiles_x;
-    return {p, ty * G::TY, (r - ty * tiles_x) * G::TX};
-}
-
-// Shared setup: barriers, tensor memory.
-struct Smem {
-    uint64_t *bar_tma, *bar_mma;
-    volatile int *abort_flag;
-    uint32_t *tmem_slot;
-};
-
-__device__ __forceinline__ Smem setup(unsigned char *smem) {
-    Smem s;
-    s.bar_tma = reinterpret_cast<uint64_t *>(smem);
-    s.bar_mma = reinterpret_cast<uint64_t *>(smem + 8);
-    s.abort_flag = reinterpret_cast<volatile int *>(smem + 16);
-    s.tmem_slot = reinterpret_cast<uint32_t *>(smem + 20);
-    if (threadIdx.x == 0) {
-        tma::mbar_init(s.bar_tma, 1);
-        tma::mbar_init(s.bar_mma, 1);
-        *s.abort_flag = 0;
-        tma::fence_barrier_init();
-    }
-    if (threadIdx.x < 32) {
-        tc5::alloc(s.tmem_slot, kTmemCols);
-        tc5::relinquish();
-    }
-    tc5::fence_before();
-    __syncthreads();
-    tc5::fence_after();
-    return s;
-}
-
-__device__ __forceinline__ void teardown(uint32_t tmem) {
-    tc5::fence_before();
-    __syncthreads();
-    if (threadIdx.x < 32) tc5::dealloc(tmem, kTmemCols);
+    return tcc::tile_of<Geo<K>::TX, Geo<K>::TY>(t, tiles_x, tiles_y);
 }
 
 // One group of SVD terms (a PSF's blur, or a view's correlation) on the input
@@ -355,7 +291,7 @@ __device__ bool run_terms(const FusedArgs &a, const Smem &s, uint32_t tmem, unsi
     for (int q = 0; q < n_terms; ++q) {
         if (q > 0) {
             // the previous term's pass 2 still reads T2 and A2
-            if (!wait_bar(s.bar_mma, ph_mma, a, s.abort_flag)) return false;
+            if (!wait_bar(s.bar1, ph_mma, a, s.abort_flag)) return false;
             ph_mma ^= 1;
             tc5::fence_after();
         }
@@ -367,9 +303,9 @@ __device__ bool run_terms(const FusedArgs &a, const Smem &s, uint32_t tmem, unsi
         if (threadIdx.x == 0) {
             tc5::fence_after();
             issue_pass1<K>(tmem, tc5::smem_u32(b1));
-            tc5::commit(s.bar_mma);
+            tc5::commit(s.bar1);
         }
-        if (!wait_bar(s.bar_mma, ph_mma, a, s.abort_flag)) return false;
+        if (!wait_bar(s.bar1, ph_mma, a, s.abort_flag)) return false;
         ph_mma ^= 1;
         tc5::fence_after();
         split_d1<K>(tmem);
@@ -378,7 +314,7 @@ __device__ bool run_terms(const FusedArgs &a, const Smem &s, uint32_t tmem, unsi
         if (threadIdx.x == 0) {
             tc5::fence_after();
             issue_pass2<K>(tmem, tc5::smem_u32(t2), q > 0);
-            tc5::commit(s.bar_mma);
+            tc5::commit(s.bar1);
         }
     }
     return true;
@@ -386,45 +322,10 @@ __device__ bool run_terms(const FusedArgs &a, const Smem &s, uint32_t tmem, unsi
 
 // Wait for the MMAs run_terms committed; D2 is then readable.
 __device__ __forceinline__ bool finish_terms(const FusedArgs &a, const Smem &s, uint32_t &ph_mma) {
-    if (!wait_bar(s.bar_mma, ph_mma, a, s.abort_flag)) return false;
+    if (!wait_bar(s.bar1, ph_mma, a, s.abort_flag)) return false;
     ph_mma ^= 1;
     tc5::fence_after();
     return true;
-}
-
-// Raw data of view v at this thread's output column and rows (NE values,
-// uint16 or FP32 bits).  Nothing here consumes a loaded value, so all NE
-// loads are in flight together; store_ratio converts them.
-template <int K>
-__device__ __forceinline__ void load_phi(const FusedArgs &a, int v, int p, int y0, int x,
-                                         uint32_t (&phi)[Geo<K>::NE]) {
-    using G = Geo<K>;
-    const long long base = (static_cast<long long>(v) * a.P + p) * a.H * a.W + x;
-    const int n = min(G::NE, a.H - y0);
-    if (a.phi_u16) {
-        const uint16_t *src = static_cast<const uint16_t *>(a.phi) + base;
-#pragma unroll
-        for (int j = 0; j < G::NE; ++j)
-            phi[j] = j < n ? static_cast<uint32_t>(__ldg(src + static_cast<long long>(y0 + j) * a.W)) : 0u;
-    } else {
-        const float *src = static_cast<const float *>(a.phi) + base;
-#pragma unroll
-        for (int j = 0; j < G::NE; ++j)
-            phi[j] = j < n ? __float_as_uint(__ldg(src + static_cast<long long>(y0 + j) * a.W)) : 0u;
-    }
-}
-
-template <int K>
-__device__ __forceinline__ void store_ratio(const FusedArgs &a, int v, int p, int y0, int x,
-                                            const uint32_t (&phi)[Geo<K>::NE], const float (&d)[Geo<K>::NE]) {
-    using G = Geo<K>;
-    const long long base = (static_cast<long long>(v) * a.P + p) * a.H * a.W + x;
-#pragma unroll
-    for (int j = 0; j < G::NE; ++j) {
-        const int y = y0 + j;
-        const float f = a.phi_u16 ? static_cast<float>(phi[j]) : __uint_as_float(phi[j]);
-        if (y < a.H) a.ratio[base + static_cast<long long>(y) * a.W] = __fdividef(f, fmaxf(d[j], a.eps));
-    }
 }
 
 // Input tile of (tile t, z) into B1, then the staging tile is released: thread
@@ -512,17 +413,17 @@ __global__ void __launch_bounds__(kThreads, 1) tc_blur_ratio_kernel(const __grid
             if (!ok) break;
             // the first view's data load overlaps the MMAs
             uint32_t phi[G::NE];
-            if (x < a.W) load_phi<K>(a, v0, c.p, c.y0 + row0, x, phi);
+            if (x < a.W) load_phi<G::NE>(a, v0, c.p, c.y0 + row0, x, phi);
             ok = finish_terms(a, s, ph_mma);
             if (!ok) break;
             float d[G::NE];
             read_d2<K>(tmem, d);
             if (x < a.W) {
-                store_ratio<K>(a, v0, c.p, c.y0 + row0, x, phi, d);
+                store_ratio<G::NE>(a, v0, c.p, c.y0 + row0, x, phi, d);
                 for (int v = v0 + 1; v < a.view_hi; ++v) {
                     if (a.ft.group[v] != g) continue;
-                    load_phi<K>(a, v, c.p, c.y0 + row0, x, phi);
-                    store_ratio<K>(a, v, c.p, c.y0 + row0, x, phi, d);
+                    load_phi<G::NE>(a, v, c.p, c.y0 + row0, x, phi);
+                    store_ratio<G::NE>(a, v, c.p, c.y0 + row0, x, phi, d);
                 }
             }
             tc5::fence_before();
@@ -615,35 +516,6 @@ __global__ void __launch_bounds__(kThreads, 1) tc_correlate_update_kernel(const 
 
 // ---- host side ------------------------------------------------------------
 
-PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
-    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-    static bool tried = false;
-    if (!tried) {
-        tried = true;
-        void *p = nullptr;
-        cudaDriverEntryPointQueryResult q;
-        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
-                cudaSuccess &&
-            q == cudaDriverEntryPointSuccess)
-            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
-    }
-    return fn;
-}
-
-bool encode(CUtensorMap *m, const void *base, int W, int H, long long D, int box_w, int box_h) {
-    auto fn = encode_fn();
-    if (!fn) return false;
-    cuuint64_t dims[3] = {static_cast<cuuint64_t>(W), static_cast<cuuint64_t>(H), static_cast<cuuint64_t>(D)};
-    cuuint64_t strides[2] = {static_cast<cuuint64_t>(W) * 4, static_cast<cuuint64_t>(W) * H * 4};
-    cuuint32_t box[3] = {static_cast<cuuint32_t>(box_w), static_cast<cuuint32_t>(box_h), 1};
-    cuuint32_t estr[3] = {1, 1, 1};
-    return fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<void *>(base), dims, strides, box, estr,
-              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
-}
-
-inline bool aligned16(const void *p) { return reinterpret_cast<uintptr_t>(p) % 16 == 0; }
-
 template <int K>
 cudaError_t launch(const FusedArgs &a, int which, cudaStream_t st) {
     using G = Geo<K>;
@@ -660,15 +532,9 @@ cudaError_t launch(const FusedArgs &a, int which, cudaStream_t st) {
         if (e != cudaSuccess) return e;
         attr_set |= bit;
     }
-    static int sms[64] = {};
-    if (!sms[dev & 63]) {
-        int n = 0;
-        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
-        sms[dev & 63] = n > 0 ? n : 1;
-    }
     const long long n_tiles = static_cast<long long>((a.W + G::TX - 1) / G::TX) * ((a.H + G::TY - 1) / G::TY) * a.P;
     if (n_tiles > 0x7fffffffLL) return cudaErrorInvalidValue;
-    long long ctas = sms[dev & 63];   // one CTA per SM (shared memory and tensor memory)
+    long long ctas = tcc::sm_count(dev);   // one CTA per SM (shared memory and tensor memory)
     if (a.max_ctas > 0 && a.max_ctas < ctas) ctas = a.max_ctas;
     const dim3 grid(static_cast<unsigned>(n_tiles < ctas ? n_tiles : ctas));
     TcParams kp;
@@ -676,11 +542,11 @@ cudaError_t launch(const FusedArgs &a, int which, cudaStream_t st) {
     kp.a = a;
     const bool tma_ok = !a.circular && (a.W % 4 == 0);
     if (which == 0) {
-        if (tma_ok && a.psi_in && aligned16(a.psi_in)) kp.use_tma = encode(&kp.map, a.psi_in, a.W, a.H, a.P, G::KA, G::ROWS);
+        if (tma_ok && a.psi_in && tcc::aligned16(a.psi_in)) kp.use_tma = tcc::encode(&kp.map, a.psi_in, a.W, a.H, a.P, G::KA, G::ROWS);
         tc_blur_ratio_kernel<K><<<grid, kThreads, G::SMEM_BYTES, st>>>(kp);
     } else {
-        if (tma_ok && aligned16(a.ratio))
-            kp.use_tma = encode(&kp.map, a.ratio, a.W, a.H, static_cast<long long>(a.ft.views) * a.P, G::KA, G::ROWS);
+        if (tma_ok && tcc::aligned16(a.ratio))
+            kp.use_tma = tcc::encode(&kp.map, a.ratio, a.W, a.H, static_cast<long long>(a.ft.views) * a.P, G::KA, G::ROWS);
         tc_correlate_update_kernel<K><<<grid, kThreads, G::SMEM_BYTES, st>>>(kp);
     }
     count_launch();

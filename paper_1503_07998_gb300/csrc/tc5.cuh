@@ -1,15 +1,16 @@
 // 5th-generation tensor core (tcgen05) building blocks in inline PTX for
 // sm_103a: tensor-memory allocation, shared-memory matrix descriptors, the
-// BF16 MMA with FP32 accumulation in tensor memory, its completion signal on
-// an mbarrier, and tensor-memory loads.
+// BF16 and TF32 MMAs with FP32 accumulation in tensor memory, their
+// completion signal on an mbarrier, and tensor-memory loads and stores.
 //
 // Operand layouts (no swizzle).  A matrix is stored as 8 x 16-byte "core
-// matrices" (8 rows of 8 BF16 values); a descriptor gives the start address,
+// matrices" (8 rows of 8 BF16 or 4 TF32 values); a descriptor gives the start address,
 // the byte stride between core matrices adjacent along K (LBO field) and the
 // byte stride between core matrices adjacent along M or N (SBO field), for
 // K-major and MN-major operands alike.
-//   K-major  element (row r, k):  (r % 8) * 16 + (r / 8) * SBO + (k % 8) * 2 + (k / 8) * LBO
-//   MN-major element (row r, k):  (r % 8) * 2  + (r / 8) * SBO + (k % 8) * 16 + (k / 8) * LBO
+//   K-major  element (row r, k):  (r % 8) * 16 + (r / 8) * SBO + (k % 8) * 2 + (k / 8) * LBO   (BF16)
+//                                 (r % 8) * 16 + (r / 8) * SBO + (k % 4) * 4 + (k / 4) * LBO   (TF32)
+//   MN-major element (row r, k):  (r % 8) * 2  + (r / 8) * SBO + (k % 8) * 16 + (k / 8) * LBO   (BF16)
 // Tensor memory: 128 lanes x 512 columns of 32 bits per SM; for M = 128 the
 // accumulator row m sits in lane m, column n in column base + n.  A warp can
 // read only the 32 lanes of its quarter (warp index mod 4).
@@ -39,6 +40,14 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t saddr, uint32_t lbo, uint32_t
 __host__ __device__ constexpr uint32_t idesc_bf16(int M, int N, bool a_mn, bool b_mn) {
     return (1u << 4) | (1u << 7) | (1u << 10) | (a_mn ? 1u << 15 : 0u) | (b_mn ? 1u << 16 : 0u) |
            (static_cast<uint32_t>(N >> 3) << 17) | (static_cast<uint32_t>(M >> 4) << 24);
+}
+
+// Instruction descriptor of kind::tf32: TF32 A and B (format code 2 in both
+// type fields), FP32 accumulator, M x N tile, both operands K-major.  One MMA
+// covers K = 8 (32 bytes of a row, two core matrices).
+__host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) {
+    return (1u << 4) | (2u << 7) | (2u << 10) | (static_cast<uint32_t>(N >> 3) << 17) |
+           (static_cast<uint32_t>(M >> 4) << 24);
 }
 
 // Whole warp: allocate `ncols` (power of two >= 32) tensor-memory columns and
@@ -118,6 +127,26 @@ __device__ __forceinline__ void mma_bf16_ta(uint32_t d_tmem, uint32_t a_tmem, ui
         "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}" ::"r"(d_tmem),
         "r"(a_tmem), "l"(b), "r"(idesc), "r"(accumulate)
         : "memory");
+}
+
+// One thread: D (tensor memory) = A * B (+ D), kind::tf32, A from tensor
+// memory (one TF32 value per 32-bit column), B from shared memory.
+__device__ __forceinline__ void mma_tf32_ta(uint32_t d_tmem, uint32_t a_tmem, uint64_t b, uint32_t idesc,
+                                            uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "r"(a_tmem), "l"(b), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+// FP32 -> TF32 (10 explicit mantissa bits), round to nearest, ties away from
+// zero; the result is an FP32 bit pattern whose low 13 bits are zero.
+__device__ __forceinline__ uint32_t to_tf32(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return r;
 }
 
 // Warp: write N consecutive columns of each thread's lane (N = 16, 8, 4, 2, 1).
