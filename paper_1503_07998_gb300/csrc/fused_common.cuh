@@ -155,6 +155,52 @@ __device__ __forceinline__ void vertical_pass(const float *__restrict__ tile, fl
     }
 }
 
+// Packed FP32 pairs (lo, hi) in one 64-bit register pair: one fma.rn.f32x2
+// does two independent FP32 FMAs with the rounding of two fmaf calls.
+__device__ __forceinline__ unsigned long long pk2(float lo, float hi) {
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ void upk2(unsigned long long r, float &lo, float &hi) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(r));
+}
+__device__ __forceinline__ unsigned long long ffma2(unsigned long long a, unsigned long long b,
+                                                    unsigned long long c) {
+    unsigned long long d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+
+// One horizontal item on packed pairs: out[j] = sum_m t[m] in[j + m + D]
+// for j = 0..15, as 8 output pairs (2p, 2p+1).  Output pair p takes tap m
+// times the input pair starting at 2p + m + D: the quads' aligned pairs for
+// even starts, pairs straddling two lanes of the quad (rebuilt) for odd
+// ones.  Same products and the same summation order per output as the
+// scalar form.
+template <int KP, int D, int NIN>
+__device__ __forceinline__ void hrow_x2(const float4 *__restrict__ src, const float (&t)[KP],
+                                        unsigned long long (&A)[kNC / 2]) {
+    float prev = 0.0f;
+#pragma unroll
+    for (int q = 0; q < (NIN + 3) / 4; ++q) {
+        const float4 v = src[q];
+        // pairs starting at 4q-1, 4q, 4q+1, 4q+2
+        const unsigned long long pr[4] = {pk2(prev, v.x), pk2(v.x, v.y), pk2(v.y, v.z), pk2(v.z, v.w)};
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const int i = 4 * q - 1 + e;     // pair start (input index from S)
+            if (i < 0 || i + 1 >= NIN) continue;
+#pragma unroll
+            for (int p = 0; p < kNC / 2; ++p) {
+                const int m = i - 2 * p - D;
+                if (m >= 0 && m < KP) A[p] = ffma2(pk2(t[m], t[m]), pr[e], A[p]);
+            }
+        }
+        prev = v.w;
+    }
+}
+
 // Horizontal pass for this thread's items: acc[h][j] += sum_m t[m] * stage[row][16g + j + m].
 // Inputs stream through registers four at a time (one 16-byte load), each
 // feeding every output it reaches, so only the 16 accumulators, the taps
@@ -177,20 +223,12 @@ __device__ __forceinline__ void horizontal_pass(const float *__restrict__ stage,
         const int row = it % G::TY;
         const int g = it / G::TY;
         const float4 *src = reinterpret_cast<const float4 *>(stage + row * G::VB_LD + g * kNC + S);
+        unsigned long long A[kNC / 2];
 #pragma unroll
-        for (int q = 0; q < (NIN + 3) / 4; ++q) {
-            const float4 v = src[q];
-            const float x4[4] = {v.x, v.y, v.z, v.w};
+        for (int p = 0; p < kNC / 2; ++p) A[p] = pk2(acc[h][2 * p], acc[h][2 * p + 1]);
+        hrow_x2<KP, D, NIN>(src, t, A);
 #pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                const int i = 4 * q + e;          // input index from S
-#pragma unroll
-                for (int j = 0; j < kNC; ++j) {
-                    const int m = i - j - D;
-                    if (i < NIN && m >= 0 && m < KP) acc[h][j] = fmaf(t[m], x4[e], acc[h][j]);
-                }
-            }
-        }
+        for (int p = 0; p < kNC / 2; ++p) upk2(A[p], acc[h][2 * p], acc[h][2 * p + 1]);
     }
 }
 
@@ -212,25 +250,17 @@ __device__ __forceinline__ void horizontal_pass_mul(const float *__restrict__ st
         const int it = threadIdx.x + h * kThreads;
         const float4 *src =
             reinterpret_cast<const float4 *>(stage + (it % G::TY) * G::VB_LD + (it / G::TY) * kNC + S);
-        float acc[kNC];
+        unsigned long long A[kNC / 2];
 #pragma unroll
-        for (int j = 0; j < kNC; ++j) acc[j] = 0.0f;
+        for (int p = 0; p < kNC / 2; ++p) A[p] = 0ull;
+        hrow_x2<KP, D, NIN>(src, t, A);
 #pragma unroll
-        for (int q = 0; q < (NIN + 3) / 4; ++q) {
-            const float4 v = src[q];
-            const float x4[4] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                const int i = 4 * q + e;
-#pragma unroll
-                for (int j = 0; j < kNC; ++j) {
-                    const int m = i - j - D;
-                    if (i < NIN && m >= 0 && m < KP) acc[j] = fmaf(t[m], x4[e], acc[j]);
-                }
-            }
+        for (int p = 0; p < kNC / 2; ++p) {
+            float lo, hi;
+            upk2(A[p], lo, hi);
+            prod[h][2 * p] *= lo;
+            prod[h][2 * p + 1] *= hi;
         }
-#pragma unroll
-        for (int j = 0; j < kNC; ++j) prod[h][j] *= acc[j];
     }
 }
 
