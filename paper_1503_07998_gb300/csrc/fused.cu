@@ -111,10 +111,10 @@ __device__ __forceinline__ void store4(float *dst, bool vec, int n, const float 
 //   MODE 0 (ratio):  ratio = phi / max(stage, eps)   (base: plane of view v)
 //   MODE 1 (update): psi_out = psi_in * stage, or mean * stage on the first
 //                    iteration                         (base: plane p)
-template <int K, int MODE>
+template <int K, int MODE, int TYF = 0>
 __device__ __forceinline__ void row_epilogue(const FusedArgs &a, int vec_ok, const float *__restrict__ stage,
                                              long long base, int y0, int x0, float mean) {
-    using G = Geo<K>;
+    using G = Geo<K, TYF>;
     constexpr int WARPS = kThreads / 32;
     constexpr int ROWS = G::TY / WARPS;
     static_assert(G::TX == 4 * 32, "one warp covers one tile row");
@@ -159,15 +159,18 @@ struct TileCoord {
     int p, y0, x0;
 };
 
-template <int K>
+template <int K, int TYF = 0>
 __device__ __forceinline__ TileCoord tile_coord(int t, int tiles_x, int tiles_y) {
-    using G = Geo<K>;
+    using G = Geo<K, TYF>;
     const int per_plane = tiles_x * tiles_y;
     const int p = t / per_plane;
     const int r = t - p * per_plane;
     const int ty = r / tiles_x;
     return {p, ty * G::TY, (r - ty * tiles_x) * G::TX};
 }
+
+// Tile height of kernel B (32 rows, three CTAs per SM where they fit).
+constexpr int kTyB = 32;
 
 // Persistent: each CTA walks tiles blockIdx.x, blockIdx.x + gridDim.x, ...
 // With TMA, the next tile's psi box is requested right after the last
@@ -339,9 +342,9 @@ blur_ratio_kernel(const __grid_constant__ KParams kp) {
 // Persistent like kernel A.  The ratio box of the next (tile, view) is
 // requested right after the last vertical pass of the current view.
 template <int K>
-__global__ void __launch_bounds__(kThreads, Geo<K>::MIN_BLOCKS)
+__global__ void __launch_bounds__(kThreads, Geo<K, kTyB>::MIN_BLOCKS)
 correlate_update_kernel(const __grid_constant__ KParams kp) {
-    using G = Geo<K>;
+    using G = Geo<K, kTyB>;
     const FusedArgs &a = kp.a;
     extern __shared__ __align__(128) unsigned char smem[];
     uint64_t *bar = reinterpret_cast<uint64_t *>(smem);
@@ -364,13 +367,13 @@ correlate_update_kernel(const __grid_constant__ KParams kp) {
     __syncthreads();
     int t = blockIdx.x;
     if (use_tma && threadIdx.x == 0 && t < n_tiles) {
-        const TileCoord c = tile_coord<K>(t, tiles_x, tiles_y);
+        const TileCoord c = tile_coord<K, kTyB>(t, tiles_x, tiles_y);
         tma::mbar_arrive_expect_tx(bar, G::TILE_BYTES);
         tma::load_3d(tile, &kp.map, bar, c.x0 - G::R4, c.y0 - G::R, a.view_lo * a.P + c.p);
     }
     uint32_t phase = 0;
     for (; t < n_tiles; t += gridDim.x) {
-        const TileCoord tc = tile_coord<K>(t, tiles_x, tiles_y);
+        const TileCoord tc = tile_coord<K, kTyB>(t, tiles_x, tiles_y);
         const int p = tc.p, y0 = tc.y0, x0 = tc.x0;
         const int t_next = t + gridDim.x;
         float prod[G::H_PER_THREAD][kNC];
@@ -385,7 +388,7 @@ correlate_update_kernel(const __grid_constant__ KParams kp) {
                 phase ^= 1u;
             } else {
                 const float *rsrc = a.ratio + (static_cast<long long>(v) * a.P + p) * plane_px;
-                load_tile_sw<K>(tile, rsrc, 0.0f, y0, x0, a.H, a.W, a.circular);
+                load_tile_sw<K, kTyB>(tile, rsrc, 0.0f, y0, x0, a.H, a.W, a.circular);
                 __syncthreads();
             }
             // the ratio box of the next (tile, view), requested once the tile is free
@@ -397,7 +400,7 @@ correlate_update_kernel(const __grid_constant__ KParams kp) {
                     nv = a.view_lo;
                 }
                 if (nt < n_tiles) {
-                    const TileCoord c2 = tile_coord<K>(nt, tiles_x, tiles_y);
+                    const TileCoord c2 = tile_coord<K, kTyB>(nt, tiles_x, tiles_y);
                     tma::fence_proxy_async_smem();
                     tma::mbar_arrive_expect_tx(bar, G::TILE_BYTES);
                     tma::load_3d(tile, &kp.map, bar, c2.x0 - G::R4, c2.y0 - G::R, nv * a.P + c2.p);
@@ -407,15 +410,15 @@ correlate_update_kernel(const __grid_constant__ KParams kp) {
             if (a.ft.crank[v] == 1 && !a.wnorm) {
                 const float *tq = kp.taps + a.ft.ctap_off[v] * 2 * K;
                 if (sm & 4u)
-                    vertical_pass<K, short_taps<K>()>(tile, stage, tq);
+                    vertical_pass<K, short_taps<K>(), kTyB>(tile, stage, tq);
                 else
-                    vertical_pass<K>(tile, stage, tq);
+                    vertical_pass<K, K, kTyB>(tile, stage, tq);
                 __syncthreads();
                 prefetch_next();
                 if (sm & 8u)
-                    horizontal_pass_mul<K, short_taps<K>()>(stage, tq + K, prod);
+                    horizontal_pass_mul<K, short_taps<K>(), kTyB>(stage, tq + K, prod);
                 else
-                    horizontal_pass_mul<K>(stage, tq + K, prod);
+                    horizontal_pass_mul<K, K, kTyB>(stage, tq + K, prod);
                 __syncthreads();
             } else {
                 float c[G::H_PER_THREAD][kNC];
@@ -426,15 +429,15 @@ correlate_update_kernel(const __grid_constant__ KParams kp) {
                 for (int q = 0; q < a.ft.crank[v]; ++q) {
                     const float *tq = kp.taps + (a.ft.ctap_off[v] + q) * 2 * K;
                     if (sm & 4u)
-                        vertical_pass<K, short_taps<K>()>(tile, stage, tq);
+                        vertical_pass<K, short_taps<K>(), kTyB>(tile, stage, tq);
                     else
-                        vertical_pass<K>(tile, stage, tq);
+                        vertical_pass<K, K, kTyB>(tile, stage, tq);
                     __syncthreads();
                     if (q == a.ft.crank[v] - 1) prefetch_next();
                     if (sm & 8u)
-                        horizontal_pass<K, short_taps<K>()>(stage, tq + K, c);
+                        horizontal_pass<K, short_taps<K>(), kTyB>(stage, tq + K, c);
                     else
-                        horizontal_pass<K>(stage, tq + K, c);
+                        horizontal_pass<K, K, kTyB>(stage, tq + K, c);
                     __syncthreads();
                 }
                 if (a.wnorm) {   // weighted MV-RL: c / n_v, or 1 where no weighted pixel is in reach
@@ -443,7 +446,7 @@ correlate_update_kernel(const __grid_constant__ KParams kp) {
 #pragma unroll
                     for (int h = 0; h < G::H_PER_THREAD; ++h) {
                         int y, x;
-                        item_origin<K>(h, y0, x0, y, x);
+                        item_origin<K, kTyB>(h, y0, x0, y, x);
                         if (y >= a.H || x >= a.W) continue;
                         const int n = min(kNC, a.W - x);
                         const long long off = vplane + static_cast<long long>(y) * a.W + x;
@@ -465,9 +468,9 @@ correlate_update_kernel(const __grid_constant__ KParams kp) {
         }
 
         // update epilogue, row by row: psi' = psi * prod with whole row segments
-        park_items<K>(stage, prod);
+        park_items<K, kTyB>(stage, prod);
         __syncthreads();
-        row_epilogue<K, 1>(a, kp.vec_ok, stage, p * plane_px, y0, x0,
+        row_epilogue<K, 1, kTyB>(a, kp.vec_ok, stage, p * plane_px, y0, x0,
                           a.psi_in ? 0.0f : __ldg(a.means + p));
         __syncthreads();   // the staging tile is rewritten by the next pass
     }
@@ -505,20 +508,20 @@ bool encode_3d(CUtensorMap *m, const void *base, int W, int H, long long D, int 
 
 inline bool aligned16(const void *p) { return reinterpret_cast<uintptr_t>(p) % 16 == 0; }
 
-template <int K>
-cudaError_t launch_pair(const FusedArgs &a, int which, cudaStream_t s) {
-    using G = Geo<K>;
+template <int K, int TYF>
+cudaError_t launch_one(const FusedArgs &a, int which, cudaStream_t s) {
+    using G = Geo<K, TYF>;
     // the shared-memory opt-in is per function and device
     static unsigned long long attr_set = 0;
     int dev = 0;
     cudaGetDevice(&dev);
     const unsigned long long bit = 1ull << (dev & 63);
     if (!(attr_set & bit)) {
-        cudaError_t e = cudaFuncSetAttribute(blur_ratio_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             G::SMEM_BYTES);
-        if (e != cudaSuccess) return e;
-        e = cudaFuncSetAttribute(correlate_update_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 G::SMEM_BYTES);
+        const cudaError_t e =
+            which == 0 ? cudaFuncSetAttribute(blur_ratio_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              G::SMEM_BYTES)
+                       : cudaFuncSetAttribute(correlate_update_kernel<K>,
+                                              cudaFuncAttributeMaxDynamicSharedMemorySize, G::SMEM_BYTES);
         if (e != cudaSuccess) return e;
         attr_set |= bit;
     }
@@ -574,7 +577,7 @@ cudaError_t dispatch(const FusedArgs &a, int which, cudaStream_t s) {
     switch (a.ft.K) {
 #define MVD_CASE(k) \
     case k:         \
-        return launch_pair<k>(a, which, s);
+        return which == 0 ? launch_one<k, 0>(a, 0, s) : launch_one<k, kTyB>(a, 1, s);
         MVD_FUSED_CASES(MVD_CASE)
 #undef MVD_CASE
         default:

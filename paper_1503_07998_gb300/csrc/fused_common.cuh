@@ -41,8 +41,9 @@ constexpr int kNC = 16;      // columns per horizontal item
 constexpr int kTX = 128;     // output tile width
 constexpr int kHeaderBytes = 128;   // mbarrier + abort flag
 constexpr int kTileOffset = kHeaderBytes;   // a multiple of 128 for the TMA destination
-// Two CTAs per SM: 228 KB per SM minus 1 KB reserved per CTA.
+// Two / three CTAs per SM: 228 KB per SM minus 1 KB reserved per CTA.
 constexpr int kTwoCtaSmem = 113 * 1024;
+constexpr int kThreeCtaSmem = 75 * 1024;
 
 __host__ __device__ constexpr int round_up(int a, int b) { return (a + b - 1) / b * b; }
 
@@ -51,7 +52,11 @@ __host__ __device__ constexpr int odd_quad_pitch(int w) {
     return ((round_up(w, 4) / 4) % 2 == 1) ? round_up(w, 4) : round_up(w, 4) + 4;
 }
 
-template <int K>
+// TYF = 0: the tile height of kernel A (64 rows while two CTAs fit on an
+// SM, else 32); TYF > 0: that height, with three CTAs per SM where their
+// shared memory fits (kernel B's choice: more resident warps hide its
+// ratio-tile and estimate loads better than taller tiles save).
+template <int K, int TYF = 0>
 struct Geo {
     static constexpr int R = (K - 1) / 2;
     static constexpr int R4 = round_up(R, 4);
@@ -65,7 +70,7 @@ struct Geo {
         return kTileOffset + ((ty + 2 * R) * BOX_W + ty * VB_LD) * 4;
     }
     // 64-row tiles while two CTAs still fit on an SM, else 32.
-    static constexpr int TY = (smem_bytes(64) <= kTwoCtaSmem) ? 64 : 32;
+    static constexpr int TY = TYF ? TYF : ((smem_bytes(64) <= kTwoCtaSmem) ? 64 : 32);
     static constexpr int BOX_H = TY + 2 * R;
     static constexpr int SMEM_BYTES = smem_bytes(TY);
     static constexpr int TILE_BYTES = BOX_H * BOX_W * 4;
@@ -74,17 +79,18 @@ struct Geo {
     static constexpr int H_PER_THREAD = H_ITEMS / kThreads;
     static_assert(H_ITEMS % kThreads == 0, "horizontal items must tile the CTA");
     static_assert(BOX_W <= 256 && BOX_H <= 256, "TMA box dimensions are at most 256");
-    static constexpr int MIN_BLOCKS = (SMEM_BYTES <= kTwoCtaSmem) ? 2 : 1;
+    static constexpr int MIN_BLOCKS =
+        (TYF && SMEM_BYTES <= kThreeCtaSmem) ? 3 : ((SMEM_BYTES <= kTwoCtaSmem) ? 2 : 1);
 };
 
 // Software tile load (circular boundary, unaligned planes): same layout as
 // the TMA box.  src == nullptr means a constant plane of value `fill`
 // (iteration 0 from the per-plane mean).  ZERO: zero outside the plane;
 // CIRCULAR: indices modulo the plane size.
-template <int K>
+template <int K, int TYF = 0>
 __device__ __forceinline__ void load_tile_sw(float *__restrict__ tile, const float *__restrict__ src,
                                              float fill, int y0, int x0, int H, int W, int circular) {
-    using G = Geo<K>;
+    using G = Geo<K, TYF>;
     constexpr int N = G::BOX_H * G::BOX_W;
     for (int idx = threadIdx.x; idx < N; idx += kThreads) {
         const int r = idx / G::BOX_W;
@@ -105,10 +111,10 @@ __device__ __forceinline__ void load_tile_sw(float *__restrict__ tile, const flo
 
 // One vertical item: NR consecutive output rows r0.. of column c, with the
 // KP central taps of the K-tap factor (KP = K: all of them).
-template <int K, int NR, int KP>
+template <int K, int NR, int KP, int TYF>
 __device__ __forceinline__ void vertical_item(const float *__restrict__ tile, float *__restrict__ stage,
                                               const float (&t)[KP], int c, int r0) {
-    using G = Geo<K>;
+    using G = Geo<K, TYF>;
     constexpr int OFF = (K - KP) / 2;
     const float *col = tile + (r0 + OFF) * G::BOX_W + G::COL0 + c;
     float acc[NR];
@@ -133,10 +139,10 @@ __device__ __forceinline__ void vertical_item(const float *__restrict__ tile, fl
 // 16-row items (TX*TY/16 = a whole number of rounds of the CTA), the 2R halo
 // columns as 8-row items (one more round), so that no warp idles for long
 // at the barrier that follows.
-template <int K, int KP = K>
+template <int K, int KP = K, int TYF = 0>
 __device__ __forceinline__ void vertical_pass(const float *__restrict__ tile, float *__restrict__ stage,
                                               const float *__restrict__ taps_s) {
-    using G = Geo<K>;
+    using G = Geo<K, TYF>;
     static_assert((G::TX * (G::TY / kNR)) % kThreads == 0, "main vertical items must tile the CTA");
     constexpr int OFF = (K - KP) / 2;
     float t[KP];
@@ -144,13 +150,13 @@ __device__ __forceinline__ void vertical_pass(const float *__restrict__ tile, fl
     for (int m = 0; m < KP; ++m) t[m] = taps_s[OFF + m];
     for (int it = threadIdx.x; it < G::TX * (G::TY / kNR); it += kThreads) {
         const int rb = it / G::TX;
-        vertical_item<K, kNR, KP>(tile, stage, t, it - rb * G::TX, rb * kNR);
+        vertical_item<K, kNR, KP, TYF>(tile, stage, t, it - rb * G::TX, rb * kNR);
     }
     if (G::R > 0) {
         constexpr int HC = G::R > 0 ? 2 * G::R : 1;   // halo columns TX .. TX+2R-1
         for (int it = threadIdx.x; it < HC * (G::TY / 8); it += kThreads) {
             const int r8 = it / HC;
-            vertical_item<K, 8, KP>(tile, stage, t, G::TX + (it - r8 * HC), r8 * 8);
+            vertical_item<K, 8, KP, TYF>(tile, stage, t, G::TX + (it - r8 * HC), r8 * 8);
         }
     }
 }
@@ -207,11 +213,11 @@ __device__ __forceinline__ void hrow_x2(const float4 *__restrict__ src, const fl
 // and one quad are live.
 // With KP < K only the KP central taps run: inputs start at the quad
 // boundary S <= OFF below the first one used, D = OFF - S places them.
-template <int K, int KP = K>
+template <int K, int KP = K, int TYF = 0>
 __device__ __forceinline__ void horizontal_pass(const float *__restrict__ stage,
                                                 const float *__restrict__ taps_s,
-                                                float (&acc)[Geo<K>::H_PER_THREAD][kNC]) {
-    using G = Geo<K>;
+                                                float (&acc)[Geo<K, TYF>::H_PER_THREAD][kNC]) {
+    using G = Geo<K, TYF>;
     constexpr int OFF = (K - KP) / 2, S = OFF & ~3, D = OFF - S;
     constexpr int NIN = kNC + KP - 1 + D;      // inputs read from S on
     float t[KP];
@@ -235,11 +241,11 @@ __device__ __forceinline__ void horizontal_pass(const float *__restrict__ stage,
 // Horizontal pass of a one-term factorisation whose result multiplies into
 // `prod` item by item (the running product over views of kernel B), so no
 // second set of accumulators stays live.
-template <int K, int KP = K>
+template <int K, int KP = K, int TYF = 0>
 __device__ __forceinline__ void horizontal_pass_mul(const float *__restrict__ stage,
                                                     const float *__restrict__ taps_s,
-                                                    float (&prod)[Geo<K>::H_PER_THREAD][kNC]) {
-    using G = Geo<K>;
+                                                    float (&prod)[Geo<K, TYF>::H_PER_THREAD][kNC]) {
+    using G = Geo<K, TYF>;
     constexpr int OFF = (K - KP) / 2, S = OFF & ~3, D = OFF - S;
     constexpr int NIN = kNC + KP - 1 + D;
     float t[KP];
@@ -268,10 +274,10 @@ __device__ __forceinline__ void horizontal_pass_mul(const float *__restrict__ st
 // output positions (row, 16g + j).  Lanes run along rows and the pitch is an
 // odd multiple of 4 floats, so the 16-byte stores are conflict-free.  The
 // caller synchronises before the tile is read back row by row.
-template <int K>
+template <int K, int TYF = 0>
 __device__ __forceinline__ void park_items(float *__restrict__ stage,
-                                           const float (&acc)[Geo<K>::H_PER_THREAD][kNC]) {
-    using G = Geo<K>;
+                                           const float (&acc)[Geo<K, TYF>::H_PER_THREAD][kNC]) {
+    using G = Geo<K, TYF>;
 #pragma unroll
     for (int h = 0; h < G::H_PER_THREAD; ++h) {
         const int it = threadIdx.x + h * kThreads;
@@ -283,9 +289,9 @@ __device__ __forceinline__ void park_items(float *__restrict__ stage,
 }
 
 // Output coordinates of horizontal item h of this thread.
-template <int K>
+template <int K, int TYF = 0>
 __device__ __forceinline__ void item_origin(int h, int y0, int x0, int &y, int &x) {
-    using G = Geo<K>;
+    using G = Geo<K, TYF>;
     const int it = threadIdx.x + h * kThreads;
     y = y0 + it % G::TY;
     x = x0 + (it / G::TY) * kNC;
