@@ -274,9 +274,15 @@ def run_mvd(args, wl):
     planes = torch.empty((V, Y, Z, X), dtype=stacks.dtype, device=dev)
     est = torch.empty((Y, Z, X), dtype=torch.float32, device=dev)
 
-    def step():
+    def step(marks=None):
+        if marks:
+            marks[0].record(stream)
         mvd.mvd_reslice(ctx, stacks, planes)
+        if marks:
+            marks[1].record(stream)
         mvd.mvd_deconvolve_planes(ctx, planes, est, init_mean=True)
+        if marks:
+            marks[2].record(stream)
 
     for _ in range(args.warmup):
         step()
@@ -287,17 +293,24 @@ def run_mvd(args, wl):
     mvd.mvd_profile_enable(ctx, True)
     n0 = mvd.mvd_launch_count()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    # per-step marks (reslice, deconvolution) for the medians; recording an
+    # event costs nothing measurable next to a step
+    step_marks = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
     torch.cuda.synchronize()
     barrier(world)
     first_row = clocks.mark()
     ev0.record(stream)
-    for _ in range(args.steps):
-        step()
+    for i in range(args.steps):
+        step(step_marks[i])
     ev1.record(stream)
     torch.cuda.synchronize()
     last_row = max(clocks.mark(), first_row + 1)   # at least the first sample after the start
     barrier(world)
     ms = ev0.elapsed_time(ev1)
+    timing = {"steps_timed": args.steps,
+              "step_ms_median": statistics.median(m[0].elapsed_time(m[2]) for m in step_marks),
+              "reslice_ms_median": statistics.median(m[0].elapsed_time(m[1]) for m in step_marks),
+              "deconvolve_ms_median": statistics.median(m[1].elapsed_time(m[2]) for m in step_marks)}
     launches = mvd.mvd_launch_count() - n0
     prof = mvd.mvd_profile_read(ctx)
     mvd.mvd_profile_enable(ctx, False)
@@ -545,6 +558,7 @@ def run_mvd(args, wl):
                            "l2": "inputs larger than L2: 512 MiB of stacks + 512 MiB of planes per step",
                            "parallelism": f"{world} GPU(s), one independent volume per GPU, no collective"},
                 "voxel_iterations_per_s": value / V,
+                "timing": timing,
                 "roofline": roof, "kernels": kr, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": int(launches), "clocks": clk, "plain_per_plane": plain,
                 "fft_route": fft_route, "tensor_route": tensor_route, "tf32_route": tf32_route, "weighted_padded": weighted, "vol3d": vol3d, "psf_grad": grad,
