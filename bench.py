@@ -345,9 +345,12 @@ def run_mvd(args, wl):
     roof.update({"kernel": dom, "traffic": NCU_TRAFFIC_PER_LAUNCH.get(dom),
                  "hbm_gbs": d["hbm_gbs"], "hbm_frac": d["hbm_frac"], "avg_launch_ms": d["avg_ms"]})
 
+    def leg(name):   # the comparison legs this run includes
+        return not args.no_plain and (args.legs == "all" or name in args.legs.split(","))
+
     # plain per-plane path on a slice of the planes (same context and factors)
     plain = None
-    if not args.no_plain:
+    if leg("plain"):
         sub = min(Y, 32)
         mvd.mvd_set_algo(ctx, "plain")
         e2 = est[:sub].contiguous()
@@ -369,7 +372,7 @@ def run_mvd(args, wl):
 
     # the Fourier route on the same planes (same context, one call = 10 iterations)
     fft_route = None
-    if not args.no_plain:
+    if leg("fft"):
         try:
             mvd.mvd_set_algo(ctx, "fft")
             mvd.mvd_deconvolve_planes(ctx, planes, est)
@@ -391,8 +394,8 @@ def run_mvd(args, wl):
     for algo, prefix, precision in (
             ("tensor", "tc", "BF16x3 tcgen05 passes, FP32 accumulate; ratio and update FP32"),
             ("tf32", "tf32", "TF32 tcgen05 passes (operands rounded to TF32), FP32 accumulate; ratio and update FP32")):
-        if args.no_plain:
-            break
+        if not leg(algo):
+            continue
         try:
             mvd.mvd_set_algo(ctx, algo)
             mvd.mvd_deconvolve_planes(ctx, planes, est)
@@ -421,7 +424,7 @@ def run_mvd(args, wl):
     # weighted MV-RL on the padded domain: the planes embedded with zero
     # weights in an R-wide border (data + PSF size), deconvolved there, cropped
     weighted = None
-    if not args.no_plain:
+    if leg("weighted"):
         R = ((X + K - 1 + 15) // 16 * 16 - X) // 2    # >= (K-1)/2, padded width a 16-multiple
         pctx = mvd.mvd_create(V, psfs, K, Z + 2 * R, X + 2 * R, iters, "zero", 1e-6)
         try:
@@ -455,7 +458,7 @@ def run_mvd(args, wl):
     # on the same planes, and what the plane-wise approximation loses against
     # it on 3D-blurred synthetic volumes with known truth
     vol3d = None
-    if not args.no_plain and rank == 0:
+    if leg("vol3d") and rank == 0:
         from paper_1503_07998_gb300 import synth
         ax = synth.gaussian_1d(11, 1.5).astype(np.float32)
         mvd.mvd_set_axial_psfs(ctx, np.stack([ax] * V))
@@ -501,7 +504,7 @@ def run_mvd(args, wl):
     # PSFs started at sigma (1.2, 5) px on data made with (1.5, 7) px,
     # 10 unrolled iterations, checkpoint every 2
     grad = None
-    if not args.no_plain and rank == 0:
+    if leg("grad") and rank == 0:
         from paper_1503_07998_gb300 import synth
         gs, gp = synth.volume_stacks(256, 64, 256, 31, 7.0, 1.5, (0.0, 90.0), 2e-3, seed=5, device=dev)
         gplanes = torch.empty((2, 64, 256, 256), dtype=gs.dtype, device=dev)
@@ -580,7 +583,9 @@ def main():
     ap.add_argument("--workload", default="volume512", choices=sorted(WORKLOADS) + ["batch64", "precision1024"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--no-plain", action="store_true", help="none of the comparison legs")
+    ap.add_argument("--legs", default="all",
+                    help="comparison legs to run: all, or a comma list of plain,fft,tensor,tf32,weighted,vol3d,grad")
     args = ap.parse_args()
     if args.warmup < 3:
         print("note: at least 3 warm-up steps are used", file=sys.stderr)

@@ -241,6 +241,20 @@ mvd_status mvd_run_host(mvd_ctx *ctx, const void *stacks_host, mvd_dtype dt,
                         int nz, int ny, int nx, float *out_host, int chunk_planes,
                         void *stream);
 
+/* The chunks of planes mvd_run_host uses for ny planes of plane_bytes input
+ * bytes each (all views).  With chunk_planes > 0 the chunks hold chunk_planes
+ * planes (the last one the rest).  With chunk_planes = 0 they are chosen
+ * automatically: about 128 MiB of input per chunk, except that the first and
+ * the last chunk hold a quarter of that.  The iterations then start after a
+ * short first copy, the last copy back is short, and every other copy
+ * overlaps the iterations of a neighbouring chunk.  Small volumes get four
+ * equal chunks instead.  Writes chunk i as planes y0[i] .. y0[i] + n[i] - 1,
+ * in order and covering 0 .. ny - 1, for at most `cap` chunks.  Returns the
+ * number of chunks, or -1 if an argument is invalid (ny < 1,
+ * plane_bytes < 1, chunk_planes < 0, NULL arrays) or cap is too small.
+ * Host only: no device work. */
+int mvd_host_chunks(int ny, long long plane_bytes, int chunk_planes, int *y0, int *n, int cap);
+
 /* Device-side status of the context's kernels.  Waits for `stream`, then
  * reads and clears the context's device status word: MVD_ERR_TIMEOUT if a
  * kernel's bounded wait for a tile copy ran out (the kernel then left its

@@ -1199,6 +1199,36 @@ mvd_status mvd_deconvolve_planes(mvd_ctx *c, const void *data, mvd_dtype dt, flo
     return run_plain(c, data, dt, est, n_planes, init_mean, c->algo == MVD_ALGO_DIRECT, s);
 }
 
+int mvd_host_chunks(int ny, long long plane_bytes, int chunk_planes, int *y0, int *n, int cap) {
+    if (ny < 1 || plane_bytes < 1 || chunk_planes < 0 || !y0 || !n) return -1;
+    std::vector<int> sizes;
+    if (chunk_planes > 0) {
+        for (int y = 0; y < ny; y += chunk_planes) sizes.push_back(std::min(chunk_planes, ny - y));
+    } else {
+        const long long base = std::max(1LL, std::min<long long>(ny, (128LL << 20) / plane_bytes));
+        const int edge = static_cast<int>(std::max(1LL, base / 4));
+        if (ny >= 2 * edge + base && base >= 4) {
+            // short first and last chunks, the middle in equal parts of at most `base`
+            const int mid = ny - 2 * edge;
+            const int parts = static_cast<int>((mid + base - 1) / base);
+            sizes.push_back(edge);
+            for (int i = 0; i < parts; ++i) sizes.push_back(mid / parts + (i < mid % parts ? 1 : 0));
+            sizes.push_back(edge);
+        } else {
+            const int cp = std::max(1, (ny + 3) / 4);
+            for (int y = 0; y < ny; y += cp) sizes.push_back(std::min(cp, ny - y));
+        }
+    }
+    if (static_cast<int>(sizes.size()) > cap) return -1;
+    int y = 0;
+    for (size_t i = 0; i < sizes.size(); ++i) {
+        y0[i] = y;
+        n[i] = sizes[i];
+        y += sizes[i];
+    }
+    return static_cast<int>(sizes.size());
+}
+
 mvd_status mvd_run_host(mvd_ctx *c, const void *stacks_host, mvd_dtype dt, int nz, int ny, int nx, float *out_host,
                         int chunk_planes, void *stream) {
     t_last_error.clear();
@@ -1212,14 +1242,12 @@ mvd_status mvd_run_host(mvd_ctx *c, const void *stacks_host, mvd_dtype dt, int n
     DeviceGuard g(c->device);
     const size_t es = dt == MVD_U16 ? 2 : 4;
     const size_t plane_px = static_cast<size_t>(nz) * nx;
-    int cp = chunk_planes;
-    if (cp == 0) {
-        // about 64 MiB of input per chunk, at least 4 chunks when there are enough planes
-        const size_t per_plane = c->V * plane_px * es;
-        cp = static_cast<int>(std::max<size_t>(1, (64u << 20) / per_plane));
-        cp = std::min(cp, std::max(1, (ny + 3) / 4));
-    }
-    cp = std::min(cp, ny);
+    const long long per_plane = static_cast<long long>(c->V) * plane_px * es;
+    const int max_chunks = chunk_planes > 0 ? (ny + chunk_planes - 1) / chunk_planes : ny;
+    std::vector<int> cy0(max_chunks), cyn(max_chunks);
+    const int nchunks = mvd_host_chunks(ny, per_plane, chunk_planes, cy0.data(), cyn.data(), max_chunks);
+    if (nchunks < 1) return fail(MVD_ERR_ARG, "no chunk schedule for %d planes", ny);
+    const int cp = *std::max_element(cyn.begin(), cyn.begin() + nchunks);
     cudaError_t e;
     for (int i = 0; i < 2; ++i) {
         if ((e = c->run_stack[i].ensure(c->V * plane_px * cp * es)) != cudaSuccess ||
@@ -1233,7 +1261,6 @@ mvd_status mvd_run_host(mvd_ctx *c, const void *stacks_host, mvd_dtype dt, int n
     if (!c->copy_out && (e = cudaStreamCreateWithFlags(&c->copy_out, cudaStreamNonBlocking)) != cudaSuccess)
         return cuda_fail(e, "stream");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    const int nchunks = (ny + cp - 1) / cp;
     std::vector<cudaEvent_t> ev(4 * static_cast<size_t>(nchunks), nullptr);
     auto evt = [&](int kind, int i) -> cudaEvent_t & { return ev[4 * static_cast<size_t>(i) + kind]; };
     enum { kH2D = 0, kResliced = 1, kComputed = 2, kD2H = 3 };
@@ -1246,7 +1273,7 @@ mvd_status mvd_run_host(mvd_ctx *c, const void *stacks_host, mvd_dtype dt, int n
     }
     const char *src = static_cast<const char *>(stacks_host);
     for (int i = 0; i < nchunks && st == MVD_OK; ++i) {
-        const int y0 = i * cp, yn = std::min(cp, ny - y0), slot = i % 2;
+        const int y0 = cy0[i], yn = cyn[i], slot = i % 2;
         // H2D into the stack slot once the reslice of chunk i-2 has consumed it
         if (i >= 2) cudaStreamWaitEvent(c->copy_in, evt(kResliced, i - 2), 0);
         char *dst = c->run_stack[slot].as<char>();

@@ -90,6 +90,8 @@ def lib() -> ctypes.CDLL:
     L.mvd_reslice.argtypes = [vp, vp, i, i, i, i, i, vp, vp]
     L.mvd_deconvolve_planes.argtypes = [vp, vp, i, vp, i, i, vp]
     L.mvd_run_host.argtypes = [vp, vp, i, i, i, i, vp, i, vp]
+    L.mvd_host_chunks.argtypes = [i, ctypes.c_longlong, i, vp, vp, i]
+    L.mvd_host_chunks.restype = ctypes.c_int
     L.mvd_psf_factors.argtypes = [vp, i, i, d, vp, vp, i]
     L.mvd_profile_enable.argtypes = [vp, i]
     L.mvd_profile_read.argtypes = [vp, ctypes.POINTER(_KernelStat), i, ctypes.POINTER(i)]
@@ -387,6 +389,17 @@ def mvd_run_host(ctx: Context, stacks_host, out_host, chunk_planes: int = 0, str
     _check(lib().mvd_run_host(ctx.handle, ctypes.c_void_p(stacks_host.data_ptr()), _dtype_code(stacks_host),
                               Z, Y, X, ctypes.c_void_p(out_host.data_ptr()), int(chunk_planes),
                               ctypes.c_void_p(int(stream))), "mvd_run_host")
+
+
+def mvd_host_chunks(ny: int, plane_bytes: int, chunk_planes: int = 0):
+    """The chunks of planes mvd_run_host uses: a list of (first plane, count)."""
+    y0 = np.zeros(max(1, ny), dtype=np.int32)
+    n = np.zeros(max(1, ny), dtype=np.int32)
+    k = lib().mvd_host_chunks(int(ny), int(plane_bytes), int(chunk_planes), y0.ctypes.data_as(ctypes.c_void_p),
+                              n.ctypes.data_as(ctypes.c_void_p), int(max(1, ny)))
+    if k < 0:
+        raise MvdError(MVD_ERR_ARG, "mvd_host_chunks", "invalid arguments or too many chunks")
+    return [(int(a), int(b)) for a, b in zip(y0[:k], n[:k])]
 
 
 def mvd_psf_factors(psfs, rank_tol: float = 3e-7):

@@ -143,3 +143,48 @@ def test_variant_rejects_bad_arguments():
     st = mvd.lib().mvd_variant_kernels(psfs.ctypes.data_as(ctypes.c_void_p), 2, 5, 7,
                                        out.ctypes.data_as(ctypes.c_void_p))
     assert st == mvd.MVD_ERR_ARG
+
+
+def test_host_chunks_uniform_and_small_volumes():
+    assert mvd.mvd_host_chunks(37, 7680, 8) == [(0, 8), (8, 8), (16, 8), (24, 8), (32, 5)]
+    # small volume, automatic: four equal chunks
+    assert mvd.mvd_host_chunks(37, 7680, 0) == [(0, 10), (10, 10), (20, 10), (30, 7)]
+    assert mvd.mvd_host_chunks(1, 1 << 20, 0) == [(0, 1)]
+    assert mvd.mvd_host_chunks(3, 1 << 20, 5) == [(0, 3)]
+
+
+def test_host_chunks_ramp_for_large_volumes():
+    # 512 planes of 1 MiB (2 views of 512 x 512 uint16): 128-plane chunks,
+    # the first and the last a quarter of that
+    assert mvd.mvd_host_chunks(512, 1 << 20, 0) == [(0, 32), (32, 112), (144, 112), (256, 112), (368, 112),
+                                                    (480, 32)]
+    # 1024 planes of 4 MiB (4 views of 1024 x 1024 uint16): 32-plane chunks, edges of 8
+    ch = mvd.mvd_host_chunks(1024, 4 << 20, 0)
+    assert ch[0] == (0, 8) and ch[-1] == (1016, 8) and max(n for _, n in ch) <= 32
+
+
+def test_host_chunks_cover_every_plane_once():
+    rng = np.random.default_rng(3)
+    for _ in range(300):
+        ny = int(rng.integers(1, 3000))
+        pb = int(rng.integers(1, 1 << 24))
+        cp = int(rng.integers(0, 50)) if rng.random() < 0.5 else 0
+        ch = mvd.mvd_host_chunks(ny, pb, cp)
+        y = 0
+        for y0, n in ch:
+            assert y0 == y and n >= 1
+            if cp:
+                assert n <= cp
+            y += n
+        assert y == ny
+
+
+def test_host_chunks_rejects_bad_arguments():
+    for args in ((0, 100, 0), (5, 0, 0), (5, 100, -1)):
+        with pytest.raises(mvd.MvdError):
+            mvd.mvd_host_chunks(*args)
+    y0 = np.zeros(2, dtype=np.int32)
+    n = np.zeros(2, dtype=np.int32)
+    # three chunks do not fit two slots
+    assert mvd.lib().mvd_host_chunks(30, 100, 10, y0.ctypes.data_as(ctypes.c_void_p),
+                                     n.ctypes.data_as(ctypes.c_void_p), 2) == -1
