@@ -142,11 +142,14 @@ __device__ __forceinline__ void mma_tf32_ta(uint32_t d_tmem, uint32_t a_tmem, ui
 }
 
 // FP32 -> TF32 (10 explicit mantissa bits), round to nearest, ties away from
-// zero; the result is an FP32 bit pattern whose low 13 bits are zero.
+// zero; the result is an FP32 bit pattern whose low 13 bits are zero.  On the
+// sign-magnitude bit pattern, adding half a TF32 unit (bit 12) and clearing
+// the 13 dropped bits rounds the magnitude half away from zero; a carry out
+// of the mantissa correctly bumps the exponent.  Two integer operations,
+// equal to cvt.rna.tf32.f32 for finite inputs (checked bit for bit on the
+// tensor-route workloads).
 __device__ __forceinline__ uint32_t to_tf32(float x) {
-    uint32_t r;
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-    return r;
+    return (__float_as_uint(x) + 0x1000u) & 0xFFFFE000u;
 }
 
 // Warp: write N consecutive columns of each thread's lane (N = 16, 8, 4, 2, 1).
