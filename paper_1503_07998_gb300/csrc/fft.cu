@@ -171,7 +171,7 @@ __global__ void __launch_bounds__(kThreads) fft_rows_kernel(const FftArgs a, int
     const long long splane = static_cast<long long>(a.H) * srow;
     __syncthreads();
 
-    if (MODE == ROW_PSI) {
+    if constexpr (MODE == ROW_PSI) {
         const float m = a.psi_in ? 0.0f : __ldg(a.means + p);
         for (int i = lane; i < Lx; i += per) {
             float r0 = 0.0f, r1 = 0.0f;
@@ -190,68 +190,67 @@ __global__ void __launch_bounds__(kThreads) fft_rows_kernel(const FftArgs a, int
             if (have0) a.S0[p * splane + y0 * srow + k] = A;
             if (have1) a.S0[p * splane + (y0 + 1) * srow + k] = B;
         }
-        return;
-    }
-
-    for (int v = a.view_lo; v < a.view_hi; ++v) {
-        float2 *T = a.T + (static_cast<long long>(v) * a.P + p) * splane;
-        // Hermitian rebuild of the two rows' full spectra into Z = A + iB
-        for (int k = lane; k < Lx; k += per) {
-            float2 A = make_float2(0.f, 0.f), B = make_float2(0.f, 0.f);
-            const bool lo = k < a.Lc;
-            const int kk = lo ? k : Lx - k;
-            if (have0) A = T[y0 * srow + kk];
-            if (have1) B = T[(y0 + 1) * srow + kk];
-            if (!lo) {
-                A.y = -A.y;
-                B.y = -B.y;
-            }
-            x[k] = make_float2(A.x - B.y, A.y + B.x);
-        }
-        __syncthreads();
-        float2 *z = fft_group<true>(x, y, Lx, a.rad_x, a.nrad_x, tw, lane, per);
-        float2 *zo = (z == x) ? y : x;
-        if (MODE == ROW_RATIO) {
-            const long long dbase = (static_cast<long long>(v) * a.P + p) * plane;
-            for (int i = lane; i < Lx; i += per) {
-                float r0 = 0.f, r1 = 0.f;
-                if (i < a.W) {
-                    const float2 b = z[i];
-                    if (have0) r0 = data_at(a.phi, a.u16, dbase + static_cast<long long>(y0) * a.W + i) / fmaxf(b.x, a.eps);
-                    if (have1) r1 = data_at(a.phi, a.u16, dbase + static_cast<long long>(y0 + 1) * a.W + i) / fmaxf(b.y, a.eps);
+    } else {
+        for (int v = a.view_lo; v < a.view_hi; ++v) {
+            float2 *T = a.T + (static_cast<long long>(v) * a.P + p) * splane;
+            // Hermitian rebuild of the two rows' full spectra into Z = A + iB
+            for (int k = lane; k < Lx; k += per) {
+                float2 A = make_float2(0.f, 0.f), B = make_float2(0.f, 0.f);
+                const bool lo = k < a.Lc;
+                const int kk = lo ? k : Lx - k;
+                if (have0) A = T[y0 * srow + kk];
+                if (have1) B = T[(y0 + 1) * srow + kk];
+                if (!lo) {
+                    A.y = -A.y;
+                    B.y = -B.y;
                 }
-                zo[i] = make_float2(r0, r1);
+                x[k] = make_float2(A.x - B.y, A.y + B.x);
             }
             __syncthreads();
-            float2 *Z = fft_group<false>(zo, z, Lx, a.rad_x, a.nrad_x, tw, lane, per);
-            for (int k = lane; k < a.Lc; k += per) {
-                const float2 q = Z[k], qc = Z[(Lx - k) % Lx];
-                if (have0) T[y0 * srow + k] = make_float2(0.5f * (q.x + qc.x), 0.5f * (q.y - qc.y));
-                if (have1) T[(y0 + 1) * srow + k] = make_float2(0.5f * (q.y + qc.y), -0.5f * (q.x - qc.x));
+            float2 *z = fft_group<true>(x, y, Lx, a.rad_x, a.nrad_x, tw, lane, per);
+            float2 *zo = (z == x) ? y : x;
+            if (MODE == ROW_RATIO) {
+                const long long dbase = (static_cast<long long>(v) * a.P + p) * plane;
+                for (int i = lane; i < Lx; i += per) {
+                    float r0 = 0.f, r1 = 0.f;
+                    if (i < a.W) {
+                        const float2 b = z[i];
+                        if (have0) r0 = data_at(a.phi, a.u16, dbase + static_cast<long long>(y0) * a.W + i) / fmaxf(b.x, a.eps);
+                        if (have1) r1 = data_at(a.phi, a.u16, dbase + static_cast<long long>(y0 + 1) * a.W + i) / fmaxf(b.y, a.eps);
+                    }
+                    zo[i] = make_float2(r0, r1);
+                }
+                __syncthreads();
+                float2 *Z = fft_group<false>(zo, z, Lx, a.rad_x, a.nrad_x, tw, lane, per);
+                for (int k = lane; k < a.Lc; k += per) {
+                    const float2 q = Z[k], qc = Z[(Lx - k) % Lx];
+                    if (have0) T[y0 * srow + k] = make_float2(0.5f * (q.x + qc.x), 0.5f * (q.y - qc.y));
+                    if (have1) T[(y0 + 1) * srow + k] = make_float2(0.5f * (q.y + qc.y), -0.5f * (q.x - qc.x));
+                }
+                __syncthreads();
+            } else {   // ROW_UPDATE
+                float *pr = prod + 2 * g * a.W;
+                const bool first = v == a.view_lo;
+                for (int i = lane; i < a.W; i += per) {
+                    const float2 c = z[i];
+                    pr[i] = first ? c.x : pr[i] * c.x;
+                    pr[a.W + i] = first ? c.y : pr[a.W + i] * c.y;
+                }
+                __syncthreads();
             }
-            __syncthreads();
-        } else {   // ROW_UPDATE
-            float *pr = prod + 2 * g * a.W;
-            const bool first = v == a.view_lo;
-            for (int i = lane; i < a.W; i += per) {
-                const float2 c = z[i];
-                pr[i] = first ? c.x : pr[i] * c.x;
-                pr[a.W + i] = first ? c.y : pr[a.W + i] * c.y;
-            }
-            __syncthreads();
         }
-    }
-    if (MODE == ROW_UPDATE) {
-        const float *pr = prod + 2 * g * a.W;
-        const float m = a.psi_in ? 0.0f : __ldg(a.means + p);
-        for (int i = lane; i < a.W; i += per) {
-            if (have0) {
-                const long long o = p * plane + static_cast<long long>(y0) * a.W + i;
-                a.psi_out[o] = (a.psi_in ? a.psi_in[o] : m) * pr[i];
-            }
-            if (have1) {
-                const long long o = p * plane + static_cast<long long>(y0 + 1) * a.W + i;
-                a.psi_out[o] = (a.psi_in ? a.psi_in[o] : m) * pr[a.W + i];
+        if (MODE == ROW_UPDATE) {
+            const float *pr = prod + 2 * g * a.W;
+            const float m = a.psi_in ? 0.0f : __ldg(a.means + p);
+            for (int i = lane; i < a.W; i += per) {
+                if (have0) {
+                    const long long o = p * plane + static_cast<long long>(y0) * a.W + i;
+                    a.psi_out[o] = (a.psi_in ? a.psi_in[o] : m) * pr[i];
+                }
+                if (have1) {
+                    const long long o = p * plane + static_cast<long long>(y0 + 1) * a.W + i;
+                    a.psi_out[o] = (a.psi_in ? a.psi_in[o] : m) * pr[a.W + i];
+                }
             }
         }
     }
