@@ -33,6 +33,11 @@ namespace fftr {
 namespace {
 
 constexpr int kThreads = 256;
+// Element loops issue kBatch global loads into registers before the batch's
+// shared-memory stores, so that several loads are in flight per thread
+// (stores through generic pointers would otherwise order every load after
+// the previous store).
+constexpr int kBatch = 4;
 
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
     return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
@@ -173,13 +178,21 @@ __global__ void __launch_bounds__(kThreads) fft_rows_kernel(const FftArgs a, int
 
     if constexpr (MODE == ROW_PSI) {
         const float m = a.psi_in ? 0.0f : __ldg(a.means + p);
-        for (int i = lane; i < Lx; i += per) {
-            float r0 = 0.0f, r1 = 0.0f;
-            if (i < a.W) {
-                if (have0) r0 = a.psi_in ? __ldg(a.psi_in + p * plane + static_cast<long long>(y0) * a.W + i) : m;
-                if (have1) r1 = a.psi_in ? __ldg(a.psi_in + p * plane + static_cast<long long>(y0 + 1) * a.W + i) : m;
+        for (int i0 = lane; i0 < Lx; i0 += kBatch * per) {
+            float r0[kBatch], r1[kBatch];
+#pragma unroll
+            for (int u = 0; u < kBatch; ++u) {
+                const int i = i0 + u * per;
+                r0[u] = r1[u] = 0.0f;
+                if (i < a.W) {
+                    if (have0) r0[u] = a.psi_in ? __ldg(a.psi_in + p * plane + static_cast<long long>(y0) * a.W + i) : m;
+                    if (have1)
+                        r1[u] = a.psi_in ? __ldg(a.psi_in + p * plane + static_cast<long long>(y0 + 1) * a.W + i) : m;
+                }
             }
-            x[i] = make_float2(r0, r1);
+#pragma unroll
+            for (int u = 0; u < kBatch; ++u)
+                if (i0 + u * per < Lx) x[i0 + u * per] = make_float2(r0[u], r1[u]);
         }
         __syncthreads();
         float2 *Z = fft_group<false>(x, y, Lx, a.rad_x, a.nrad_x, tw, lane, per);
@@ -194,31 +207,57 @@ __global__ void __launch_bounds__(kThreads) fft_rows_kernel(const FftArgs a, int
         for (int v = a.view_lo; v < a.view_hi; ++v) {
             float2 *T = a.T + (static_cast<long long>(v) * a.P + p) * splane;
             // Hermitian rebuild of the two rows' full spectra into Z = A + iB
-            for (int k = lane; k < Lx; k += per) {
-                float2 A = make_float2(0.f, 0.f), B = make_float2(0.f, 0.f);
-                const bool lo = k < a.Lc;
-                const int kk = lo ? k : Lx - k;
-                if (have0) A = T[y0 * srow + kk];
-                if (have1) B = T[(y0 + 1) * srow + kk];
-                if (!lo) {
-                    A.y = -A.y;
-                    B.y = -B.y;
+            for (int k0 = lane; k0 < Lx; k0 += kBatch * per) {
+                float2 A[kBatch], B[kBatch];
+#pragma unroll
+                for (int u = 0; u < kBatch; ++u) {
+                    const int k = k0 + u * per;
+                    A[u] = B[u] = make_float2(0.f, 0.f);
+                    if (k < Lx) {
+                        const int kk = k < a.Lc ? k : Lx - k;
+                        if (have0) A[u] = T[y0 * srow + kk];
+                        if (have1) B[u] = T[(y0 + 1) * srow + kk];
+                    }
                 }
-                x[k] = make_float2(A.x - B.y, A.y + B.x);
+#pragma unroll
+                for (int u = 0; u < kBatch; ++u) {
+                    const int k = k0 + u * per;
+                    if (k >= Lx) continue;
+                    if (k >= a.Lc) {
+                        A[u].y = -A[u].y;
+                        B[u].y = -B[u].y;
+                    }
+                    x[k] = make_float2(A[u].x - B[u].y, A[u].y + B[u].x);
+                }
             }
             __syncthreads();
             float2 *z = fft_group<true>(x, y, Lx, a.rad_x, a.nrad_x, tw, lane, per);
             float2 *zo = (z == x) ? y : x;
             if (MODE == ROW_RATIO) {
                 const long long dbase = (static_cast<long long>(v) * a.P + p) * plane;
-                for (int i = lane; i < Lx; i += per) {
-                    float r0 = 0.f, r1 = 0.f;
-                    if (i < a.W) {
-                        const float2 b = z[i];
-                        if (have0) r0 = data_at(a.phi, a.u16, dbase + static_cast<long long>(y0) * a.W + i) / fmaxf(b.x, a.eps);
-                        if (have1) r1 = data_at(a.phi, a.u16, dbase + static_cast<long long>(y0 + 1) * a.W + i) / fmaxf(b.y, a.eps);
+                for (int i0 = lane; i0 < Lx; i0 += kBatch * per) {
+                    float d0[kBatch], d1[kBatch];
+#pragma unroll
+                    for (int u = 0; u < kBatch; ++u) {
+                        const int i = i0 + u * per;
+                        d0[u] = d1[u] = 0.f;
+                        if (i < a.W) {
+                            if (have0) d0[u] = data_at(a.phi, a.u16, dbase + static_cast<long long>(y0) * a.W + i);
+                            if (have1) d1[u] = data_at(a.phi, a.u16, dbase + static_cast<long long>(y0 + 1) * a.W + i);
+                        }
                     }
-                    zo[i] = make_float2(r0, r1);
+#pragma unroll
+                    for (int u = 0; u < kBatch; ++u) {
+                        const int i = i0 + u * per;
+                        if (i >= Lx) continue;
+                        float r0 = 0.f, r1 = 0.f;
+                        if (i < a.W) {
+                            const float2 b = z[i];
+                            if (have0) r0 = d0[u] / fmaxf(b.x, a.eps);
+                            if (have1) r1 = d1[u] / fmaxf(b.y, a.eps);
+                        }
+                        zo[i] = make_float2(r0, r1);
+                    }
                 }
                 __syncthreads();
                 float2 *Z = fft_group<false>(zo, z, Lx, a.rad_x, a.nrad_x, tw, lane, per);
@@ -242,14 +281,25 @@ __global__ void __launch_bounds__(kThreads) fft_rows_kernel(const FftArgs a, int
         if (MODE == ROW_UPDATE) {
             const float *pr = prod + 2 * g * a.W;
             const float m = a.psi_in ? 0.0f : __ldg(a.means + p);
-            for (int i = lane; i < a.W; i += per) {
-                if (have0) {
-                    const long long o = p * plane + static_cast<long long>(y0) * a.W + i;
-                    a.psi_out[o] = (a.psi_in ? a.psi_in[o] : m) * pr[i];
+            const long long o0 = p * plane + static_cast<long long>(y0) * a.W;
+            const long long o1 = o0 + a.W;
+            for (int i0 = lane; i0 < a.W; i0 += kBatch * per) {
+                float q0[kBatch], q1[kBatch];   // psi (may be psi_out itself: each element is read before written)
+#pragma unroll
+                for (int u = 0; u < kBatch; ++u) {
+                    const int i = i0 + u * per;
+                    q0[u] = q1[u] = m;
+                    if (i < a.W && a.psi_in) {
+                        if (have0) q0[u] = a.psi_in[o0 + i];
+                        if (have1) q1[u] = a.psi_in[o1 + i];
+                    }
                 }
-                if (have1) {
-                    const long long o = p * plane + static_cast<long long>(y0 + 1) * a.W + i;
-                    a.psi_out[o] = (a.psi_in ? a.psi_in[o] : m) * pr[a.W + i];
+#pragma unroll
+                for (int u = 0; u < kBatch; ++u) {
+                    const int i = i0 + u * per;
+                    if (i >= a.W) continue;
+                    if (have0) a.psi_out[o0 + i] = q0[u] * pr[i];
+                    if (have1) a.psi_out[o1 + i] = q1[u] * pr[a.W + i];
                 }
             }
         }
@@ -274,11 +324,19 @@ __global__ void __launch_bounds__(kThreads) fft_cols_kernel(const FftArgs a, int
     const long long hplane = static_cast<long long>(Ly) * srow;
 
     auto load = [&](const float2 *src, float2 *dst) {   // rows < H, zero beyond
-        for (int idx = threadIdx.x; idx < Ly * CB; idx += kThreads) {
-            const int r = idx / CB, c = idx - r * CB;
-            float2 v = make_float2(0.f, 0.f);
-            if (r < a.H && c0 + c < a.Lc) v = src[r * srow + c0 + c];
-            dst[c * LD + r] = v;
+        for (int idx0 = threadIdx.x; idx0 < Ly * CB; idx0 += kBatch * kThreads) {
+            float2 v[kBatch];
+#pragma unroll
+            for (int u = 0; u < kBatch; ++u) {
+                const int idx = idx0 + u * kThreads, r = idx / CB, c = idx - r * CB;
+                v[u] = make_float2(0.f, 0.f);
+                if (idx < Ly * CB && r < a.H && c0 + c < a.Lc) v[u] = src[r * srow + c0 + c];
+            }
+#pragma unroll
+            for (int u = 0; u < kBatch; ++u) {
+                const int idx = idx0 + u * kThreads, r = idx / CB, c = idx - r * CB;
+                if (idx < Ly * CB) dst[c * LD + r] = v[u];
+            }
         }
     };
     auto store = [&](const float2 *src, float2 *dst) {  // rows < H
@@ -298,11 +356,20 @@ __global__ void __launch_bounds__(kThreads) fft_cols_kernel(const FftArgs a, int
         const float2 *psi_base = Psi - cl * LD;
         for (int v = a.view_lo; v < a.view_hi; ++v) {
             const float2 *Hs = a.spec + static_cast<long long>(v) * hplane;
-            for (int idx = threadIdx.x; idx < Ly * CB; idx += kThreads) {
-                const int c = idx / Ly, r = idx - c * Ly;
-                float2 h = make_float2(0.f, 0.f);
-                if (c0 + c < a.Lc) h = __ldg(Hs + r * srow + c0 + c);
-                w0[c * LD + r] = cmul(psi_base[c * LD + r], h);
+            // columns fastest: each row's CB spectrum values are one coalesced run
+            for (int idx0 = threadIdx.x; idx0 < Ly * CB; idx0 += kBatch * kThreads) {
+                float2 h[kBatch];
+#pragma unroll
+                for (int u = 0; u < kBatch; ++u) {
+                    const int idx = idx0 + u * kThreads, r = idx / CB, c = idx - r * CB;
+                    h[u] = make_float2(0.f, 0.f);
+                    if (idx < Ly * CB && c0 + c < a.Lc) h[u] = __ldg(Hs + r * srow + c0 + c);
+                }
+#pragma unroll
+                for (int u = 0; u < kBatch; ++u) {
+                    const int idx = idx0 + u * kThreads, r = idx / CB, c = idx - r * CB;
+                    if (idx < Ly * CB) w0[c * LD + r] = cmul(psi_base[c * LD + r], h[u]);
+                }
             }
             __syncthreads();
             float2 *res = fft_group<true>(w0 + cl * LD, w1 + cl * LD, Ly, a.rad_y, a.nrad_y, tw, lane, per);
@@ -317,11 +384,19 @@ __global__ void __launch_bounds__(kThreads) fft_cols_kernel(const FftArgs a, int
             __syncthreads();
             float2 *F = fft_group<false>(b0 + cl * LD, b1 + cl * LD, Ly, a.rad_y, a.nrad_y, tw, lane, per);
             float2 *Fb = F - cl * LD;
-            for (int idx = threadIdx.x; idx < Ly * CB; idx += kThreads) {
-                const int c = idx / Ly, r = idx - c * Ly;
-                float2 h = make_float2(0.f, 0.f);
-                if (c0 + c < a.Lc) h = __ldg(Hs + r * srow + c0 + c);
-                Fb[c * LD + r] = cmulc(Fb[c * LD + r], h);
+            for (int idx0 = threadIdx.x; idx0 < Ly * CB; idx0 += kBatch * kThreads) {
+                float2 h[kBatch];
+#pragma unroll
+                for (int u = 0; u < kBatch; ++u) {
+                    const int idx = idx0 + u * kThreads, r = idx / CB, c = idx - r * CB;
+                    h[u] = make_float2(0.f, 0.f);
+                    if (idx < Ly * CB && c0 + c < a.Lc) h[u] = __ldg(Hs + r * srow + c0 + c);
+                }
+#pragma unroll
+                for (int u = 0; u < kBatch; ++u) {
+                    const int idx = idx0 + u * kThreads, r = idx / CB, c = idx - r * CB;
+                    if (idx < Ly * CB) Fb[c * LD + r] = cmulc(Fb[c * LD + r], h[u]);
+                }
             }
             __syncthreads();
             float2 *o = (Fb == b0) ? b1 : b0;
