@@ -179,8 +179,15 @@ mvd_status mvd_create(mvd_ctx **out, int views, const float *psfs_host, int psf_
 /* Release the context and every device buffer it owns.  NULL is accepted. */
 mvd_status mvd_destroy(mvd_ctx *ctx);
 
-/* Select the route (default MVD_ALGO_FUSED).  MVD_ERR_UNSUPPORTED if the
- * fused path cannot take this PSF size (it takes K <= 47). */
+/* Select the route (default MVD_ALGO_FUSED when the PSFs' separable terms
+ * fit its parameter block, else the Fourier route, else plain).
+ * MVD_ERR_UNSUPPORTED if the route cannot take this context:
+ *   MVD_ALGO_FUSED        K <= 47 and the separable terms fit;
+ *   MVD_ALGO_FFT          a padded grid of 2^a 3^b 5^c sides <= 2048 exists;
+ *   MVD_ALGO_TENSOR/TF32  odd K <= 47;
+ *   MVD_ALGO_PLAIN/DIRECT any K.
+ * Weights, axial profiles, mvd_run_host and mvd_psf_grad add their own
+ * restrictions (see there). */
 mvd_status mvd_set_algo(mvd_ctx *ctx, mvd_algo algo);
 
 /* Select how the views combine within one iteration (default simultaneous). */
