@@ -223,9 +223,10 @@ blur_ratio_kernel(const __grid_constant__ KParams kp) {
             if (!wait_tile(bar, phase, a, abort_flag)) return;
             phase ^= 1u;
         } else {
-            const float *psi = a.psi_in ? a.psi_in + p * plane_px : nullptr;
-            const float fill = a.psi_in ? 0.0f : __ldg(a.means + p);
-            load_tile_sw<K>(tile, psi, fill, y0, x0, a.H, a.W, a.circular);
+            if (a.psi_in)
+                load_tile_sw<K>(tile, a.psi_in + p * plane_px, 0.0f, y0, x0, a.H, a.W, a.circular);
+            else
+                fill_tile_const<K>(tile, __ldg(a.means + p), y0, x0, a.H, a.W, a.circular);
             __syncthreads();
         }
         const int t_next = t + gridDim.x;

@@ -109,6 +109,26 @@ __device__ __forceinline__ void load_tile_sw(float *__restrict__ tile, const flo
     }
 }
 
+// The first iteration's tile: psi is the plane's mean inside the plane
+// (and, for CIRCULAR, everywhere), zero outside for ZERO.  Same values as
+// load_tile_sw with a null source, written as whole 16-byte quads.
+template <int K, int TYF = 0>
+__device__ __forceinline__ void fill_tile_const(float *__restrict__ tile, float fill, int y0, int x0, int H, int W,
+                                                int circular) {
+    using G = Geo<K, TYF>;
+    static_assert(G::BOX_W % 4 == 0, "box rows are whole quads");
+    constexpr int QW = G::BOX_W / 4;
+    for (int q = threadIdx.x; q < G::BOX_H * QW; q += kThreads) {
+        const int r = q / QW, c = 4 * (q - r * QW);
+        const int gy = y0 - G::R + r, gx = x0 - G::R4 + c;
+        const bool row_in = circular || (gy >= 0 && gy < H);
+        float v[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) v[e] = (row_in && (circular || (gx + e >= 0 && gx + e < W))) ? fill : 0.0f;
+        *reinterpret_cast<float4 *>(tile + r * G::BOX_W + c) = make_float4(v[0], v[1], v[2], v[3]);
+    }
+}
+
 // One vertical item: NR consecutive output rows r0.. of column c, with the
 // KP central taps of the K-tap factor (KP = K: all of them).
 template <int K, int NR, int KP, int TYF>
