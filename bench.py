@@ -59,7 +59,7 @@ ALU_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 # scaled to the full workload (None until measured for the current kernels).
 # Taken on 128 of the 512 planes (--workload slab512) and scaled by 4; see
 # profiles/fused_kernels_volume512.md.
-NCU_TRAFFIC_PER_LAUNCH = {"blur_ratio": 1.9403e9, "correlate_update": 2.0278e9}
+NCU_TRAFFIC_PER_LAUNCH = {"blur_ratio": 1.9368e9, "correlate_update": 2.0153e9}
 
 
 def _peaks():
