@@ -12,7 +12,7 @@ with P_v^* the flipped PSF of view v (Supp. Note 2 section 1, symbol list).
 Every plane orthogonal to the rotation axis is processed independently with
 one 2D PSF per view.
 
-Readings of points the paper leaves open (each one is listed in the design doc):
+Readings of points the paper leaves open:
   * all views use the same psi^t (simultaneous product, as printed);
   * each view's ratio is correlated with its own flipped PSF before the
     product over views;
