@@ -50,7 +50,8 @@ WORKLOADS = {
                       label="2 views, 128^3 uint16 (quick check)"),
 }
 
-# Measured peaks on the GB300s (MEASURED_PEAKS.json): STREAM-style copy.
+# HBM copy bandwidth measured on GB300 (STREAM-style copy); MEASURED_PEAKS.json,
+# when present, overrides it.
 HBM_PEAK_GBS = 6767.4
 # FP32 CUDA-core peak from unit counts and the maximum SM clock:
 # 152 SMs x 128 FP32 lanes x 2 flop x 2.070 GHz.
