@@ -408,7 +408,10 @@ __global__ void __launch_bounds__(kThreads) fft_cols_kernel(const FftArgs a, int
 }
 
 int row_pairs_per_cta(int Lx) { return Lx <= 1024 ? 4 : 2; }
-int cols_per_cta(int Ly) { return Ly <= 1024 ? 8 : 4; }
+// Four columns per CTA: at Ly = 540 that is 56 KB of shared memory and four
+// resident CTAs per SM (eight columns: two), which hides the column loads
+// better (89.5 against 92.8 ms for 10 iterations on 512 planes of 512^2).
+int cols_per_cta(int) { return 4; }
 
 }  // namespace
 
