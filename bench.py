@@ -1,21 +1,21 @@
 #!/usr/bin/env python
 """Throughput of plane-wise multi-view Richardson-Lucy on GB300.
 
-One step = the whole hot path over one synthetic volume: reslice both view
-stacks into planes on the GPU, start every plane from its mean, run 10
-MV-RL iterations over all 512 planes.  Workload (one per GPU, weak scaling):
-2 views of 512^3 uint16 Gaussian-blob stacks (density 1e-4 per voxel,
-Poisson noise), 31x31 Gaussian PSFs sigma (1.5, 8) px, the second view
-turned by 90 degrees, zero boundary, eps 1e-6.
+One step = the whole hot path over one synthetic volume: reslice every view
+stack into planes on the GPU, start every plane from its mean, run 10 MV-RL
+iterations over all planes.  Default workload (one per GPU, weak scaling):
+4 views of 1024^3 uint16 Gaussian-blob stacks (density 5e-5 per voxel,
+Poisson noise) at 0/90/180/270 degrees, 41x41 Gaussian PSFs sigma (1.8, 10)
+px, views updating the estimate in sequence, zero boundary, eps 1e-6.
 
 Prints one JSON line (rank 0).  `value` counts voxel-view-iterations per
 second over all GPUs (planes x pixels x iterations x views / time); inputs
-are device-resident and larger than L2 (1 GiB of stacks and planes per
+are device-resident and larger than L2 (16 GiB of stacks and planes per
 step).  `e2e` is the same metric through mvd_run_host with pinned host
 buffers, copies included.  `--impl reference` times the FP64 CPU oracle on
 a sample of the same workload instead.
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference] [--workload NAME]
 """
 
 from __future__ import annotations
@@ -36,44 +36,82 @@ sys.path.insert(0, ROOT)
 METRIC = "voxel-iterations/s per view for MV-RL vs plain per-plane path; % HBM roofline"
 UNIT = "voxel-view-iterations/s"
 
+_VOL1024 = dict(Z=1024, Y=1024, X=1024, K=41, sigma_axial=10.0, sigma_lateral=1.8, angles=(0.0, 90.0, 180.0, 270.0),
+                density=5e-5, iters=10, seed=0, order="sequential")
+_VOL512 = dict(Z=512, Y=512, X=512, K=31, sigma_axial=8.0, sigma_lateral=1.5, angles=(0.0, 90.0), density=1e-4,
+               iters=10, seed=0, order="simultaneous")
 WORKLOADS = {
-    "volume512": dict(Z=512, Y=512, X=512, K=31, sigma_axial=8.0, sigma_lateral=1.5, angles=(0.0, 90.0),
-                      density=1e-4, iters=10, seed=0,
+    "volume1024x4": dict(_VOL1024,
+                         label="4 views, 1024^3 uint16 stacks resliced on the GPU to 1024 planes of 1024x1024, "
+                               "41x41 PSFs sigma (1.8, 10) px at 0/90/180/270 degrees, views in sequence, "
+                               "10 iterations"),
+    "slab1024x4": dict(_VOL1024, Y=64,
+                       label="4 views, 1024x64x1024 uint16 slab: 64 planes of 1024x1024 of the 4-view 1024^3 "
+                             "workload (profiling case)"),
+    "volume512": dict(_VOL512,
                       label="2 views, 512^3 uint16 stacks resliced on the GPU to 512 planes of 512x512, "
                             "31x31 PSFs sigma (1.5, 8) px turned by 90 degrees, 10 iterations"),
-    "slab512": dict(Z=512, Y=128, X=512, K=31, sigma_axial=8.0, sigma_lateral=1.5, angles=(0.0, 90.0),
-                    density=1e-4, iters=10, seed=0,
+    "slab512": dict(_VOL512, Y=128,
                     label="2 views, 512x128x512 uint16 slab: 128 planes of 512x512 (profiling case, "
                           "one quarter of the 512^3 volume)"),
-    "volume128": dict(Z=128, Y=128, X=128, K=31, sigma_axial=8.0, sigma_lateral=1.5, angles=(0.0, 90.0),
-                      density=1e-4, iters=10, seed=0,
-                      label="2 views, 128^3 uint16 (quick check)"),
+    "volume128": dict(_VOL512, Z=128, Y=128, X=128, label="2 views, 128^3 uint16 (quick check)"),
 }
+DEFAULT_WORKLOAD = "volume1024x4"
 
 # HBM copy bandwidth measured on GB300 (STREAM-style copy); MEASURED_PEAKS.json,
 # when present, overrides it.
 HBM_PEAK_GBS = 6767.4
-# FP32 CUDA-core peak from unit counts and the maximum SM clock:
-# 152 SMs x 128 FP32 lanes x 2 flop x 2.070 GHz.
-ALU_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
-# dram__bytes_read.sum + dram__bytes_write.sum per launch from one ncu capture,
-# scaled to the full workload (None until measured for the current kernels).
-# Taken on 128 of the 512 planes (--workload slab512) and scaled by 4; see
-# profiles/fused_kernels_volume512.md.
-NCU_TRAFFIC_PER_LAUNCH = {"blur_ratio": 1.9368e9, "correlate_update": 2.0153e9}
+# FP32 CUDA-core peak: SMs x 128 FP32 lanes x 2 flop x the maximum SM clock
+# (2070 MHz on GB300 unless MEASURED_PEAKS.json gives another).
+FP32_LANES_PER_SM = 128
+SM_MAX_MHZ = 2070.0
+# dram__bytes_read.sum + dram__bytes_write.sum per launch from one ncu capture
+# of the current kernels on the workload's profiling slab, scaled to a full
+# launch by the planes processed (traffic is proportional to the planes);
+# None where no capture of the current kernels exists.  The captures are
+# summarised under profiles/ (fused_kernels_volume1024x4.md,
+# fused_kernels_volume512.md).
+NCU_TRAFFIC_PER_LAUNCH = {
+    "volume1024x4": {"blur_ratio": None, "correlate_update": None},
+    "volume512": {"blur_ratio": None, "correlate_update": None},
+}
+
+
+def _measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except Exception:
+        return {}
 
 
 def _peaks():
-    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
-    hbm = HBM_PEAK_GBS
-    src = "fallback"
-    try:
-        with open(path) as f:
-            hbm = float(json.load(f)["hbm_gbs"])
-            src = "measured"
-    except Exception:
-        pass
-    return hbm, src
+    m = _measured_peaks()
+    if "hbm_gbs" in m:
+        return float(m["hbm_gbs"]), "measured"
+    return HBM_PEAK_GBS, "fallback"
+
+
+def alu_peak_tflops(sms: int):
+    """FP32 FMA peak from the device's SM count and the maximum SM clock."""
+    mhz = float(_measured_peaks().get("sm_max_mhz", SM_MAX_MHZ))
+    return sms * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12, \
+        f"derived: {sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 flop x {mhz:.0f} MHz"
+
+
+def kernel_budget(order: str, V: int, es: int, K: int):
+    """Algorithmic bytes and FLOP per pixel of one launch of the fused kernels.
+
+    A launch covers every pixel of every plane once, for the views it takes
+    part in: all V (simultaneous product) or one (views in sequence).  Per
+    pixel and view in that launch, kernel A reads the estimate once for all
+    its views (4 B), reads the data (es B) and writes the ratio (4 B); kernel
+    B reads the ratio (4 B) and reads and writes the estimate once (8 B).
+    FLOP: a rank-1 separable K x K PSF is two 1D passes of K taps, 2 FLOP per
+    tap, per view, in each kernel (8 V K per voxel-iteration in all)."""
+    vl = 1 if order == "sequential" else V
+    return {"blur_ratio": (4 + (es + 4) * vl, 4 * K * vl),
+            "correlate_update": (4 * vl + 8, 4 * K * vl)}
 
 
 # ----------------------------------------------------------------- clocks
@@ -149,10 +187,11 @@ def _oracle_plane(args):
     os.environ.setdefault("OMP_NUM_THREADS", "1")
     import numpy as np
     import oracle
-    phi, psfs, iters = args
+    phi, psfs, iters, order = args
     t0 = time.perf_counter()
-    oracle.rl_planes(phi[:, None].astype(np.float64), psfs, iters, boundary="zero", eps=1e-6, route="fft")
-    return time.perf_counter() - t0
+    psi = oracle.rl_planes(phi[:, None].astype(np.float64), psfs, iters, boundary="zero", eps=1e-6, route="fft",
+                           order=order)
+    return time.perf_counter() - t0, psi[0]
 
 
 def _warm_worker(_):
@@ -163,19 +202,46 @@ def _warm_worker(_):
     return os.getpid()
 
 
-def oracle_sample(pool, planes_np, psfs, iters):
-    """Oracle over the sampled planes [V][S][H][W], one plane per worker."""
+def oracle_sample(pool, planes_np, psfs, iters, order):
+    """Oracle over the sampled planes [V][S][H][W], one plane per worker.
+    Returns (wall seconds, results [S][H][W] FP64)."""
+    import numpy as np
     t0 = time.perf_counter()
-    pool.map(_oracle_plane, [(planes_np[:, s], psfs, iters) for s in range(planes_np.shape[1])])
-    return time.perf_counter() - t0
+    out = pool.map(_oracle_plane, [(planes_np[:, s], psfs, iters, order) for s in range(planes_np.shape[1])])
+    return time.perf_counter() - t0, np.stack([o[1] for o in out])
 
 
 def n_workers():
+    """Every host core this process may run on."""
     try:
         n = len(os.sched_getaffinity(0))
     except Exception:
         n = os.cpu_count() or 1
-    return max(1, min(n, 16))
+    return max(1, n)
+
+
+def sample_planes(stacks, idx):
+    """Planes y in idx of every view, [V][S][Z][X] numpy, cut from the
+    synthetic stacks [V][Z][Y][X] by torch slicing (plane y of view v is
+    stacks[v, :, y, :]); the library's reslice kernel is not involved."""
+    import numpy as np
+    import torch
+    return np.stack([stacks[:, :, int(y), :].to(torch.int32).cpu().numpy() for y in idx], axis=1)
+
+
+def error_vs_oracle(got, ref):
+    """rel-L2 and per-pixel errors of a route's sampled planes against the
+    FP64 oracle: ||g-o||/||o||; max |g-o| / max(|o|, tau), tau = 1e-3 max|o|;
+    and the unfloored per-pixel maximum."""
+    import numpy as np
+    g = np.asarray(got, dtype=np.float64)
+    o = np.asarray(ref, dtype=np.float64)
+    tau = 1e-3 * float(np.abs(o).max())
+    d = np.abs(g - o)
+    return {"rel_l2": float(np.linalg.norm(g - o) / np.linalg.norm(o)),
+            "per_pixel": float((d / np.maximum(np.abs(o), tau)).max()),
+            "per_pixel_unfloored": float((d / np.maximum(np.abs(o), 1e-300)).max()),
+            "planes": int(g.shape[0]), "finite": bool(np.all(np.isfinite(g)))}
 
 
 # ----------------------------------------------------------------- helpers
@@ -214,7 +280,21 @@ def make_inputs(wl, seed, device):
                                wl["angles"], wl["density"], seed=seed, device=device)
 
 
-def kernel_roofline(prof, name, units_per_launch, bytes_per_unit, flops_per_unit, hbm_peak):
+def workload_config(wl, world):
+    """The `config` object of both arms (the same keys and values)."""
+    V = len(wl["angles"])
+    stack_mib = V * wl["Z"] * wl["Y"] * wl["X"] * 2 / 2**20
+    return {"workload": wl["label"], "views": V, "volume": [wl["Z"], wl["Y"], wl["X"]], "psf": wl["K"],
+            "sigma_px": [wl["sigma_lateral"], wl["sigma_axial"]], "angles_deg": list(wl["angles"]),
+            "iters": wl["iters"], "order": wl["order"], "boundary": "zero", "planes_per_gpu": wl["Y"],
+            "data_dtype": "u16",
+            "l2": (f"inputs larger than L2: {stack_mib:.0f} MiB of stacks + {stack_mib:.0f} MiB of planes per step"
+                   if 2 * stack_mib > 129 else f"inputs smaller than L2 ({2 * stack_mib:.0f} MiB): a quick check, "
+                                               "not a bench line"),
+            "parallelism": f"{world} GPU(s), one independent volume per GPU, no collective"}
+
+
+def kernel_roofline(prof, name, units_per_launch, bytes_per_unit, flops_per_unit, hbm_peak, alu_peak):
     total_ms, n = prof.get(name, (0.0, 0))
     if not n:
         return None
@@ -222,9 +302,27 @@ def kernel_roofline(prof, name, units_per_launch, bytes_per_unit, flops_per_unit
     gbs = units_per_launch * bytes_per_unit / t / 1e9
     tfl = units_per_launch * flops_per_unit / t / 1e12
     return {"avg_ms": total_ms / n, "launches": n, "hbm_gbs": gbs, "hbm_frac": gbs / hbm_peak,
-            "tflops": tfl, "alu_frac": tfl / ALU_PEAK_TFLOPS,
+            "tflops": tfl, "alu_frac": tfl / alu_peak,
             "bytes_per_unit": bytes_per_unit, "flops_per_unit": flops_per_unit,
             "units_per_launch": units_per_launch}
+
+
+def timed_call(stream, fn, prof_ctx=None):
+    """Device time of fn() with CUDA events on the launching stream."""
+    import torch
+    from paper_1503_07998_gb300 import mvd
+    if prof_ctx is not None:
+        mvd.mvd_profile_enable(prof_ctx, True)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    fn()
+    b.record(stream)
+    torch.cuda.synchronize()
+    prof = None
+    if prof_ctx is not None:
+        prof = mvd.mvd_profile_read(prof_ctx)
+        mvd.mvd_profile_enable(prof_ctx, False)
+    return a.elapsed_time(b), prof
 
 
 # ----------------------------------------------------------------- arms
@@ -237,26 +335,26 @@ def run_reference(args, wl):
     S = n_workers()
     ctx = mp.get_context("spawn")
     pool = ctx.Pool(S)
+    pool.map(_warm_worker, range(S))
     dev = "cuda:0" if torch.cuda.is_available() else "cpu"
     stacks, psfs = make_inputs(wl, wl["seed"], dev)
     V = stacks.shape[0]
     idx = np.linspace(0, wl["Y"] - 1, S).round().astype(int)
-    # plane y of view v is stacks[v, :, y, :]; uint16 CUDA tensors have no
-    # advanced indexing, so planes are copied one by one
-    planes = np.stack([stacks[:, :, int(y), :].cpu().numpy() for y in idx], axis=1)
+    planes = sample_planes(stacks, idx)
     del stacks
     for _ in range(args.warmup):
-        oracle_sample(pool, planes, psfs, wl["iters"])
-    times = [oracle_sample(pool, planes, psfs, wl["iters"]) for _ in range(args.steps)]
+        oracle_sample(pool, planes, psfs, wl["iters"], wl["order"])
+    times = [oracle_sample(pool, planes, psfs, wl["iters"], wl["order"])[0] for _ in range(args.steps)]
     pool.close()
     t = sum(times) / len(times)
     units = S * wl["Z"] * wl["X"] * wl["iters"] * V
     value = units / t
-    sample = f"{S} planes of the workload (one per process), FP64 FFT route, {wl['iters']} iterations"
+    sample = (f"{S} of the {wl['Y']} planes (one per process, all {S} host cores), FP64 Fourier route, "
+              f"{wl['iters']} iterations, views {wl['order']}")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": wl["label"], "sample": sample},
+            "config": workload_config(wl, world),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": S, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
@@ -265,19 +363,30 @@ def run_reference(args, wl):
 
 def run_mvd(args, wl):
     import numpy as np
-    S = n_workers()
     import torch
+    S = n_workers()
     world, rank, local = dist_setup(args.gpus)
     from paper_1503_07998_gb300 import mvd
     dev = torch.device("cuda", torch.cuda.current_device())
     stream = torch.cuda.current_stream(dev)
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    alu_peak, alu_src = alu_peak_tflops(sms)
+    hbm_peak, hbm_src = _peaks()
     stacks, psfs = make_inputs(wl, wl["seed"] + rank, dev)
     V, Z, Y, X = stacks.shape
-    K, iters = wl["K"], wl["iters"]
+    K, iters, order = wl["K"], wl["iters"], wl["order"]
     ctx = mvd.mvd_create(V, psfs, K, Z, X, iters, "zero", 1e-6)
-    info = mvd.mvd_get_info(ctx)
+    mvd.mvd_set_update_order(ctx, order)
     planes = torch.empty((V, Y, Z, X), dtype=stacks.dtype, device=dev)
     est = torch.empty((Y, Z, X), dtype=torch.float32, device=dev)
+    # planes whose results are compared with the FP64 oracle (cut from the
+    # synthetic stacks, not from the library's reslice)
+    idx = np.linspace(0, Y - 1, S).round().astype(int) if rank == 0 else np.zeros(0, dtype=int)
+    sampled = {}
+
+    def keep(name):
+        if rank == 0 and not args.no_cpu:
+            sampled[name] = np.stack([est[int(y)].cpu().numpy() for y in idx])
 
     def step(marks=None):
         if marks:
@@ -323,32 +432,30 @@ def run_mvd(args, wl):
     ms_max = reduce_max(ms, world)
     units_per_step = Y * Z * X * iters * V
     value = units_per_step * world * args.steps / (ms_max / 1e3)
+    keep("fused")
 
-    # roofline of the dominant kernel
-    hbm_peak, hbm_src = _peaks()
-    vi_per_launch = Y * Z * X
-    # 2K flop per output of each 1D pass, two passes per SVD term
-    # 2 FLOP per tap of every 1D pass the fused kernels run (narrow factors
-    # run with their 17 central taps): one blur per distinct PSF, one
-    # correlation per view
-    flops_a = info.flops_blur
-    flops_b = info.flops_corr
+    # roofline of the dominant kernel, on the algorithmic counts
     es = 2 if stacks.dtype == torch.uint16 else 4
-    kr = {
-        "blur_ratio": kernel_roofline(prof, "blur_ratio", vi_per_launch, 4 + (es + 4) * V, flops_a, hbm_peak),
-        "correlate_update": kernel_roofline(prof, "correlate_update", vi_per_launch, 4 * V + 8, flops_b, hbm_peak),
-        "reslice": kernel_roofline(prof, "reslice", Y * Z * X * V, 2 * es, 0, hbm_peak),
-    }
+    px = Y * Z * X                                   # pixels of one launch
+    budget = kernel_budget(order, V, es, K)
+    kr = {n: kernel_roofline(prof, n, px, b, f, hbm_peak, alu_peak) for n, (b, f) in budget.items()}
+    kr["reslice"] = kernel_roofline(prof, "reslice", px * V, 2 * es, 0, hbm_peak, alu_peak)
+    kr["plane_means"] = kernel_roofline(prof, "plane_means", px * V, es, 0, hbm_peak, alu_peak)
     dom = max((k for k in kr if kr[k]), key=lambda k: kr[k]["avg_ms"] * kr[k]["launches"])
     d = kr[dom]
     if d["alu_frac"] >= d["hbm_frac"]:
-        roof = {"bound": "alu", "achieved": d["tflops"], "peak": ALU_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": d["alu_frac"], "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz"}
+        roof = {"bound": "alu", "achieved": d["tflops"], "peak": alu_peak, "unit": "TFLOP/s",
+                "frac": d["alu_frac"], "peak_source": alu_src}
     else:
         roof = {"bound": "hbm", "achieved": d["hbm_gbs"], "peak": hbm_peak, "unit": "GB/s",
                 "frac": d["hbm_frac"], "peak_source": hbm_src}
-    roof.update({"kernel": dom, "traffic": NCU_TRAFFIC_PER_LAUNCH.get(dom),
-                 "hbm_gbs": d["hbm_gbs"], "hbm_frac": d["hbm_frac"], "avg_launch_ms": d["avg_ms"]})
+    roof.update({"kernel": dom, "traffic": NCU_TRAFFIC_PER_LAUNCH.get(args.workload, {}).get(dom),
+                 "algorithmic_bytes_per_launch": px * d["bytes_per_unit"],
+                 "algorithmic_flops_per_launch": px * d["flops_per_unit"],
+                 "hbm_gbs": d["hbm_gbs"], "hbm_frac": d["hbm_frac"], "hbm_peak": hbm_peak,
+                 "tflops": d["tflops"], "alu_frac": d["alu_frac"], "alu_peak": alu_peak,
+                 "avg_launch_ms": d["avg_ms"], "launches": d["launches"],
+                 "share_of_timed_region": d["avg_ms"] * d["launches"] / ms})
 
     def leg(name):   # the comparison legs this run includes
         return not args.no_plain and (args.legs == "all" or name in args.legs.split(","))
@@ -362,18 +469,14 @@ def run_mvd(args, wl):
         p2 = planes[:, :sub].contiguous()
         mvd.mvd_deconvolve_planes(ctx, p2, e2)
         torch.cuda.synchronize()
-        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a0.record(stream)
-        mvd.mvd_deconvolve_planes(ctx, p2, e2)
-        a1.record(stream)
-        torch.cuda.synchronize()
-        pms = a0.elapsed_time(a1)
+        pms, _ = timed_call(stream, lambda: mvd.mvd_deconvolve_planes(ctx, p2, e2))
         mvd.mvd_set_algo(ctx, "fused")
         fused_ms = sum(v[0] for k, v in prof.items() if k in ("blur_ratio", "correlate_update", "plane_means"))
         fused_ms_per_plane = fused_ms / args.steps / Y
         plain_val = sub * Z * X * iters * V / (pms / 1e3)
         plain = {"value": plain_val, "unit": UNIT, "planes": sub,
                  "speedup_of_fused": (pms / sub) / fused_ms_per_plane}
+        del e2, p2
 
     # the Fourier route on the same planes (same context, one call = 10 iterations)
     fft_route = None
@@ -382,14 +485,13 @@ def run_mvd(args, wl):
             mvd.mvd_set_algo(ctx, "fft")
             mvd.mvd_deconvolve_planes(ctx, planes, est)
             torch.cuda.synchronize()
-            f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            f0.record(stream)
-            mvd.mvd_deconvolve_planes(ctx, planes, est)
-            f1.record(stream)
-            torch.cuda.synchronize()
-            fms = f0.elapsed_time(f1)
+            fms, fprof = timed_call(stream, lambda: mvd.mvd_deconvolve_planes(ctx, planes, est), ctx)
+            keep("fft")
             fft_route = {"value": units_per_step / (fms / 1e3), "unit": UNIT, "ms": fms,
-                         "note": "deconvolution only (no reslice), hand-written mixed-radix FFT route"}
+                         "note": "deconvolution only (no reslice), hand-written mixed-radix FFT route",
+                         "kernels": {k: {"total_ms": v[0], "launches": v[1]} for k, v in fprof.items()}}
+        except mvd.MvdError as e:
+            fft_route = {"unavailable": str(e)}
         finally:
             mvd.mvd_set_algo(ctx, "fused")
 
@@ -405,18 +507,10 @@ def run_mvd(args, wl):
             mvd.mvd_set_algo(ctx, algo)
             mvd.mvd_deconvolve_planes(ctx, planes, est)
             torch.cuda.synchronize()
-            mvd.mvd_profile_enable(ctx, True)
-            f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            f0.record(stream)
-            mvd.mvd_deconvolve_planes(ctx, planes, est)
-            f1.record(stream)
-            torch.cuda.synchronize()
-            tprof = mvd.mvd_profile_read(ctx)
-            mvd.mvd_profile_enable(ctx, False)
-            tms = f0.elapsed_time(f1)
-            tk = {n: kernel_roofline(tprof, n, vi_per_launch, b, f, hbm_peak)
-                  for n, b, f in ((prefix + "_blur_ratio", 4 + (es + 4) * V, flops_a),
-                                  (prefix + "_correlate_update", 4 * V + 8, flops_b))}
+            tms, tprof = timed_call(stream, lambda: mvd.mvd_deconvolve_planes(ctx, planes, est), ctx)
+            keep(algo)
+            tk = {prefix + "_" + n: kernel_roofline(tprof, prefix + "_" + n, px, b, f, hbm_peak, alu_peak)
+                  for n, (b, f) in budget.items()}
             tc_routes[algo] = {"value": units_per_step / (tms / 1e3), "unit": UNIT, "ms": tms,
                                "precision": precision, "note": "deconvolution only (no reslice)", "kernels": tk}
         except mvd.MvdError as e:
@@ -432,6 +526,7 @@ def run_mvd(args, wl):
     if leg("weighted"):
         R = ((X + K - 1 + 15) // 16 * 16 - X) // 2    # >= (K-1)/2, padded width a 16-multiple
         pctx = mvd.mvd_create(V, psfs, K, Z + 2 * R, X + 2 * R, iters, "zero", 1e-6)
+        mvd.mvd_set_update_order(pctx, order)
         try:
             def padded_run():
                 pd, pw = mvd.mvd_embed_padded(planes, R)
@@ -439,67 +534,53 @@ def run_mvd(args, wl):
                 pest = torch.empty((Y, Z + 2 * R, X + 2 * R), device=dev)
                 mvd.mvd_deconvolve_planes(pctx, pd, pest)
                 return mvd.mvd_crop_planes(pest, R), (pd, pw, pest)
-            out, keep = padded_run()
+            out, kept = padded_run()
             torch.cuda.synchronize()
-            del out, keep
-            mvd.mvd_profile_enable(pctx, True)
-            w0, w1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            w0.record(stream)
-            out, keep = padded_run()
-            w1.record(stream)
-            torch.cuda.synchronize()
-            wprof = mvd.mvd_profile_read(pctx)
-            wms = w0.elapsed_time(w1)
+            del out, kept
+            res = {}
+            wms, wprof = timed_call(stream, lambda: res.setdefault("r", padded_run()), pctx)
             weighted = {"value": units_per_step / (wms / 1e3), "unit": UNIT, "ms": wms,
                         "note": f"padded-domain estimate ({Z + 2 * R}x{X + 2 * R} planes, zero weights in a {R}-pixel "
                                 "border, one weight plane per view), embed + weight normalisers + iterations + crop; "
                                 "value counts the data voxels",
                         "kernels": {k: {"total_ms": v[0], "launches": v[1]} for k, v in wprof.items()}}
-            del out, keep
+            del res
         finally:
             pctx.close()
 
-    # 3D MV-RL (PSF a_v(y) P_v(z, x), axial sigma 1.5 px = the lateral width)
-    # on the same planes, and what the plane-wise approximation loses against
-    # it on 3D-blurred synthetic volumes with known truth
+    # 3D MV-RL (PSF a_v(y) P_v(z, x), axial sigma = the lateral width) on the
+    # same planes, and what the plane-wise approximation loses against it on
+    # 3D-blurred synthetic volumes with known truth
     vol3d = None
     if leg("vol3d") and rank == 0:
         from paper_1503_07998_gb300 import synth
-        ax = synth.gaussian_1d(11, 1.5).astype(np.float32)
+        ax = synth.gaussian_1d(11, wl["sigma_lateral"]).astype(np.float32)
         mvd.mvd_set_axial_psfs(ctx, np.stack([ax] * V))
         try:
             mvd.mvd_deconvolve_planes(ctx, planes, est)
             torch.cuda.synchronize()
-            mvd.mvd_profile_enable(ctx, True)
-            v0, v1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            v0.record(stream)
-            mvd.mvd_deconvolve_planes(ctx, planes, est)
-            v1.record(stream)
-            torch.cuda.synchronize()
-            vprof = mvd.mvd_profile_read(ctx)
-            mvd.mvd_profile_enable(ctx, False)
-            vms = v0.elapsed_time(v1)
+            vms, vprof = timed_call(stream, lambda: mvd.mvd_deconvolve_planes(ctx, planes, est), ctx)
         finally:
             mvd.mvd_set_axial_psfs(ctx, None)
         study = []
         for sy in (1.5, 3.0, 6.0):
             cs = synth.volume3d_case(48, 128, 128, 31, 8.0, 1.5, sy, n_blobs=200, seed=7)
-            sctx = mvd.mvd_create(V, cs["psfs"], 31, 128, 128, iters, "zero", 1e-6)
+            sctx = mvd.mvd_create(2, cs["psfs"], 31, 128, 128, iters, "zero", 1e-6)
             try:
-                d = torch.from_numpy(cs["phi"]).to(dev)
+                dd = torch.from_numpy(cs["phi"].astype(np.int32)).to(torch.uint16).to(dev)
                 e = torch.empty((48, 128, 128), device=dev)
                 errs = {}
                 for name, axial in (("planewise", None), ("3d", cs["axial"])):
                     mvd.mvd_set_axial_psfs(sctx, axial)
-                    mvd.mvd_deconvolve_planes(sctx, d, e)
+                    mvd.mvd_deconvolve_planes(sctx, dd, e)
                     torch.cuda.synchronize()
                     errs[name] = float(np.linalg.norm(e.cpu().numpy() - cs["truth"]) / np.linalg.norm(cs["truth"]))
                 study.append({"sigma_y": sy, "rel_l2_to_truth": errs})
             finally:
                 sctx.close()
         vol3d = {"value": units_per_step / (vms / 1e3), "unit": UNIT, "ms": vms,
-                 "note": "3D route on the same planes (axial Gaussian sigma 1.5, 11 taps): fused in-plane passes "
-                         "+ axial passes; deconvolution only",
+                 "note": f"3D route on the same planes (axial Gaussian sigma {wl['sigma_lateral']}, 11 taps): "
+                         "fused in-plane passes + axial passes; deconvolution only",
                  "kernels": {k: {"total_ms": v[0], "launches": v[1]} for k, v in vprof.items()},
                  "study": {"config": "2 views, 48 planes of 128x128, 200 blobs, K=31 sigma (1.5, 8), 10 iterations, "
                                      "data blurred in 3D with an axial Gaussian of sigma_y, Poisson noise",
@@ -511,7 +592,7 @@ def run_mvd(args, wl):
     grad = None
     if leg("grad") and rank == 0:
         from paper_1503_07998_gb300 import synth
-        gs, gp = synth.volume_stacks(256, 64, 256, 31, 7.0, 1.5, (0.0, 90.0), 2e-3, seed=5, device=dev)
+        gs, _ = synth.volume_stacks(256, 64, 256, 31, 7.0, 1.5, (0.0, 90.0), 2e-3, seed=5, device=dev)
         gplanes = torch.empty((2, 64, 256, 256), dtype=gs.dtype, device=dev)
         init = np.stack([synth.gaussian_psf(31, 5.0, 1.2, a) for a in (0.0, 90.0)])
         gctx = mvd.mvd_create(2, init, 31, 256, 256, 10, "zero", 1e-6)
@@ -531,8 +612,9 @@ def run_mvd(args, wl):
     # end to end through host buffers (pinned)
     e2e = None
     if not args.no_e2e:
-        host_in = stacks.cpu().pin_memory()
-        host_out = torch.empty((Y, Z, X), dtype=torch.float32).pin_memory()
+        host_in = torch.empty(stacks.shape, dtype=stacks.dtype, pin_memory=True)
+        host_in.copy_(stacks)
+        host_out = torch.empty((Y, Z, X), dtype=torch.float32, pin_memory=True)
         mvd.mvd_run_host(ctx, host_in, host_out)
         torch.cuda.synchronize()
         barrier(world)
@@ -545,36 +627,38 @@ def run_mvd(args, wl):
         e2e = {"value": units_per_step * world / te, "unit": UNIT,
                "h2d_bytes_per_step": int(host_in.numel() * host_in.element_size()),
                "d2h_bytes_per_step": int(host_out.numel() * host_out.element_size()),
-               "ms_per_step": te * 1e3}
+               "ms_per_step": te * 1e3, "steps_timed": ne}
+        del host_in, host_out
 
     cpu = None
+    errors = None
     if not args.no_cpu and world == 1 and rank == 0:
         # spawned workers (safe after CUDA initialisation), created only now:
         # a pool held through the timed regions slowed the host pipeline's
         # end-to-end time by a quarter
         pool = mp.get_context("spawn").Pool(S)
         pool.map(_warm_worker, range(S))
-        idx = np.linspace(0, Y - 1, S).round().astype(int)
-        sample_planes = np.stack([planes[:, int(y)].cpu().numpy() for y in idx], axis=1)
-        t = oracle_sample(pool, sample_planes, psfs, iters)
+        sp = sample_planes(stacks, idx)
+        t, ref = oracle_sample(pool, sp, psfs, iters, order)
         pool.close()
         cpu = {"value": S * Z * X * iters * V / t, "unit": UNIT, "cores": S, "kind": "oracle",
-               "sample": f"{S} of the {Y} planes (one per process), FP64 FFT route, {iters} iterations"}
+               "sample": f"{S} of the {Y} planes (one per process, all {S} host cores), FP64 Fourier route, "
+                         f"{iters} iterations, views {order}"}
+        errors = {name: error_vs_oracle(got, ref) for name, got in sampled.items()}
 
     ctx.close()
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-                "config": {"workload": wl["label"], "views": V, "volume": [Z, Y, X], "psf": K, "iters": iters,
-                           "planes_per_gpu": Y, "data_dtype": "u16",
-                           "l2": "inputs larger than L2: 512 MiB of stacks + 512 MiB of planes per step",
-                           "parallelism": f"{world} GPU(s), one independent volume per GPU, no collective"},
+                "config": workload_config(wl, world),
                 "voxel_iterations_per_s": value / V,
                 "timing": timing,
                 "roofline": roof, "kernels": kr, "cpu_baseline": cpu, "e2e": e2e,
-                "gpu_launches": int(launches), "clocks": clk, "plain_per_plane": plain,
-                "fft_route": fft_route, "tensor_route": tensor_route, "tf32_route": tf32_route, "weighted_padded": weighted, "vol3d": vol3d, "psf_grad": grad,
+                "error_vs_oracle": errors,
+                "gpu_launches": int(launches), "clocks": clk, "sms": sms, "plain_per_plane": plain,
+                "fft_route": fft_route, "tensor_route": tensor_route, "tf32_route": tf32_route,
+                "weighted_padded": weighted, "vol3d": vol3d, "psf_grad": grad,
                 "paper_context": "GTX TITAN Black, 2 views, 1024^3 padded, 10 it: 21.1 s = 1.02e9 voxel-view-it/s "
                                  "(Supp. Table 1); another machine, not the target"}
         print(json.dumps(line))
@@ -590,7 +674,7 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="mvd", choices=["mvd", "reference"])
-    ap.add_argument("--workload", default="volume512", choices=sorted(WORKLOADS) + ["batch64", "precision1024"])
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS) + ["batch64"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-plain", action="store_true", help="none of the comparison legs")
@@ -602,84 +686,10 @@ def main():
         args.warmup = 3
     if args.workload == "batch64":
         return run_batch(args)
-    if args.workload == "precision1024":
-        return run_precision(args)
     wl = WORKLOADS[args.workload]
     if args.impl == "reference":
         return run_reference(args, wl)
     return run_mvd(args, wl)
-
-
-def run_precision(args):
-    """The precision configuration: 4 views of 1024^3 uint16 blobs (density
-    5e-5) at 0/90/180/270 degrees, 41x41 PSFs sigma (1.8, 10) px, views in
-    sequence, 10 iterations over all 1024 planes, on the FP32 fused route and
-    on the BF16x3 and TF32 tensor-core routes; `value` is the FP32 route's
-    throughput, the tensor routes' differences to it are measured on the GPU
-    (their errors against the FP64 oracle are stated by the parity tests)."""
-    import torch
-    world, rank, _ = dist_setup(args.gpus)
-    from paper_1503_07998_gb300 import mvd, synth
-    dev = torch.device("cuda", torch.cuda.current_device())
-    stream = torch.cuda.current_stream(dev)
-    stacks, psfs = synth.volume_stacks(1024, 1024, 1024, 41, 10.0, 1.8, (0.0, 90.0, 180.0, 270.0), 5e-5, seed=0,
-                                       device=dev)
-    V, Z, Y, X = stacks.shape
-    iters = 10
-    ctx = mvd.mvd_create(V, psfs, 41, Z, X, iters, "zero", 1e-6)
-    mvd.mvd_set_update_order(ctx, "sequential")
-    planes = torch.empty((V, Y, Z, X), dtype=stacks.dtype, device=dev)
-    mvd.mvd_reslice(ctx, stacks, planes)
-    del stacks
-    units = Y * Z * X * iters * V
-    routes, ests = {}, {}
-    clocks = ClockSampler(torch.cuda.current_device())
-    clocks.start()
-    n0 = mvd.mvd_launch_count()
-    clk = None
-    for route in ("fused", "tensor", "tf32"):
-        mvd.mvd_set_algo(ctx, route)
-        est = torch.empty((Y, Z, X), device=dev)
-        for _ in range(args.warmup):
-            mvd.mvd_deconvolve_planes(ctx, planes, est)
-        torch.cuda.synchronize()
-        barrier(world)
-        first_row = clocks.mark()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for _ in range(args.steps):
-            mvd.mvd_deconvolve_planes(ctx, planes, est)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        last_row = max(clocks.mark(), first_row + 1)
-        ms = reduce_max(e0.elapsed_time(e1) / args.steps, world)
-        routes[route] = {"ms_per_step": ms, "value": units * world / (ms / 1e3), "unit": UNIT}
-        if route == "fused":
-            clk = (first_row, last_row)
-        ests[route] = est
-    clk = clocks.stop(*clk)
-    launches = mvd.mvd_launch_count() - n0
-    ref_norm = torch.linalg.vector_norm(ests["fused"])
-    diff = {r: float((torch.linalg.vector_norm(ests[r] - ests["fused"]) / ref_norm).item())
-            for r in ("tensor", "tf32")}
-    ctx.close()
-    if rank == 0:
-        line = {"metric": METRIC, "value": routes["fused"]["value"], "unit": UNIT, "n_gpus": world,
-                "steps": args.steps, "warmup": args.warmup, "ms_per_step": routes["fused"]["ms_per_step"],
-                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-                "data": "synthetic",
-                "config": {"workload": "4 views, 1024^3 uint16 stacks resliced on the GPU, 41x41 PSFs sigma (1.8, 10) "
-                                       "px at 0/90/180/270 degrees, views in sequence, 10 iterations",
-                           "l2": "inputs larger than L2",
-                           "parallelism": f"{world} GPU(s), one independent volume per GPU, no collective"},
-                "routes": routes,
-                "tensor_rel_l2_vs_fp32": diff["tensor"], "tf32_rel_l2_vs_fp32": diff["tf32"],
-                "clocks": clk, "gpu_launches": int(launches)}
-        print(json.dumps(line))
-    if world > 1:
-        import torch.distributed as dist
-        dist.destroy_process_group()
-    return 0
 
 
 def run_batch(args):

@@ -167,7 +167,12 @@ typedef struct {
 /* Create a context for `views` views with K x K PSFs psfs_host[V][K][K]
  * (FP32, host memory, copied), planes of plane_h x plane_w pixels, `iters`
  * RL iterations, the given boundary and division guard eps
- * (ratio = phi / max(blur, eps)).
+ * (ratio = phi / max(blur, eps)).  These are the quantities of the update
+ * equation of Supp. Note 1 (one 2D PSF per view, Results: the plane-wise
+ * approximation) and of the user's choice of the iteration count (Supp.
+ * Note 2 sec. 2); the context keeps the PSFs' separable factors and the
+ * device scratch the iterations need (the buffers of the memory table of
+ * Supp. Note 1 that the library owns).
  *
  * Errors (MVD_ERR_ARG): views < 1 or > 64, K even or < 1, plane sizes < 1,
  * iters < 0, eps <= 0 or not finite, a PSF entry negative or not finite, a
@@ -176,7 +181,9 @@ typedef struct {
 mvd_status mvd_create(mvd_ctx **out, int views, const float *psfs_host, int psf_size,
                       int plane_h, int plane_w, int iters, mvd_boundary boundary, float eps);
 
-/* Release the context and every device buffer it owns.  NULL is accepted. */
+/* Release the context and every device buffer it owns (the library-owned
+ * buffers of Supp. Note 1's memory table: ratio scratch, means, spectra);
+ * caller-owned buffers are untouched.  NULL is accepted. */
 mvd_status mvd_destroy(mvd_ctx *ctx);
 
 /* Select the route (default MVD_ALGO_FUSED when the PSFs' separable terms
@@ -335,7 +342,8 @@ mvd_status mvd_batch_destroy(mvd_batch *b);
  * kept every `checkpoint_every` iterations and each segment is recomputed
  * before it is swept.  Tile sums are FP32, their combination FP64.
  *   loss_host    receives L (may be NULL)
- *   grad_dev     [V][K][K] FP32, receives dL/dP
+ *   grad_dev     [V][K][K] FP32, receives dL/dP; NULL computes the loss
+ *                alone (forward iterations and data fit, no reverse sweep)
  *   estimate_dev [P][H][W] FP32 or NULL: receives psi_T
  * Uses the context's PSFs, boundary and eps with direct K x K stencils
  * (K <= 63).  MVD_ERR_UNSUPPORTED for the sequential update order and for a
@@ -405,11 +413,11 @@ mvd_status mvd_set_psfs(mvd_ctx *ctx, const float *psfs_host);
  * arguments of mvd_create and mvd_deconvolve_planes together, needs no
  * context, and runs the fused path (simultaneous order, default rank
  * tolerance) with all its scratch in one library-owned static device array
- * of 32 MiB (status word, factor taps, per-plane means and the V ratio planes
- * of every plane).  Every GPU that loads the library holds that array until
- * the process exits.
+ * of 32 MiB (status word, per-plane means and the V ratio planes of every
+ * plane; the factor taps travel in the kernels' parameter blocks).  Every
+ * GPU that loads the library holds that array until the process exits.
  *   - Limits: views <= 8, K odd and <= 47, and
- *     256 + V*K*4*K*4 + 4*n_planes + 4*V*n_planes*H*W bytes (each part rounded
+ *     256 + 4*n_planes + 4*V*n_planes*H*W bytes (the first two parts rounded
  *     up to 256) must fit in 32 MiB; larger calls fail with MVD_ERR_ARG and a
  *     message giving the bytes needed (split the planes over several calls).
  *   - The first call on a device looks up the array's device address with
@@ -417,15 +425,32 @@ mvd_status mvd_set_psfs(mvd_ctx *ctx, const float *psfs_host);
  *   - Every call shares the one array and reuses what the last call left
  *     there; calls whose work overlaps on the GPU (other streams, other host
  *     threads) race.  Serialise them.
- *   - Device-side wait timeouts are not reported by this call.
+ *   - The call clears the status word at the start of the array; a tile
+ *     wait that runs out sets it, and the call still returns MVD_OK (the
+ *     result is then incomplete).  mvd_static_device_status reads it.
  * data_dev, estimate_dev, init_mean and stream mean what they mean for
- * mvd_deconvolve_planes; the other arguments what they mean for mvd_create. */
+ * mvd_deconvolve_planes; the other arguments what they mean for mvd_create
+ * (MVD_ERR_ARG for a negative or non-finite PSF entry or a PSF with
+ * sum <= 0). */
 mvd_status mvd_deconvolve_planes_static(int views, const float *psfs_host, int psf_size,
                                         int plane_h, int plane_w, int iters,
                                         mvd_boundary boundary, float eps,
                                         const void *data_dev, mvd_dtype dt,
                                         float *estimate_dev, int n_planes, int init_mean,
                                         void *stream);
+
+/* Device-side status of the last mvd_deconvolve_planes_static call on the
+ * current device (no counterpart in the paper): waits for `stream`, then
+ * reads and clears the status word in the static array.  MVD_ERR_TIMEOUT if
+ * a tile wait of that call ran out (its estimate is incomplete), MVD_OK
+ * otherwise.  Allocates nothing. */
+mvd_status mvd_static_device_status(void *stream);
+
+/* Clock cycles a tile wait of mvd_deconvolve_planes_static may spin before
+ * it gives up and sets the status word (default 2e9, about one second;
+ * 0 restores it).  A negative value injects the fault, as for
+ * mvd_set_wait_budget.  Applies to every later static call in the process. */
+mvd_status mvd_static_set_wait_budget(long long cycles);
 
 /* Per-kernel device time of this context's launches, taken with CUDA events
  * recorded on the launching stream around every kernel.  Enabling (on != 0)
@@ -461,6 +486,10 @@ mvd_status mvd_psf_factors(const float *psfs_host, int views, int psf_size, doub
 mvd_status mvd_variant_kernels(const float *psfs_host, int views, int psf_size, mvd_variant variant,
                                float *x_out);
 
+/* Fixed English text of a status code (a static string; never NULL).  The
+ * paper's C workflow is called from a Java plugin through JNI (Supp. Note 2
+ * sec. 4); this library is such a C interface, and every entry point of it
+ * reports failures as an mvd_status that this turns into text. */
 const char *mvd_status_string(mvd_status s);
 
 /* Detail of the last error raised on the calling thread ("" if none). */
@@ -469,6 +498,14 @@ const char *mvd_last_error(void);
 /* Number of kernels this library has launched in this process (all
  * contexts, all threads); used to count launches inside a timed region. */
 uint64_t mvd_launch_count(void);
+
+/* Test hook for the out-of-memory paths (no counterpart in the paper): the
+ * next n device allocations the library makes, in any context, fail as if
+ * cudaMalloc had returned cudaErrorMemoryAllocation, so the calls that
+ * needed them return MVD_ERR_NOMEM.  A buffer that was to grow is released
+ * first, as on a real failure; the context stays usable and allocates again
+ * on a later call.  0 clears.  MVD_ERR_ARG for n < 0.  Needs no GPU. */
+mvd_status mvd_debug_fail_allocations(int n);
 
 #ifdef __cplusplus
 }

@@ -52,7 +52,7 @@ def _compile(src, verbose):
         return obj
     common = ["-O3", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC]
     if src.endswith(".cu"):
-        cmd = [nvcc, *ARCH, "-lineinfo", "--use_fast_math", *common, "-c", src, "-o", obj]
+        cmd = [nvcc, *ARCH, "-lineinfo", *common, "-c", src, "-o", obj]
         if verbose:
             cmd.insert(1, "-Xptxas=-v")
     else:

@@ -61,6 +61,17 @@ struct DeviceGuard {
     }
 };
 
+// Test hook (mvd_debug_fail_allocations): this many of the next device
+// allocations fail as if cudaMalloc had run out of memory.
+std::atomic<int> g_fail_allocs{0};
+
+bool take_injected_failure() {
+    int n = g_fail_allocs.load();
+    while (n > 0)
+        if (g_fail_allocs.compare_exchange_weak(n, n - 1)) return true;
+    return false;
+}
+
 // Device buffer that only grows.
 struct DevBuf {
     void *ptr = nullptr;
@@ -72,6 +83,7 @@ struct DevBuf {
             ptr = nullptr;
             bytes = 0;
         }
+        if (take_injected_failure()) return cudaErrorMemoryAllocation;
         cudaError_t e = cudaMalloc(&ptr, want);
         if (e == cudaSuccess) bytes = want;
         return e;
@@ -84,8 +96,6 @@ struct DevBuf {
     template <typename T>
     T *as() const { return static_cast<T *>(ptr); }
 };
-
-constexpr double kDefaultRankTol = 3e-7;
 
 // CUDA-event timing of every launch of a context (mvd_profile_*): an event is
 // recorded before each launch, labelled with the kernel that follows it, and
@@ -157,7 +167,7 @@ struct mvd_ctx {
     mvd_algo algo = MVD_ALGO_FUSED;
     mvd_update_order order = MVD_ORDER_SIMULTANEOUS;
     mvd_variant variant = MVD_VARIANT_INDEPENDENT;
-    double rank_tol = kDefaultRankTol;
+    double rank_tol = mvd::kDefaultRankTol;
     std::vector<float> psfs;
     std::vector<float> corr_psfs;        // a variant's flip(X_v), [V][K][K]; empty for plain MV-RL
     bool psf_dev_fresh = false;          // psf_dev holds the current psfs (+ corr_psfs)
@@ -614,8 +624,9 @@ mvd_status mvd_psf_grad(mvd_ctx *c, const void *data, mvd_dtype dt, int P, int c
                         float *grad_dev, float *est_dev, void *stream) {
     t_last_error.clear();
     if (!c) return fail(MVD_ERR_ARG, "ctx is NULL");
-    if (!data || !grad_dev) return fail(MVD_ERR_ARG, "NULL buffer");
+    if (!data) return fail(MVD_ERR_ARG, "NULL buffer");
     if (dt != MVD_U16 && dt != MVD_F32) return fail(MVD_ERR_ARG, "unknown dtype");
+    const bool want_grad = grad_dev != nullptr;   // NULL: the loss alone (no reverse sweep)
     if (P < 1 || P > 65535 || ckpt < 1) return fail(MVD_ERR_ARG, "need 1 <= n_planes <= 65535 and checkpoint_every >= 1");
     if (c->order != MVD_ORDER_SIMULTANEOUS) return fail(MVD_ERR_UNSUPPORTED, "the gradient follows the simultaneous order");
     if (c->variant != MVD_VARIANT_INDEPENDENT || c->weights || c->Ka > 0)
@@ -672,7 +683,7 @@ mvd_status mvd_psf_grad(mvd_ctx *c, const void *data, mvd_dtype dt, int P, int c
     // forward sweep, keeping psi at every checkpoint
     float *cur = psiA, *nxt = psiB;
     for (int t = 0; t < T; ++t) {
-        if (t % ckpt == 0) MVD_TRY(cudaMemcpyAsync(ck + (t / ckpt) * n, cur, n * sizeof(float), cudaMemcpyDeviceToDevice, s));
+        if (want_grad && t % ckpt == 0) MVD_TRY(cudaMemcpyAsync(ck + (t / ckpt) * n, cur, n * sizeof(float), cudaMemcpyDeviceToDevice, s));
         MVD_TRY(step(cur, nxt, fb, fr, fc));
         std::swap(cur, nxt);
     }
@@ -682,11 +693,12 @@ mvd_status mvd_psf_grad(mvd_ctx *c, const void *data, mvd_dtype dt, int P, int c
     for (int v = 0; v < V; ++v) {
         MVD_TRY(mvd::adj::stencil(cur, rb, P_v(v), K, H, W, P, circ, 0, 0, s));                 // y_v
         MVD_TRY(mvd::adj::terminal(phi_v(v), u16, rb, bb, loss, n, eps, s));                  // ybar in bb
+        if (!want_grad) continue;
         MVD_TRY(mvd::adj::stencil(bb, pbar, P_v(v), K, H, W, P, circ, 1, 1, s));              // psibar += P (*) ybar
         MVD_TRY(mvd::adj::lag_sum(bb, cur, G + static_cast<size_t>(v) * K * K, K, H, W, P, circ, -1, s));
     }
     // reverse sweep, segment by segment
-    for (int sg = nck - 1; sg >= 0; --sg) {
+    for (int sg = want_grad ? nck - 1 : -1; sg >= 0; --sg) {
         const int t0 = sg * ckpt, L = std::min(T, t0 + ckpt) - t0;
         MVD_TRY(cudaMemcpyAsync(sp, ck + sg * n, n * sizeof(float), cudaMemcpyDeviceToDevice, s));
         for (int u = 0; u < L; ++u) {
@@ -707,7 +719,7 @@ mvd_status mvd_psf_grad(mvd_ctx *c, const void *data, mvd_dtype dt, int P, int c
             std::swap(pbar, pbar2);
         }
     }
-    MVD_TRY(mvd::adj::to_float(G, grad_dev, V * K * K, s));
+    if (want_grad) MVD_TRY(mvd::adj::to_float(G, grad_dev, V * K * K, s));
     c->prof.end(s);
     double L_host = 0;
     MVD_TRY(cudaMemcpyAsync(&L_host, loss, sizeof(double), cudaMemcpyDeviceToHost, s));
@@ -777,6 +789,13 @@ mvd_status mvd_psf_factors(const float *psfs, int views, int K, double tol, int 
 }
 
 uint64_t mvd_launch_count(void) { return mvd::g_launches.load(std::memory_order_relaxed); }
+
+mvd_status mvd_debug_fail_allocations(int n) {
+    t_last_error.clear();
+    if (n < 0) return fail(MVD_ERR_ARG, "n must be >= 0");
+    g_fail_allocs.store(n);
+    return MVD_OK;
+}
 
 mvd_status mvd_create(mvd_ctx **out, int views, const float *psfs_host, int psf_size, int plane_h, int plane_w,
                       int iters, mvd_boundary boundary, float eps) {

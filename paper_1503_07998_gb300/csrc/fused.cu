@@ -147,7 +147,7 @@ __device__ __forceinline__ void row_epilogue(const FusedArgs &a, int vec_ok, con
         const float s[4] = {s4.x, s4.y, s4.z, s4.w};
         float o[4];
 #pragma unroll
-        for (int j = 0; j < 4; ++j) o[j] = MODE == 0 ? __fdividef(in[k][j], fmaxf(s[j], a.eps)) : in[k][j] * s[j];
+        for (int j = 0; j < 4; ++j) o[j] = MODE == 0 ? __fdiv_rn(in[k][j], fmaxf(s[j], a.eps)) : in[k][j] * s[j];
         float *dst = (MODE == 0 ? a.ratio : a.psi_out) + base + static_cast<long long>(y) * a.W + x;
         store4(dst, vec, n, o);
     }
@@ -331,7 +331,7 @@ blur_ratio_kernel(const __grid_constant__ KParams kp) {
 #pragma unroll
                         for (int e = 0; e < 4; ++e)
                             r[e] = a.store_blur ? acc[h][4 * q4 + e]
-                                                : __fdividef(ph[4 * q4 + e], fmaxf(acc[h][4 * q4 + e], a.eps));
+                                                : __fdiv_rn(ph[4 * q4 + e], fmaxf(acc[h][4 * q4 + e], a.eps));
                         store4(a.ratio + off + 4 * q4, kp.vec_ok && n == kNC, max(0, min(4, n - 4 * q4)), r);
                     }
                 }

@@ -14,6 +14,9 @@ constexpr int kMaxViews = 64;
 // rank tolerance (narrow Gaussians) run with this many taps on the fused path.
 constexpr int kShortTaps = 17;
 constexpr int kFusedMaxK = 47;   // largest PSF side with a fused-kernel instance
+// Relative Frobenius norm below which trailing SVD terms of a PSF are dropped
+// by default: below the FP32 rounding of the PSF's entries.
+constexpr double kDefaultRankTol = 3e-7;
 
 // Launch accounting (mvd_launch_count).
 void count_launch(int n = 1);

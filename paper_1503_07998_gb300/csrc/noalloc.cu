@@ -6,10 +6,11 @@
 // call cudaMalloc: an allocation can block on the whole device, its latency
 // is unbounded, and the host application may account for every byte itself.
 // This entry point therefore needs no context and allocates nothing.  The
-// fused kernels' scratch (the device status word, the factor taps, the
-// per-plane means and the ratio planes) lives in one file-scope device array
-// of kStaticScratchBytes that every GPU loading this library holds until the
-// process exits.
+// fused kernels' scratch (the device status word, the per-plane means and the
+// ratio planes) lives in one file-scope device array of kStaticScratchBytes
+// that every GPU loading this library holds until the process exits.  The
+// factor taps travel in the kernels' parameter blocks, so they need no
+// device copy.
 //
 // The array's name is only a host-side stand-in in host code, so its device
 // address is looked up with cudaGetSymbolAddress once per device (with that
@@ -17,6 +18,7 @@
 // what the kernels receive.
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -36,8 +38,29 @@ __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
 std::mutex g_mu;
 void *g_scratch_ptr[64] = {};                                  // per device, set once
 float g_taps_host[kStaticMaxViews * mvd::kFusedMaxK * 4 * mvd::kFusedMaxK];   // guarded by g_mu
+std::atomic<long long> g_wait_budget{mvd::kDefaultWaitBudget};
 
 inline size_t round_up(size_t n) { return (n + kAlign - 1) / kAlign * kAlign; }
+
+// Device address of the static array on the current device (looked up once
+// per device); nullptr with the last error set on failure.  Caller holds g_mu.
+unsigned char *scratch_base() {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+        mvd::set_last_error("cudaGetDevice failed");
+        return nullptr;
+    }
+    if (!g_scratch_ptr[dev]) {
+        void *p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+        if (e != cudaSuccess || !p) {
+            mvd::set_last_error("cudaGetSymbolAddress of the static scratch failed");
+            return nullptr;
+        }
+        g_scratch_ptr[dev] = p;
+    }
+    return static_cast<unsigned char *>(g_scratch_ptr[dev]);
+}
 
 }  // namespace
 
@@ -65,6 +88,11 @@ extern "C" mvd_status mvd_deconvolve_planes_static(int views, const float *psfs_
     const size_t KK = static_cast<size_t>(psf_size) * psf_size;
     for (size_t i = 0; i < KK * views; ++i)
         if (!std::isfinite(psfs_host[i]) || psfs_host[i] < 0.0f) return fail(MVD_ERR_ARG, "PSF entries must be finite and >= 0");
+    for (int v = 0; v < views; ++v) {
+        double sum = 0.0;
+        for (size_t i = 0; i < KK; ++i) sum += psfs_host[KK * v + i];
+        if (!(sum > 0.0)) return fail(MVD_ERR_ARG, "every PSF must have a positive sum");
+    }
     if (n_planes == 0) return MVD_OK;
     {
         const char *d0 = static_cast<const char *>(data_dev), *e0 = reinterpret_cast<const char *>(estimate_dev);
@@ -73,11 +101,9 @@ extern "C" mvd_status mvd_deconvolve_planes_static(int views, const float *psfs_
         if (d0 < e0 + ebytes && e0 < d0 + dbytes) return fail(MVD_ERR_ARG, "data and estimate overlap");
     }
 
-    // scratch layout: status word | taps | means | ratio planes
+    // scratch layout: status word | means | ratio planes
     const size_t plane_px = static_cast<size_t>(plane_h) * plane_w;
-    const size_t taps_bytes = static_cast<size_t>(views) * psf_size * 4 * psf_size * sizeof(float);
-    const size_t off_taps = kAlign;
-    const size_t off_means = off_taps + round_up(taps_bytes);
+    const size_t off_means = kAlign;
     const size_t off_ratio = off_means + round_up(static_cast<size_t>(n_planes) * sizeof(float));
     const size_t need = off_ratio + static_cast<size_t>(views) * n_planes * plane_px * sizeof(float);
     if (need > kStaticScratchBytes) {
@@ -89,29 +115,18 @@ extern "C" mvd_status mvd_deconvolve_planes_static(int views, const float *psfs_
     }
 
     std::lock_guard<std::mutex> lock(g_mu);
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess || dev < 0 || dev >= 64) return fail(MVD_ERR_CUDA, "cudaGetDevice failed");
-    if (!g_scratch_ptr[dev]) {
-        void *p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_static_scratch);
-        if (e != cudaSuccess || !p) return fail(MVD_ERR_CUDA, "cudaGetSymbolAddress of the static scratch failed");
-        g_scratch_ptr[dev] = p;
-    }
-    unsigned char *base = static_cast<unsigned char *>(g_scratch_ptr[dev]);
+    unsigned char *base = scratch_base();
+    if (!base) return MVD_ERR_CUDA;
 
     mvd::FactorTable ft;
     char msg[200] = {0};
-    if (!mvd::factorise_psfs(psfs_host, views, psf_size, 3e-7, ft, g_taps_host,
+    if (!mvd::factorise_psfs(psfs_host, views, psf_size, mvd::kDefaultRankTol, ft, g_taps_host,
                              static_cast<int>(sizeof g_taps_host / sizeof(float)), msg, sizeof msg))
         return fail(MVD_ERR_ARG, "PSF factorisation failed");
     if (!mvd::fused_taps_fit(ft)) return fail(MVD_ERR_ARG, "the PSFs need too many separable terms for this call");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    // pageable source: the call returns once g_taps_host has been staged
-    e = cudaMemcpyAsync(base + off_taps, g_taps_host, static_cast<size_t>(ft.total_terms) * 4 * psf_size * sizeof(float),
-                        cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(base, 0, kAlign, s);   // status word starts at zero
-    if (e != cudaSuccess) return fail(MVD_ERR_CUDA, "scratch set-up copy failed");
+    cudaError_t e = cudaMemsetAsync(base, 0, kAlign, s);   // status word starts at zero
+    if (e != cudaSuccess) return fail(MVD_ERR_CUDA, "scratch set-up failed");
 
     float *means = reinterpret_cast<float *>(base + off_means);
     if (init_mean) {
@@ -124,7 +139,7 @@ extern "C" mvd_status mvd_deconvolve_planes_static(int views, const float *psfs_
     a.phi = data_dev;
     a.phi_u16 = dt == MVD_U16;
     a.ratio = reinterpret_cast<float *>(base + off_ratio);
-    a.taps = reinterpret_cast<const float *>(base + off_taps);
+    a.taps = nullptr;   // the fused kernels take their taps from the parameter block
     a.taps_host = g_taps_host;
     a.ft = ft;
     a.H = plane_h;
@@ -135,7 +150,7 @@ extern "C" mvd_status mvd_deconvolve_planes_static(int views, const float *psfs_
     a.view_lo = 0;
     a.view_hi = views;
     a.err = reinterpret_cast<int *>(base);
-    a.wait_budget = mvd::kDefaultWaitBudget;
+    a.wait_budget = g_wait_budget.load();
     if (iters == 0 && init_mean) {
         for (int p = 0; p < n_planes; ++p) {
             e = mvd::plain_fill(estimate_dev + p * plane_px, means, p, plane_px, s);
@@ -149,5 +164,32 @@ extern "C" mvd_status mvd_deconvolve_planes_static(int views, const float *psfs_
         if ((e = mvd::launch_fused_correlate_update(a, s)) != cudaSuccess)
             return fail(MVD_ERR_CUDA, "correlate/update kernel failed");
     }
+    return MVD_OK;
+}
+
+extern "C" mvd_status mvd_static_device_status(void *stream) {
+    mvd::set_last_error("");
+    std::lock_guard<std::mutex> lock(g_mu);
+    unsigned char *base = scratch_base();
+    if (!base) return MVD_ERR_CUDA;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    int word = 0;
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (e == cudaSuccess) e = cudaMemcpy(&word, base, sizeof word, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemset(base, 0, sizeof word);
+    if (e != cudaSuccess) {
+        mvd::set_last_error(cudaGetErrorString(e));
+        return MVD_ERR_CUDA;
+    }
+    if (word & mvd::kDevTimeout) {
+        mvd::set_last_error("a tile wait of the static deconvolution timed out; its estimate is incomplete");
+        return MVD_ERR_TIMEOUT;
+    }
+    return MVD_OK;
+}
+
+extern "C" mvd_status mvd_static_set_wait_budget(long long cycles) {
+    mvd::set_last_error("");
+    g_wait_budget.store(cycles == 0 ? mvd::kDefaultWaitBudget : cycles);
     return MVD_OK;
 }

@@ -91,7 +91,7 @@ ratio_kernel(const void *__restrict__ phi, int u16, const float *__restrict__ w,
     if (i >= n) return;
     float d = u16 ? static_cast<float>(static_cast<const uint16_t *>(phi)[i]) : static_cast<const float *>(phi)[i];
     if (w) d *= w[i];
-    r[i] = __fdividef(d, fmaxf(blur[i], eps));
+    r[i] = __fdiv_rn(d, fmaxf(blur[i], eps));
 }
 
 // c = c / n_v where the footprint reaches a weighted pixel, else 1 (m < 0)

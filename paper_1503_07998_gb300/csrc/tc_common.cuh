@@ -135,7 +135,7 @@ __device__ __forceinline__ void store_ratio(const FusedArgs &a, int v, int p, in
     for (int j = 0; j < NE; ++j) {
         const int y = y0 + j;
         const float f = a.phi_u16 ? static_cast<float>(phi[j]) : __uint_as_float(phi[j]);
-        if (y < a.H) a.ratio[base + static_cast<long long>(y) * a.W] = __fdividef(f, fmaxf(d[j], a.eps));
+        if (y < a.H) a.ratio[base + static_cast<long long>(y) * a.W] = __fdiv_rn(f, fmaxf(d[j], a.eps));
     }
 }
 

@@ -70,7 +70,7 @@ axial_ratio_kernel(const float *__restrict__ blur, const void *__restrict__ phi,
         const long long o = static_cast<long long>(y0 + j) * plane + px;
         const float d = u16 ? static_cast<float>(static_cast<const uint16_t *>(phi)[o])
                             : static_cast<const float *>(phi)[o];
-        r[o] = __fdividef(d, fmaxf(sacc, eps));
+        r[o] = __fdiv_rn(d, fmaxf(sacc, eps));
     }
 }
 

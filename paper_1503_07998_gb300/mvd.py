@@ -85,6 +85,9 @@ def lib() -> ctypes.CDLL:
     L.mvd_batch_info.argtypes = [vp, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i)]
     L.mvd_batch_destroy.argtypes = [vp]
     L.mvd_deconvolve_planes_static.argtypes = [i, vp, i, i, i, i, i, f, vp, i, vp, i, i, vp]
+    L.mvd_static_device_status.argtypes = [vp]
+    L.mvd_static_set_wait_budget.argtypes = [ctypes.c_longlong]
+    L.mvd_debug_fail_allocations.argtypes = [i]
     L.mvd_set_wait_budget.argtypes = [vp, ctypes.c_longlong]
     L.mvd_get_info.argtypes = [vp, ctypes.POINTER(_Info)]
     L.mvd_reslice.argtypes = [vp, vp, i, i, i, i, i, vp, vp]
@@ -104,7 +107,8 @@ def lib() -> ctypes.CDLL:
     for name in ("mvd_create", "mvd_destroy", "mvd_set_algo", "mvd_set_rank_tolerance", "mvd_get_info",
                  "mvd_set_update_order", "mvd_set_variant", "mvd_variant_kernels", "mvd_device_status",
                  "mvd_set_weights", "mvd_embed_padded", "mvd_crop_planes", "mvd_set_axial_psfs", "mvd_set_wait_budget",
-                 "mvd_deconvolve_planes_static", "mvd_psf_grad", "mvd_set_psfs", "mvd_autotune",
+                 "mvd_deconvolve_planes_static", "mvd_static_device_status", "mvd_static_set_wait_budget",
+                 "mvd_debug_fail_allocations", "mvd_psf_grad", "mvd_set_psfs", "mvd_autotune",
                  "mvd_batch_create", "mvd_batch_tune", "mvd_batch_run", "mvd_batch_info", "mvd_batch_destroy",
                  "mvd_reslice", "mvd_deconvolve_planes", "mvd_run_host", "mvd_psf_factors",
                  "mvd_profile_enable", "mvd_profile_read"):
@@ -373,6 +377,23 @@ def mvd_deconvolve_planes_static(psfs, data, estimate, iters: int, boundary: str
            "mvd_deconvolve_planes_static")
 
 
+def mvd_static_device_status(stream=None) -> None:
+    """Raise MvdError (MVD_ERR_TIMEOUT) if a tile wait of the last
+    mvd_deconvolve_planes_static call ran out; waits for the stream."""
+    import torch
+    s = torch.cuda.current_stream().cuda_stream if stream is None else int(stream)
+    _check(lib().mvd_static_device_status(ctypes.c_void_p(s)), "mvd_static_device_status")
+
+
+def mvd_static_set_wait_budget(cycles: int) -> None:
+    _check(lib().mvd_static_set_wait_budget(int(cycles)), "mvd_static_set_wait_budget")
+
+
+def mvd_debug_fail_allocations(n: int) -> None:
+    """Test hook: the next n device allocations of the library fail."""
+    _check(lib().mvd_debug_fail_allocations(int(n)), "mvd_debug_fail_allocations")
+
+
 def mvd_run_host(ctx: Context, stacks_host, out_host, chunk_planes: int = 0, stream=None) -> None:
     """Host stacks [V][Z][Y][X] -> host result [Y][Z][X] float32 (torch CPU tensors,
     ideally pinned)."""
@@ -459,6 +480,26 @@ def mvd_psf_grad(ctx: Context, data, checkpoint_every: int = 2, estimate=None, s
     return loss.value, grad
 
 
+def mvd_poisson_loss(ctx: Context, data, estimate=None, stream=None) -> float:
+    """The Poisson data fit of mvd_psf_grad without its gradient (grad_dev
+    NULL: forward iterations and data fit only)."""
+    import torch
+    _require_cuda(data)
+    V, P, H, W = data.shape
+    if V != ctx.views or (H, W) != (ctx.H, ctx.W):
+        raise ValueError("data shape does not match the context")
+    est_ptr = None
+    if estimate is not None:
+        _require_cuda(estimate)
+        if tuple(estimate.shape) != (P, H, W) or estimate.dtype != torch.float32:
+            raise ValueError("estimate must be float32 [P][H][W]")
+        est_ptr = ctypes.c_void_p(estimate.data_ptr())
+    loss = ctypes.c_double(0.0)
+    _check(lib().mvd_psf_grad(ctx.handle, ctypes.c_void_p(data.data_ptr()), _dtype_code(data), P, 1,
+                              ctypes.byref(loss), None, est_ptr, _stream_of(data, stream)), "mvd_psf_grad")
+    return loss.value
+
+
 def _psf_loss_function():
     import torch
 
@@ -470,6 +511,11 @@ def _psf_loss_function():
         @staticmethod
         def forward(fctx, psfs, ctx, data, checkpoint_every):
             mvd_set_psfs(ctx, psfs.detach().to("cpu", torch.float32).numpy())
+            if not fctx.needs_input_grad[0]:
+                # loss only: the forward iterations and the data fit, no
+                # reverse sweep
+                loss = mvd_poisson_loss(ctx, data)
+                return torch.tensor(loss, dtype=torch.float64, device=psfs.device)
             loss, grad = mvd_psf_grad(ctx, data, checkpoint_every)
             fctx.save_for_backward(grad)
             return torch.tensor(loss, dtype=torch.float64, device=psfs.device)

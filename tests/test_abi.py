@@ -188,3 +188,27 @@ def test_host_chunks_rejects_bad_arguments():
     # three chunks do not fit two slots
     assert mvd.lib().mvd_host_chunks(30, 100, 10, y0.ctypes.data_as(ctypes.c_void_p),
                                      n.ctypes.data_as(ctypes.c_void_p), 2) == -1
+
+
+@pytest.mark.parametrize("bad", ["zero_sum", "negative", "nan"])
+def test_static_entry_point_rejects_bad_psfs_before_device_work(bad):
+    """mvd_deconvolve_planes_static checks its PSFs as mvd_create does, before
+    it touches the device: the buffer addresses passed here are never used."""
+    p = np.full((2, 5, 5), 0.04, dtype=np.float32)
+    if bad == "zero_sum":
+        p[1] = 0.0
+    elif bad == "negative":
+        p[0, 2, 2] = -1e-3
+    else:
+        p[1, 0, 4] = np.nan
+    fake_data, fake_est = ctypes.c_void_p(1 << 20), ctypes.c_void_p(1 << 30)
+    st = mvd.lib().mvd_deconvolve_planes_static(2, p.ctypes.data_as(ctypes.c_void_p), 5, 16, 16, 3, 0, 1e-6,
+                                                fake_data, mvd.DTYPE["f32"], fake_est, 1, 1, None)
+    assert st == mvd.MVD_ERR_ARG, (bad, st)
+    assert "PSF" in mvd.mvd_last_error()
+
+
+def test_allocation_failure_hook_arguments():
+    assert mvd.lib().mvd_debug_fail_allocations(-1) == mvd.MVD_ERR_ARG
+    assert mvd.lib().mvd_debug_fail_allocations(0) == mvd.MVD_OK
+    assert mvd.lib().mvd_static_set_wait_budget(0) == mvd.MVD_OK

@@ -44,3 +44,37 @@ def test_injected_wait_timeout_is_reported_and_context_recovers(mvd):
         assert_parity(est.cpu().numpy(), ref, what="after recovery")
     finally:
         ctx.close()
+
+
+def test_allocation_failure_returns_nomem_and_context_recovers(mvd):
+    """The test hook makes the next device allocation fail as an exhausted
+    cudaMalloc would: the call that needed it returns MVD_ERR_NOMEM, and the
+    same context allocates and deconvolves correctly on the next call."""
+    rng = np.random.default_rng(22)
+    V, P, H, W, K = 2, 3, 64, 96, 7
+    psfs = (rng.random((V, K, K)) + 0.1).astype(np.float32)
+    phi = rng.uniform(10, 100, size=(V, P, H, W)).astype(np.float32)
+    # a context whose creation needs memory
+    mvd.mvd_debug_fail_allocations(1)
+    try:
+        with pytest.raises(mvd.MvdError) as ei:
+            mvd.mvd_create(V, psfs, K, H, W, 3, "zero", 1e-6)
+        assert ei.value.status == mvd.MVD_ERR_NOMEM
+    finally:
+        mvd.mvd_debug_fail_allocations(0)
+    ctx = mvd.mvd_create(V, psfs, K, H, W, 3, "zero", 1e-6)
+    try:
+        d = torch.from_numpy(phi).cuda()
+        est = torch.empty((P, H, W), device="cuda")
+        mvd.mvd_debug_fail_allocations(1)      # the first call's workspace
+        with pytest.raises(mvd.MvdError) as ei:
+            mvd.mvd_deconvolve_planes(ctx, d, est)
+        assert ei.value.status == mvd.MVD_ERR_NOMEM
+        mvd.mvd_debug_fail_allocations(0)
+        mvd.mvd_deconvolve_planes(ctx, d, est)
+        torch.cuda.synchronize()
+        mvd.mvd_device_status(ctx)
+        assert_parity(est.cpu().numpy(), oracle.rl_planes(phi, psfs, 3), what="after allocation failure")
+    finally:
+        mvd.mvd_debug_fail_allocations(0)
+        ctx.close()

@@ -94,3 +94,53 @@ def test_autograd_function_backward(mvd):
         assert rel(p.grad.numpy(), 2.0 * ref_g) <= 1e-4
     finally:
         ctx.close()
+
+
+def test_gradient_at_the_calibration_workload_size(mvd):
+    """The calibration workload at full size, in the launch configuration the
+    benchmark times: 2 views, 64 planes of 256x256 blob data made with sigma
+    (1.5, 7) px PSFs, free 31x31 PSFs at sigma (1.2, 5), 10 iterations,
+    checkpoint every 2.  Loss and gradient are sums over planes, so the call
+    on all 64 planes must equal the sum of calls on four blocks of 16, and
+    single-plane calls on two sampled planes must match the FP64 oracle."""
+    stacks, _ = synth.volume_stacks(256, 64, 256, 31, 7.0, 1.5, (0.0, 90.0), 2e-3, seed=5, device="cpu")
+    planes = np.ascontiguousarray(stacks.to(torch.int32).numpy().transpose(0, 2, 1, 3))   # [V][Y][Z][X]
+    init = np.stack([synth.gaussian_psf(31, 5.0, 1.2, a) for a in (0, 90)])
+    ctx = mvd.mvd_create(2, init, 31, 256, 256, 10, "zero", 1e-6)
+    try:
+        d = torch.from_numpy(planes.astype(np.int32)).to(torch.uint16).cuda()
+        loss_all, g_all = mvd.mvd_psf_grad(ctx, d, 2)
+        g_all = g_all.cpu().numpy().astype(np.float64)
+        loss_sum, g_sum = 0.0, np.zeros_like(g_all)
+        for b in range(4):
+            lb, gb = mvd.mvd_psf_grad(ctx, d[:, 16 * b:16 * (b + 1)].contiguous(), 2)
+            loss_sum += lb
+            g_sum += gb.cpu().numpy()
+        assert abs(loss_all - loss_sum) <= 1e-9 * abs(loss_all)
+        assert rel(g_all, g_sum) <= 1e-5, rel(g_all, g_sum)
+        for y in (5, 40):
+            lp, gp = mvd.mvd_psf_grad(ctx, d[:, y:y + 1].contiguous(), 2)
+            ref_loss, ref_g, _ = oracle.rl_loss_and_psf_grad(planes[:, y:y + 1].astype(np.float64), init, 10, "zero")
+            assert abs(lp - ref_loss) <= 1e-6 * abs(ref_loss), (y, lp, ref_loss)
+            assert rel(gp.cpu().numpy().astype(np.float64), ref_g) <= 1e-4, (y, rel(gp.cpu().numpy(), ref_g))
+    finally:
+        ctx.close()
+
+
+def test_loss_without_gradient_matches_the_gradient_call(mvd):
+    """psf_fit_loss without requires_grad runs the forward iterations and the
+    data fit only (no reverse sweep) and gives the same loss."""
+    rng = np.random.default_rng(62)
+    V, P, H, W, K, T = 2, 2, 48, 40, 9, 4
+    psfs = (rng.random((V, K, K)) + 0.05).astype(np.float32)
+    phi = rng.uniform(5, 80, size=(V, P, H, W)).astype(np.float32)
+    ctx = mvd.mvd_create(V, psfs, K, H, W, T, "zero", 1e-6)
+    try:
+        d = torch.from_numpy(phi).cuda()
+        with_grad, _ = mvd.mvd_psf_grad(ctx, d, 2)
+        loss = mvd.psf_fit_loss(torch.tensor(psfs), ctx, d, 2)
+        assert not loss.requires_grad
+        assert abs(loss.item() - with_grad) <= 1e-12 * abs(with_grad)
+        assert abs(mvd.mvd_poisson_loss(ctx, d) - with_grad) <= 1e-12 * abs(with_grad)
+    finally:
+        ctx.close()

@@ -245,6 +245,38 @@ def test_psf_gradient_matches_central_differences(boundary):
     assert np.linalg.norm(grad - fd) <= 1e-6 * np.linalg.norm(fd)
 
 
+@pytest.mark.slow
+def test_psf_gradient_at_the_calibration_setting():
+    """The PSF-calibration setting itself: two views of blob data made with
+    sigma (1.5, 7) px, free 31x31 PSFs at sigma (1.2, 5), 10 unrolled
+    iterations, a 32x32 crop; the reverse-sweep gradient against FP64
+    central differences with h = 1e-4 on 48 seeded taps of both views.  The
+    finite differences carry an O(h^2) truncation error: halving h must cut
+    the gap to the gradient about four-fold, so what is left is truncation
+    and not a wrong term (a dropped or wrong term would leave a gap that does
+    not shrink with h)."""
+    case = synth.plane_case(seed=71, H=32, W=32, n_planes=1, n_blobs=6, K=31, sigma_axial=7.0,
+                            sigma_lateral=1.5, dtype=np.float64)
+    psfs = np.stack([synth.gaussian_psf(31, 5.0, 1.2, a) for a in (0, 90)]).astype(np.float64)
+    _, grad, _ = oracle.rl_loss_and_psf_grad(case.phi, psfs, 10, "zero")
+    taps = np.random.default_rng(5).choice(psfs.size, 48, replace=False)
+
+    def fd(h):
+        out = []
+        for k in taps:
+            v, i, j = np.unravel_index(k, psfs.shape)
+            p = psfs.copy(); p[v, i, j] += h
+            m = psfs.copy(); m[v, i, j] -= h
+            out.append((oracle.rl_loss(case.phi, p, 10, "zero") - oracle.rl_loss(case.phi, m, 10, "zero")) / (2 * h))
+        return np.array(out)
+
+    g = grad.reshape(-1)[taps]
+    gap1 = np.linalg.norm(fd(1e-4) - g) / np.linalg.norm(g)
+    gap2 = np.linalg.norm(fd(5e-5) - g) / np.linalg.norm(g)
+    assert gap1 <= 1e-5, (gap1, gap2)
+    assert 2.5 <= gap1 / gap2 <= 6.0, (gap1, gap2)
+
+
 def test_gradient_zero_iterations_is_data_fit_only():
     """T = 0: L = sum_v NLL(P_v * mean, phi_v) and its gradient has the
     closed form dL/dP_v[i,j] = sum_x (1 - phi/y)(x) * m * [x - d_ij in plane]."""
