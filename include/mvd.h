@@ -158,9 +158,10 @@ typedef struct {
     int flops_blur;             /* fused kernels, FLOP per voxel and launch:
                                    2 per tap of every 1D pass run, blur of
                                    every distinct PSF (narrow factors run
-                                   with their 17 central taps when the rest
-                                   is below the rank tolerance; full taps
-                                   with weights set)                        */
+                                   with their 17 central taps for K <= 31,
+                                   21 above, when the rest is below the
+                                   rank tolerance; full taps with weights
+                                   set)                                     */
     int flops_corr;             /* the same for the correlation of all views */
 } mvd_info;
 

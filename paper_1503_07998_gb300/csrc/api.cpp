@@ -1121,7 +1121,7 @@ mvd_status mvd_get_info(const mvd_ctx *c, mvd_info *info) {
     for (int v = 0; v < c->V && v < 16; ++v) info->rank[v] = c->ft.rank[v];
     for (int v = 0; v < c->V && v < 16; ++v) info->corr_rank[v] = c->ft.crank[v];
     auto taps = [&](int v, unsigned bit) {
-        return (!c->weights && (c->ft.short_mask[v] & bit)) ? mvd::kShortTaps : c->K;
+        return (!c->weights && (c->ft.short_mask[v] & bit)) ? mvd::short_tap_count(c->K) : c->K;
     };
     for (int g = 0; g < c->ft.n_groups; ++g) {
         const int lead = c->ft.group_leader[g];

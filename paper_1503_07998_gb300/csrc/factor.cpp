@@ -205,15 +205,16 @@ bool factorise_psfs(const float *psfs, int views, int K, double rank_tol, Factor
         off += r;
     }
     ft.total_terms = off;
-    // short factors: the mass outside the kShortTaps central taps is within the tolerance
-    if (K > kShortTaps && rank_tol > 0) {
-        const int OFF = (K - kShortTaps) / 2;
+    // short factors: the mass outside the short_tap_count(K) central taps is within the tolerance
+    const int KS = short_tap_count(K);
+    if (K > KS && rank_tol > 0) {
+        const int OFF = (K - KS) / 2;
         auto trimmable = [&](int term, int kind) {
             const float *t = taps_out + static_cast<size_t>(term) * 4 * K + static_cast<size_t>(kind) * K;
             double all = 0, tail = 0;
             for (int m = 0; m < K; ++m) {
                 all += std::fabs(t[m]);
-                if (m < OFF || m >= OFF + kShortTaps) tail += std::fabs(t[m]);
+                if (m < OFF || m >= OFF + KS) tail += std::fabs(t[m]);
             }
             return all > 0 && tail <= rank_tol * all;
         };

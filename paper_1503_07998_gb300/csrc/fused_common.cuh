@@ -35,7 +35,7 @@ namespace fused {
 
 constexpr int kThreads = 256;
 template <int K>
-__host__ __device__ constexpr int short_taps() { return K > kShortTaps ? kShortTaps : K; }
+__host__ __device__ constexpr int short_taps() { return short_tap_count(K); }
 constexpr int kNR = 16;      // rows per vertical item
 constexpr int kNC = 16;      // columns per horizontal item
 constexpr int kTX = 128;     // output tile width

@@ -10,9 +10,11 @@
 namespace mvd {
 
 constexpr int kMaxViews = 64;
-// 1D factors whose taps beyond +-8 of the centre carry no mass above the
-// rank tolerance (narrow Gaussians) run with this many taps on the fused path.
-constexpr int kShortTaps = 17;
+// 1D factors whose taps outside the short_tap_count(K) central ones carry no
+// mass above the rank tolerance (narrow Gaussians) run with that many taps on
+// the fused path: 17 (+-8) for K <= 31, 21 (+-10, Gaussians up to sigma of
+// about 2 px) for larger K.
+__host__ __device__ constexpr int short_tap_count(int K) { return K <= 17 ? K : (K <= 31 ? 17 : 21); }
 constexpr int kFusedMaxK = 47;   // largest PSF side with a fused-kernel instance
 // Relative Frobenius norm below which trailing SVD terms of a PSF are dropped
 // by default: below the FP32 rounding of the PSF's entries.
@@ -39,7 +41,7 @@ struct FactorTable {
     int crank[kMaxViews] = {};       // terms of the correlation step (= rank for plain MV-RL)
     // per view, the 1D factor kinds (bit k: blur vertical, blur horizontal,
     // correlation vertical, correlation horizontal) whose every term keeps
-    // all but a rank-tolerance share of its mass in the kShortTaps central taps
+    // all but a rank-tolerance share of its mass in the short_tap_count(K) central taps
     unsigned char short_mask[kMaxViews] = {};
     int ctap_off[kMaxViews] = {};    // their offset (= tap_off for plain MV-RL)
     int group[kMaxViews] = {};       // blur group (views with identical PSFs)

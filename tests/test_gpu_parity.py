@@ -281,6 +281,11 @@ def test_volume_1024_cubed_four_views_sampled_planes(mvd):
         assert mvd.mvd_get_info(ctx).algo == mvd.ALGO["fused"]
         planes = torch.empty((V, Y, Z, X), dtype=stacks.dtype, device=DEV)
         mvd.mvd_reslice(ctx, stacks, planes)
+        sample = [3, 700]
+        # the oracle's planes are cut from the synthetic stacks by torch
+        # slicing (plane y of view v is stacks[v, :, y, :]), not taken from
+        # the library's reslice
+        phi = np.stack([stacks[:, :, i, :].to(torch.int32).cpu().numpy() for i in sample], axis=1)
         del stacks
         est = torch.empty((Y, Z, X), dtype=torch.float32, device=DEV)
         mvd.mvd_deconvolve_planes(ctx, planes, est)
@@ -288,8 +293,6 @@ def test_volume_1024_cubed_four_views_sampled_planes(mvd):
         mvd.mvd_device_status(ctx)
     finally:
         ctx.close()
-    sample = [3, 700]
-    phi = np.stack([planes[:, i].cpu().numpy() for i in sample], axis=1)
     ref = oracle.rl_planes(phi, psfs, 10, eps=1e-6, route="fft", order="sequential")
     assert_parity(est[sample].cpu().numpy(), ref, what="1024^3 4 views sampled planes")
 
@@ -311,10 +314,35 @@ def test_volume_512_cubed_two_views_sampled_planes(mvd):
     finally:
         ctx.close()
     sample = [0, 255, 511]
-    # torch has no advanced indexing for uint16 CUDA tensors: copy plane by plane
-    phi = np.stack([planes[:, i].cpu().numpy() for i in sample], axis=1)
+    # oracle planes cut from the synthetic stacks (plane y of view v is
+    # stacks[v, :, y, :]), plane by plane (uint16 CUDA tensors have no
+    # advanced indexing)
+    phi = np.stack([stacks[:, :, i, :].to(torch.int32).cpu().numpy() for i in sample], axis=1)
     ref = oracle.rl_planes(phi, psfs, 10, eps=1e-6, route="fft")
     assert_parity(est[sample].cpu().numpy(), ref, what="512^3 sampled planes")
+
+
+def test_narrow_factors_of_large_psfs_run_with_21_central_taps(mvd):
+    """41x41 PSFs sigma (1.8, 10) at 0/90 degrees: the lateral factors keep
+    all but ~1e-7 of their mass in their 21 central taps (17 would leave
+    ~2e-6, above the rank tolerance), so the fused kernels run those passes
+    with 21 taps; the result matches the oracle."""
+    c = synth.plane_case(seed=62, H=160, W=272, n_planes=2, n_blobs=60, K=41, sigma_axial=10.0,
+                         sigma_lateral=1.8, angles=(0, 90, 180, 270), iters=5, dtype=np.uint16)
+    V, P, H, W = c.phi.shape
+    ctx = mvd.mvd_create(V, c.psfs, 41, H, W, 5, "zero", 1e-6)
+    try:
+        info = mvd.mvd_get_info(ctx)
+        assert info.flops_blur == 2 * 2 * (41 + 21) and info.flops_corr == 4 * 2 * (41 + 21)
+    finally:
+        ctx.close()
+    ref = oracle.rl_planes(c.phi, c.psfs, 5, eps=1e-6, route="fft", order="sequential")
+    assert_parity(run_gpu(mvd, c.phi, c.psfs, 5, order="sequential"), ref, what="21-tap factors, 4 views")
+    # two views with distinct PSFs: the simultaneous product (kernel B's
+    # rank-1 path over both views)
+    phi2, psfs2 = c.phi[:2], c.psfs[:2]
+    ref = oracle.rl_planes(phi2, psfs2, 5, eps=1e-6, route="fft")
+    assert_parity(run_gpu(mvd, phi2, psfs2, 5), ref, what="21-tap factors, 2 views")
 
 
 def test_narrow_factors_run_with_central_taps(mvd):
