@@ -180,6 +180,7 @@ struct mvd_ctx {
     std::vector<float> taps_host;
     mvd::FactorTable ft;
     DevBuf taps, psf_dev, means, ratio, plain;
+    DevBuf psi_split;                    // split copy of the estimate (warp-specialised tensor kernels)
     // end-to-end pipeline
     DevBuf run_stack[2], run_planes, run_est[2];
     cudaStream_t copy_in = nullptr, copy_out = nullptr;
@@ -290,8 +291,14 @@ cudaError_t prepare_workspace(mvd_ctx *c, int P) {
         e = c->fft.S0.ensure(rows * sizeof(float2));
         if (e == cudaSuccess) e = c->fft.T.ensure(rows * c->V * sizeof(float2));
     }
-    if (e == cudaSuccess && ((c->algo == MVD_ALGO_FUSED && mvd::fused_taps_fit(c->ft)) || tensor_algo(c->algo)))
-        e = c->ratio.ensure(static_cast<size_t>(c->V) * P * plane_px * sizeof(float));
+    if (e == cudaSuccess && ((c->algo == MVD_ALGO_FUSED && mvd::fused_taps_fit(c->ft)) || tensor_algo(c->algo))) {
+        size_t bytes = static_cast<size_t>(c->V) * P * plane_px * sizeof(float);
+        if (c->algo == MVD_ALGO_TENSOR) {   // split ratio and estimate of the warp-specialised kernels
+            bytes = std::max(bytes, mvd::tcw_split_bytes(c->W, c->H, static_cast<long long>(c->V) * P));
+            e = c->psi_split.ensure(mvd::tcw_split_bytes(c->W, c->H, P));
+        }
+        if (e == cudaSuccess) e = c->ratio.ensure(bytes);
+    }
     if (e == cudaSuccess) e = c->plain.ensure(4 * plane_px * sizeof(float));
     if (e == cudaSuccess) e = upload_psf_dev(c);
     return e;
@@ -300,7 +307,13 @@ cudaError_t prepare_workspace(mvd_ctx *c, int P) {
 mvd_status run_fused(mvd_ctx *c, const void *data, mvd_dtype dt, float *est, int P, int init_mean,
                      cudaStream_t s) {
     const size_t plane_px = static_cast<size_t>(c->H) * c->W;
-    cudaError_t e = c->ratio.ensure(static_cast<size_t>(c->V) * P * plane_px * sizeof(float));
+    // the tensor route's split ratio and estimate round each row up to 8 columns
+    const bool ws_route = c->algo == MVD_ALGO_TENSOR;
+    const size_t ratio_bytes =
+        std::max(static_cast<size_t>(c->V) * P * plane_px * sizeof(float),
+                 ws_route ? mvd::tcw_split_bytes(c->W, c->H, static_cast<long long>(c->V) * P) : size_t(0));
+    cudaError_t e = c->ratio.ensure(ratio_bytes);
+    if (e == cudaSuccess && ws_route) e = c->psi_split.ensure(mvd::tcw_split_bytes(c->W, c->H, P));
     if (e != cudaSuccess) return fail(MVD_ERR_NOMEM, "ratio workspace: %s", cudaGetErrorString(e));
     mvd::FusedArgs a = fused_args(c, data, dt, est, P);
     if (c->iters == 0 && init_mean) {
@@ -328,17 +341,52 @@ mvd_status run_fused(mvd_ctx *c, const void *data, mvd_dtype dt, float *est, int
         corr_name = "tf32_correlate_update";
     }
     bool first = init_mean != 0;
+    // The tensor route runs a launch on its warp-specialised kernels when they
+    // take it (tcw_eligible).  Between two such kernels the data travel split
+    // (BF16 hi/lo, what their products use): the blur writes the ratio split
+    // when the correlation that follows reads it, and the correlation writes a
+    // split copy of the estimate when the next blur reads one.
+    auto ws_eligible = [&](int lo, int which) {
+        mvd::FusedArgs b = a;
+        b.view_lo = lo;
+        b.view_hi = lo + step;
+        b.psi_in = est;
+        return ws_route && mvd::tcw_eligible(b, which);
+    };
+    bool psi_split_valid = false;   // the split estimate holds the current estimate
+    const int n_launch = c->iters * ((c->V + step - 1) / step);
+    int li = 0;
     for (int t = 0; t < c->iters; ++t) {
-        for (int v0 = 0; v0 < c->V; v0 += step) {
+        for (int v0 = 0; v0 < c->V; v0 += step, ++li) {
             a.view_lo = v0;
             a.view_hi = v0 + step;
             a.psi_in = first ? nullptr : est;
             first = false;
-            c->prof.mark(s, blur_name);
-            e = blur(a, s);
+            const bool wa = ws_route && mvd::tcw_eligible(a, 0), wb = ws_route && mvd::tcw_eligible(a, 1);
+            mvd::TcwIo io{};
+            io.psi_split = c->psi_split.as<uint16_t>();
+            c->prof.mark(s, wa ? "tcw_blur_ratio" : blur_name);
+            if (wa) {
+                io.in_mode = !a.psi_in ? mvd::kInConst : (psi_split_valid ? mvd::kInSplit : mvd::kInF32);
+                io.ratio_split = wb;
+                e = mvd::launch_tcw(a, 0, io, s);
+            } else {
+                e = blur(a, s);
+            }
             if (e != cudaSuccess) return cuda_fail(e, "blur/ratio kernel");
-            c->prof.mark(s, corr_name);
-            e = corr(a, s);
+            c->prof.mark(s, wb ? "tcw_correlate_update" : corr_name);
+            if (wb) {
+                // the next launch's blur reads the split estimate if it runs on the same kernels
+                const int nv0 = v0 + step < c->V ? v0 + step : 0;
+                io.in_mode = wa ? mvd::kInSplit : mvd::kInF32;
+                io.ratio_split = 0;
+                io.write_psi_split = li + 1 < n_launch && ws_eligible(nv0, 0);
+                e = mvd::launch_tcw(a, 1, io, s);
+                psi_split_valid = io.write_psi_split != 0;
+            } else {
+                e = corr(a, s);
+                psi_split_valid = false;
+            }
             if (e != cudaSuccess) return cuda_fail(e, "correlate/update kernel");
         }
     }
@@ -940,6 +988,7 @@ mvd_status mvd_destroy(mvd_ctx *c) {
     c->psf_dev.release();
     c->means.release();
     c->ratio.release();
+    c->psi_split.release();
     c->plain.release();
     for (auto &b : c->run_stack) b.release();
     for (auto &b : c->run_est) b.release();

@@ -128,6 +128,22 @@ bool tc_supported(int K);
 void tc_tile_shape(int K, int *tile_h, int *tile_w);
 cudaError_t launch_tc_blur_ratio(const FusedArgs &a, cudaStream_t s);
 cudaError_t launch_tc_correlate_update(const FusedArgs &a, cudaStream_t s);
+// Warp-specialised BF16x3 tensor-core kernels (tcw.cu) for launches whose
+// views share one rank-1 factorisation on the zero boundary; the tensor
+// route runs a launch on them whenever tcw_eligible says so.
+constexpr int kInConst = 0;   // input: the constant first estimate (the plane means)
+constexpr int kInF32 = 1;     // input: FP32 planes, split by the kernel
+constexpr int kInSplit = 2;   // input: planes written already split (hi, lo BF16, column-blocked)
+struct TcwIo {
+    int in_mode;              // kInConst / kInF32 / kInSplit (blur: the estimate; correlation: the ratio)
+    int ratio_split;          // blur: write the ratio split (for a split-input correlation), else FP32
+    uint16_t *psi_split;      // split copy of the estimate, [P][2][G][H][8] (G = W rounded up to 8, / 8)
+    int write_psi_split;      // correlation: also write the split estimate (for a split-input blur)
+};
+bool tcw_eligible(const FusedArgs &a, int which);   // which: 0 blur/ratio, 1 correlate/update
+// Bytes of `planes` split planes (hi and lo, columns rounded up to 8).
+size_t tcw_split_bytes(int W, int H, long long planes);
+cudaError_t launch_tcw(const FusedArgs &a, int which, const TcwIo &io, cudaStream_t s);
 // TF32 variant of the tensor-core kernels (same K range and tile rule).
 void tf32_tile_shape(int K, int *tile_h, int *tile_w);
 cudaError_t launch_tf32_blur_ratio(const FusedArgs &a, cudaStream_t s);

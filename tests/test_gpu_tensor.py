@@ -56,7 +56,10 @@ def run_tc(mvd, phi, psfs, iters, boundary="zero", eps=1e-6, order="simultaneous
         mvd.mvd_device_status(ctx)
         prof = mvd.mvd_profile_read(ctx)
         if iters > 0:
-            assert "tc_blur_ratio" in prof and "tc_correlate_update" in prof
+            # launches whose views share one rank-1 factorisation run on the
+            # warp-specialised kernels (tcw_*), the others on tc_*
+            assert any(k in prof for k in ("tc_blur_ratio", "tcw_blur_ratio"))
+            assert any(k in prof for k in ("tc_correlate_update", "tcw_correlate_update"))
         return est.cpu().numpy()
     finally:
         ctx.close()
