@@ -69,10 +69,10 @@ SM_MAX_MHZ = 2070.0
 # of the current kernels on the workload's profiling slab, scaled to a full
 # launch by the planes processed (traffic is proportional to the planes);
 # None where no capture of the current kernels exists.  The captures are
-# summarised under profiles/ (fused_kernels_volume1024x4.md,
-# fused_kernels_volume512.md).
+# summarised under profiles/ (fused_kernels_volume1024x4.md); the 512^3
+# workload's kernels have changed since its capture.
 NCU_TRAFFIC_PER_LAUNCH = {
-    "volume1024x4": {"blur_ratio": None, "correlate_update": None},
+    "volume1024x4": {"blur_ratio": 1.0070e10, "correlate_update": 1.2221e10},
     "volume512": {"blur_ratio": None, "correlate_update": None},
 }
 
