@@ -189,11 +189,11 @@ struct mvd_ctx {
     DevBuf grad_ws, grad_acc;            // PSF-gradient workspace (floats) and FP64 sums
     long long wait_budget = mvd::kDefaultWaitBudget;
     int max_ctas = 0;                    // persistent-grid cap set by a batch's tuner
-    // Fourier route: padded grid, radix lists, twiddles, PSF spectra, spectra scratch
+    // Fourier route: padded grid, transform plans, twiddles, PSF spectra, spectra scratch
     struct {
         bool planned = false;
         int Ly = 0, Lx = 0, Lc = 0, LcP = 0;
-        int rad_x[mvd::fftr::kMaxRadices], nrad_x = 0, rad_y[mvd::fftr::kMaxRadices], nrad_y = 0;
+        mvd::fftr::FftPlan1 px{}, py{};
         DevBuf tw_x, tw_y, spec, cspec, S0, T;
     } fft;
 };
@@ -409,23 +409,21 @@ bool fft_grid(const mvd_ctx *c, int *Ly, int *Lx) {
     return true;
 }
 
-// Twiddle tables and PSF spectra (host FP64 transforms) for the Fourier route.
+// Transform plans, twiddle tables and PSF spectra (host FP64 transforms) for
+// the Fourier route.
 mvd_status fft_plan(mvd_ctx *c) {
     if (c->fft.planned) return MVD_OK;
     auto &f = c->fft;
     if (!fft_grid(c, &f.Ly, &f.Lx)) return fail(MVD_ERR_UNSUPPORTED, "no Fourier grid for this plane size");
     f.Lc = f.Lx / 2 + 1;
     f.LcP = (f.Lc + 7) / 8 * 8;
-    mvd::fftr::radix_list(f.Lx, f.rad_x, &f.nrad_x);
-    mvd::fftr::radix_list(f.Ly, f.rad_y, &f.nrad_y);
     std::vector<float2> tx, ty, spec, all, call;
-    mvd::fftr::twiddles(f.Lx, tx);
-    mvd::fftr::twiddles(f.Ly, ty);
-    const size_t per = static_cast<size_t>(f.Ly) * f.LcP;
+    if (!mvd::fftr::make_plan(f.Lx, f.px, tx) || !mvd::fftr::make_plan(f.Ly, f.py, ty))
+        return fail(MVD_ERR_UNSUPPORTED, "no transform plan for %d x %d", f.Ly, f.Lx);
+    const size_t per = static_cast<size_t>(f.Lc) * f.Ly;
     all.resize(per * c->V);
     for (int v = 0; v < c->V; ++v) {
-        mvd::fftr::psf_spectrum(c->psfs.data() + static_cast<size_t>(v) * c->K * c->K, c->K, f.Ly, f.Lx, f.Lc, f.LcP,
-                                spec);
+        mvd::fftr::psf_spectrum(c->psfs.data() + static_cast<size_t>(v) * c->K * c->K, c->K, f.Ly, f.Lx, f.Lc, spec);
         std::copy(spec.begin(), spec.end(), all.begin() + v * per);
     }
     // a variant correlates with its own kernels: spectra of their flips
@@ -433,10 +431,13 @@ mvd_status fft_plan(mvd_ctx *c) {
         call.resize(per * c->V);
         for (int v = 0; v < c->V; ++v) {
             mvd::fftr::psf_spectrum(c->corr_psfs.data() + static_cast<size_t>(v) * c->K * c->K, c->K, f.Ly, f.Lx,
-                                    f.Lc, f.LcP, spec);
+                                    f.Lc, spec);
             std::copy(spec.begin(), spec.end(), call.begin() + v * per);
         }
     }
+    // a plan of one stage has no twiddles: keep one entry so that the buffers exist
+    if (tx.empty()) tx.push_back(make_float2(1.f, 0.f));
+    if (ty.empty()) ty.push_back(make_float2(1.f, 0.f));
     cudaError_t e;
     if ((e = f.tw_x.ensure(tx.size() * sizeof(float2))) != cudaSuccess ||
         (e = f.tw_y.ensure(ty.size() * sizeof(float2))) != cudaSuccess ||
@@ -475,10 +476,8 @@ mvd_status run_fft(mvd_ctx *c, const void *data, mvd_dtype dt, float *est, int P
     a.Lx = f.Lx;
     a.Lc = f.Lc;
     a.LcP = f.LcP;
-    std::copy(f.rad_x, f.rad_x + f.nrad_x, a.rad_x);
-    std::copy(f.rad_y, f.rad_y + f.nrad_y, a.rad_y);
-    a.nrad_x = f.nrad_x;
-    a.nrad_y = f.nrad_y;
+    a.px = f.px;
+    a.py = f.py;
     a.tw_x = f.tw_x.as<float2>();
     a.tw_y = f.tw_y.as<float2>();
     a.spec = f.spec.as<float2>();
@@ -493,6 +492,9 @@ mvd_status run_fft(mvd_ctx *c, const void *data, mvd_dtype dt, float *est, int P
     a.u16 = dt == MVD_U16;
     a.S0 = f.S0.as<float2>();
     a.T = f.T.as<float2>();
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const int step = c->order == MVD_ORDER_SEQUENTIAL ? 1 : c->V;
     bool first = init_mean != 0;
     for (int t = 0; t < c->iters; ++t) {
@@ -502,7 +504,7 @@ mvd_status run_fft(mvd_ctx *c, const void *data, mvd_dtype dt, float *est, int P
             a.psi_in = first ? nullptr : est;
             first = false;
             c->prof.mark(s, "fft_iteration");
-            if ((e = mvd::fftr::launch_iteration(a, s)) != cudaSuccess) return cuda_fail(e, "Fourier kernels");
+            if ((e = mvd::fftr::launch_iteration(a, sms, s)) != cudaSuccess) return cuda_fail(e, "Fourier kernels");
         }
     }
     c->prof.end(s);

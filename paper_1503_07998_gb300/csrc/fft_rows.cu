@@ -1,0 +1,256 @@
+// Row passes of the Fourier route (Supp. Note 2 sec. 4): F (estimate rows to
+// half spectra), R (inverse rows, ratio, forward rows) and U (inverse rows,
+// multiplicative update).  One warp transforms one pair of real rows packed
+// as one complex row (a + i b); the two half spectra are separated (and
+// rebuilt) through Hermitian symmetry.  Warps take (plane, row pair) items
+// in a grid-stride loop; the only CTA barrier is the one after the plan and
+// the twiddles are staged into shared memory.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdint>
+
+#include "fft_engine.cuh"
+#include "mvd_internal.h"
+
+namespace mvd {
+namespace fftr {
+
+namespace {
+
+constexpr int kWarps = 8;                // at most; fewer when the rows are long
+constexpr int kThreads = 32 * kWarps;
+constexpr size_t kSmemCap = 227 * 1024;
+// Element loops issue kBatch global loads into registers before the batch's
+// shared-memory stores, so that several loads are in flight per lane.
+constexpr int kBatch = 4;
+constexpr int kPlanBytes = 128;
+static_assert(sizeof(FftPlan1) <= kPlanBytes, "plan copy");
+
+enum RowMode { ROW_PSI = 0, ROW_RATIO = 1, ROW_UPDATE = 2 };
+
+__device__ __forceinline__ float data_at(const void *phi, int u16, long long i) {
+    return u16 ? static_cast<float>(__ldg(static_cast<const uint16_t *>(phi) + i))
+               : __ldg(static_cast<const float *>(phi) + i);
+}
+
+__host__ __device__ inline int buf_len(int Lx) { return (Lx + 1) & ~1; }
+
+// Rebuild the full spectrum of the packed row pair (y0, y0 + 1) from their
+// stored half spectra: Z_k = A_k + i B_k with A_{L-k} = conj(A_k).
+__device__ __forceinline__ void load_pair_spectrum(const FftArgs &a, const float2 *T, int y0, bool have1,
+                                                   float2 *x, int lane) {
+    const int Lx = a.Lx, Lc = a.Lc;
+    const long long srow = a.LcP;
+    const float2 *r0 = T + y0 * srow, *r1 = r0 + srow;
+    for (int k0 = lane; k0 < Lx; k0 += 32 * kBatch) {
+        float2 A[kBatch], B[kBatch];
+#pragma unroll
+        for (int u = 0; u < kBatch; ++u) {
+            const int k = k0 + 32 * u;
+            A[u] = B[u] = make_float2(0.f, 0.f);
+            if (k < Lx) {
+                const int kk = k < Lc ? k : Lx - k;
+                A[u] = r0[kk];
+                if (have1) B[u] = r1[kk];
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < kBatch; ++u) {
+            const int k = k0 + 32 * u;
+            if (k >= Lx) continue;
+            if (k >= Lc) {
+                A[u].y = -A[u].y;
+                B[u].y = -B[u].y;
+            }
+            x[k] = make_float2(A[u].x - B[u].y, A[u].y + B[u].x);
+        }
+    }
+}
+
+// Separate the packed transform Z of rows (y0, y0 + 1) into their half
+// spectra and store them: A_k = (Z_k + conj Z_{L-k}) / 2, B_k = (Z_k - conj Z_{L-k}) / (2i).
+__device__ __forceinline__ void store_pair_spectrum(const FftArgs &a, const float2 *Z, float2 *dst, int y0,
+                                                    bool have1, int lane) {
+    const int Lx = a.Lx;
+    const long long srow = a.LcP;
+    float2 *r0 = dst + y0 * srow, *r1 = r0 + srow;
+    for (int k = lane; k < a.Lc; k += 32) {
+        const float2 z = Z[k], zc = Z[k == 0 ? 0 : Lx - k];
+        r0[k] = make_float2(0.5f * (z.x + zc.x), 0.5f * (z.y - zc.y));
+        if (have1) r1[k] = make_float2(0.5f * (z.y + zc.y), -0.5f * (z.x - zc.x));
+    }
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(kThreads) fft_rows_kernel(const FftArgs a, int pairs, int use_prod) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    FftPlan1 *pl = reinterpret_cast<FftPlan1 *>(smem);
+    float2 *tw = reinterpret_cast<float2 *>(smem + kPlanBytes);
+    const int twl = (a.px.tw_len + 1) & ~1;
+    const int BL = buf_len(a.Lx);
+    const int nw = blockDim.x >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    float2 *x = tw + twl + static_cast<size_t>(warp) * 2 * BL;
+    float2 *y = x + BL;
+    float *prod = reinterpret_cast<float *>(tw + twl + static_cast<size_t>(nw) * 2 * BL) + warp * 2 * a.W;
+    if (threadIdx.x == 0) *pl = a.px;
+    for (int i = threadIdx.x; i < a.px.tw_len; i += blockDim.x) tw[i] = a.tw_x[i];
+    __syncthreads();
+
+    const int Lx = a.Lx, W = a.W;
+    const long long plane = static_cast<long long>(a.H) * W;
+    const long long splane = static_cast<long long>(a.H) * a.LcP;
+    const long long items = static_cast<long long>(a.P) * pairs;
+    for (long long it = static_cast<long long>(blockIdx.x) * nw + warp; it < items;
+         it += static_cast<long long>(gridDim.x) * nw) {
+        const int p = static_cast<int>(it / pairs);
+        const int y0 = 2 * static_cast<int>(it - static_cast<long long>(p) * pairs);
+        const bool have1 = y0 + 1 < a.H;
+        const long long o0 = p * plane + static_cast<long long>(y0) * W;
+        const long long o1 = o0 + W;
+        const float m = a.psi_in ? 0.0f : __ldg(a.means + p);
+
+        if constexpr (MODE == ROW_PSI) {
+            for (int i0 = lane; i0 < Lx; i0 += 32 * kBatch) {
+                float r0[kBatch], r1[kBatch];
+#pragma unroll
+                for (int u = 0; u < kBatch; ++u) {
+                    const int i = i0 + 32 * u;
+                    r0[u] = r1[u] = 0.0f;
+                    if (i < W) {
+                        r0[u] = a.psi_in ? __ldg(a.psi_in + o0 + i) : m;
+                        if (have1) r1[u] = a.psi_in ? __ldg(a.psi_in + o1 + i) : m;
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < kBatch; ++u)
+                    if (i0 + 32 * u < Lx) x[i0 + 32 * u] = make_float2(r0[u], r1[u]);
+            }
+            __syncwarp();
+            const float2 *Z = fft_warp<false>(x, y, *pl, tw, lane);
+            store_pair_spectrum(a, Z, a.S0 + p * splane, y0, have1, lane);
+        } else {
+            for (int v = a.view_lo; v < a.view_hi; ++v) {
+                float2 *T = a.T + (static_cast<long long>(v) * a.P + p) * splane;
+                load_pair_spectrum(a, T, y0, have1, x, lane);
+                __syncwarp();
+                float2 *z = fft_warp<true>(x, y, *pl, tw, lane);
+                float2 *zo = (z == x) ? y : x;
+                if constexpr (MODE == ROW_RATIO) {
+                    const long long d0 = (static_cast<long long>(v) * a.P + p) * plane + static_cast<long long>(y0) * W;
+                    for (int i0 = lane; i0 < Lx; i0 += 32 * kBatch) {
+                        float q0[kBatch], q1[kBatch];
+#pragma unroll
+                        for (int u = 0; u < kBatch; ++u) {
+                            const int i = i0 + 32 * u;
+                            q0[u] = q1[u] = 0.f;
+                            if (i < W) {
+                                q0[u] = data_at(a.phi, a.u16, d0 + i);
+                                if (have1) q1[u] = data_at(a.phi, a.u16, d0 + W + i);
+                            }
+                        }
+#pragma unroll
+                        for (int u = 0; u < kBatch; ++u) {
+                            const int i = i0 + 32 * u;
+                            if (i >= Lx) continue;
+                            float r0 = 0.f, r1 = 0.f;
+                            if (i < W) {
+                                const float2 b = z[i];
+                                r0 = __fdiv_rn(q0[u], fmaxf(b.x, a.eps));
+                                if (have1) r1 = __fdiv_rn(q1[u], fmaxf(b.y, a.eps));
+                            }
+                            zo[i] = make_float2(r0, r1);
+                        }
+                    }
+                    __syncwarp();
+                    const float2 *Z = fft_warp<false>(zo, z, *pl, tw, lane);
+                    store_pair_spectrum(a, Z, T, y0, have1, lane);
+                } else if (use_prod) {   // ROW_UPDATE, several views: product of their c_v
+                    const bool first = v == a.view_lo;
+                    for (int i = lane; i < W; i += 32) {
+                        const float2 c = z[i];
+                        prod[i] = first ? c.x : prod[i] * c.x;
+                        prod[W + i] = first ? c.y : prod[W + i] * c.y;
+                    }
+                } else {                 // ROW_UPDATE, one view: psi <- psi * c_v
+                    for (int i0 = lane; i0 < W; i0 += 32 * kBatch) {
+                        float q0[kBatch], q1[kBatch];   // psi (may be psi_out itself: read before written)
+#pragma unroll
+                        for (int u = 0; u < kBatch; ++u) {
+                            const int i = i0 + 32 * u;
+                            q0[u] = q1[u] = m;
+                            if (i < W && a.psi_in) {
+                                q0[u] = a.psi_in[o0 + i];
+                                if (have1) q1[u] = a.psi_in[o1 + i];
+                            }
+                        }
+#pragma unroll
+                        for (int u = 0; u < kBatch; ++u) {
+                            const int i = i0 + 32 * u;
+                            if (i >= W) continue;
+                            const float2 c = z[i];
+                            a.psi_out[o0 + i] = q0[u] * c.x;
+                            if (have1) a.psi_out[o1 + i] = q1[u] * c.y;
+                        }
+                    }
+                }
+                __syncwarp();
+            }
+            if (MODE == ROW_UPDATE && use_prod) {
+                for (int i0 = lane; i0 < W; i0 += 32 * kBatch) {
+                    float q0[kBatch], q1[kBatch];
+#pragma unroll
+                    for (int u = 0; u < kBatch; ++u) {
+                        const int i = i0 + 32 * u;
+                        q0[u] = q1[u] = m;
+                        if (i < W && a.psi_in) {
+                            q0[u] = a.psi_in[o0 + i];
+                            if (have1) q1[u] = a.psi_in[o1 + i];
+                        }
+                    }
+#pragma unroll
+                    for (int u = 0; u < kBatch; ++u) {
+                        const int i = i0 + 32 * u;
+                        if (i >= W) continue;
+                        a.psi_out[o0 + i] = q0[u] * prod[i];
+                        if (have1) a.psi_out[o1 + i] = q1[u] * prod[W + i];
+                    }
+                }
+            }
+        }
+        __syncwarp();
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_rows(int mode, const FftArgs &a, int sms, cudaStream_t s) {
+    const int pairs = (a.H + 1) / 2;
+    const int use_prod = mode == ROW_UPDATE && a.view_hi - a.view_lo > 1;
+    const size_t fixed = kPlanBytes + static_cast<size_t>((a.px.tw_len + 1) & ~1) * sizeof(float2);
+    const size_t per_warp = 2ull * buf_len(a.Lx) * sizeof(float2) + (use_prod ? 2ull * a.W * sizeof(float) : 0);
+    const int nw = static_cast<int>(std::min<size_t>(kWarps, (kSmemCap - fixed) / per_warp));
+    if (nw < 1) return cudaErrorInvalidValue;
+    const size_t smem = fixed + nw * per_warp;
+    const void *fn = mode == ROW_PSI     ? reinterpret_cast<const void *>(fft_rows_kernel<ROW_PSI>)
+                     : mode == ROW_RATIO ? reinterpret_cast<const void *>(fft_rows_kernel<ROW_RATIO>)
+                                         : reinterpret_cast<const void *>(fft_rows_kernel<ROW_UPDATE>);
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, 32 * nw, smem)) != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    const long long items = static_cast<long long>(a.P) * pairs;
+    const long long need = (items + nw - 1) / nw;
+    const int grid = static_cast<int>(std::min<long long>(need, static_cast<long long>(per_sm) * std::max(sms, 1)));
+    if (grid < 1) return cudaSuccess;
+    switch (mode) {
+        case ROW_PSI: fft_rows_kernel<ROW_PSI><<<grid, 32 * nw, smem, s>>>(a, pairs, use_prod); break;
+        case ROW_RATIO: fft_rows_kernel<ROW_RATIO><<<grid, 32 * nw, smem, s>>>(a, pairs, use_prod); break;
+        default: fft_rows_kernel<ROW_UPDATE><<<grid, 32 * nw, smem, s>>>(a, pairs, use_prod); break;
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace fftr
+}  // namespace mvd

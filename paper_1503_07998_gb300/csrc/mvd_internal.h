@@ -149,15 +149,28 @@ void tf32_tile_shape(int K, int *tile_h, int *tile_w);
 cudaError_t launch_tf32_blur_ratio(const FusedArgs &a, cudaStream_t s);
 cudaError_t launch_tf32_correlate_update(const FusedArgs &a, cudaStream_t s);
 
-// Fourier route (fft.cu).
+// Fourier route (fft.cu, fft_rows.cu, fft_cols.cu).
 namespace fftr {
 constexpr int kMaxRadices = 16;
 constexpr int kMaxLen = 2048;          // largest padded side
+constexpr int kMaxStages = 5;
+// One Stockham stage of a warp transform: radix R after stages whose radices
+// multiply to p; M = N / R butterflies; its twiddles start at tw_off of the
+// axis's table ((R - 1) p entries exp(+2 pi i q k / (p R)), q >= 1, k < p),
+// none when p == 1; rp = 1 / p.
+struct FftStage {
+    int R, p, M, tw_off;
+    float rp;
+};
+struct FftPlan1 {
+    int N, nst, tw_len;                // length, stages, twiddle entries of all stages
+    FftStage st[kMaxStages];
+};
 struct FftArgs {
     int Ly, Lx, Lc, LcP;               // padded grid, half-spectrum columns and their pitch
-    int rad_x[kMaxRadices], nrad_x, rad_y[kMaxRadices], nrad_y;
-    const float2 *tw_x, *tw_y;         // exp(+2 pi i k / L) tables
-    const float2 *spec;                // [V][Ly][LcP] PSF spectra / (Ly Lx)
+    FftPlan1 px, py;                   // row (length Lx) and column (length Ly) transforms
+    const float2 *tw_x, *tw_y;         // their stage twiddle tables
+    const float2 *spec;                // [V][Lc][Ly] PSF spectra / (Ly Lx), column by column
     const float2 *cspec;               // spectra the correlation uses (= spec for plain MV-RL)
     int H, W, P, view_lo, view_hi;
     float eps;
@@ -171,9 +184,13 @@ struct FftArgs {
 };
 bool smooth_size(int n, int *out);
 bool radix_list(int n, int *rad, int *nrad);
-void twiddles(int N, std::vector<float2> &out);
-void psf_spectrum(const float *psf, int K, int Ly, int Lx, int Lc, int LcP, std::vector<float2> &out);
-cudaError_t launch_iteration(const FftArgs &a, cudaStream_t s);
+// Stages of a warp transform of length N (2 <= N <= kMaxLen, factors 2, 3, 5)
+// and their twiddle table; false if N has another factor.
+bool make_plan(int N, FftPlan1 &plan, std::vector<float2> &tw);
+void psf_spectrum(const float *psf, int K, int Ly, int Lx, int Lc, std::vector<float2> &out);
+cudaError_t launch_rows(int mode, const FftArgs &a, int sms, cudaStream_t s);   // 0 estimate, 1 ratio, 2 update
+cudaError_t launch_cols(int mode, const FftArgs &a, int sms, cudaStream_t s);   // 0 blur, 1 correlation
+cudaError_t launch_iteration(const FftArgs &a, int sms, cudaStream_t s);
 }  // namespace fftr
 
 // PSF-gradient building blocks (adjoint.cu); every call covers P planes.
