@@ -23,7 +23,7 @@ namespace {
 constexpr int kWarps = 8;                // columns per CTA at most
 constexpr int kThreads = 32 * kWarps;
 constexpr size_t kSmemCap = 227 * 1024;
-constexpr int kBatch = 4;
+constexpr int kBatch = 8;
 constexpr int kPlanBytes = 128;
 static_assert(sizeof(FftPlan1) <= kPlanBytes, "plan copy");
 

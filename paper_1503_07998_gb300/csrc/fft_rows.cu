@@ -23,7 +23,7 @@ constexpr int kThreads = 32 * kWarps;
 constexpr size_t kSmemCap = 227 * 1024;
 // Element loops issue kBatch global loads into registers before the batch's
 // shared-memory stores, so that several loads are in flight per lane.
-constexpr int kBatch = 4;
+constexpr int kBatch = 8;
 constexpr int kPlanBytes = 128;
 static_assert(sizeof(FftPlan1) <= kPlanBytes, "plan copy");
 
