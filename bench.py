@@ -738,15 +738,33 @@ def run_batch(args):
     ms = reduce_max(e0.elapsed_time(e1) / args.steps, world)
     units = sum(v["P"] * v["H"] * v["W"] * v["iters"] * v["views"] for v in allv)
     info = mvd.mvd_batch_info(batch)
+    info.update(mvd.mvd_batch_queue_info(batch))
+    mvd.mvd_batch_device_status(batch)
+    # the schedule the tuner did not keep, timed the same way (one step)
+    chosen = info["schedule"]
+    other = "graph" if chosen == "queue" else "queue"
+    schedules = {chosen: ms}
+    try:
+        mvd.mvd_batch_set_schedule(batch, other)
+        mvd.mvd_batch_run(batch)
+        torch.cuda.synchronize()
+        oms, _ = timed_call(stream, lambda: mvd.mvd_batch_run(batch))
+        mvd.mvd_batch_device_status(batch)
+        schedules[other] = oms
+        schedules[other + "_info"] = mvd.mvd_batch_queue_info(batch)
+    except mvd.MvdError as e:
+        schedules[other] = {"unavailable": str(e)}
+    mvd.mvd_batch_set_schedule(batch, chosen)
     line = {"metric": METRIC, "value": units / (ms / 1e3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "strong",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "64 uneven volumes in one captured CUDA graph per GPU (see run_batch)",
+            "config": {"workload": "64 uneven volumes per GPU, one captured CUDA graph, fused-route volumes on "
+                                   "the persistent queue when the tuner keeps it (see run_batch)",
                        "voxels": int(sum(v["P"] * v["H"] * v["W"] for v in allv)),
                        "voxel_view_iterations": int(units), "order": "sequential",
                        "l2": "inputs larger than L2",
                        "parallelism": f"{world} GPU(s), volumes dealt round robin, no collective"},
-            "batch": info, "tune_s": tune_s, "clocks": clk,
+            "batch": info, "schedules_ms": schedules, "tune_s": tune_s, "clocks": clk,
             "gpu_launches": int(mvd.mvd_launch_count() - n0)}
     batch.close()
     if rank == 0:

@@ -328,6 +328,36 @@ mvd_status mvd_batch_run(mvd_batch *b, void *stream);
  * kernel nodes in the graph (0 before the first run). */
 mvd_status mvd_batch_info(const mvd_batch *b, int *concurrent, int *max_ctas, int *graph_kernels);
 
+/* Schedules of a batch.
+ * MVD_BATCH_GRAPH: every volume is its own graph branch of per-iteration
+ *   kernel launches (1 + 2 * iters per volume and view group).
+ * MVD_BATCH_QUEUE: the volumes on the fused separable route (PSFs of rank
+ *   low enough for it, K <= 47) run as ONE persistent launch per PSF-size
+ *   class (K <= 17, <= 31, <= 47; factors padded with zero taps) over a
+ *   device-side queue of (phase, volume, plane, tile) work items, where a
+ *   phase is one half (blur/ratio or correlate/update) of an iteration's
+ *   view group (Supp. Note 1 update).  Items are taken in phase order from
+ *   an atomic counter; before reading, an item waits until every tile of its
+ *   plane has finished the previous phase (a per-plane counter in device
+ *   memory).  The waits are bounded by the batch's wait budget; an expired
+ *   wait sets MVD_ERR_TIMEOUT in the batch's status word and every CTA of the
+ *   launch leaves.  The other volumes (Fourier or other routes) stay graph
+ *   branches.  Reslicing and the per-plane means run before the queue
+ *   launches in the same graph.
+ * mvd_batch_tune times both and keeps the faster; these calls override or
+ * read the choice (the graph is recaptured on the next run). */
+typedef enum { MVD_BATCH_GRAPH = 0, MVD_BATCH_QUEUE = 1 } mvd_batch_schedule;
+mvd_status mvd_batch_set_schedule(mvd_batch *b, int schedule);
+/* schedule in use, volumes on the queue and their work items in total. */
+mvd_status mvd_batch_queue_info(const mvd_batch *b, int *schedule, int *queue_volumes, long long *queue_items);
+/* Clock cycles one queue wait may spin before it reports a timeout (0: the
+ * default, about one second).  A negative budget makes every wait report a
+ * timeout once its counter is reached: a test hook for the error path. */
+mvd_status mvd_batch_set_wait_budget(mvd_batch *b, long long cycles);
+/* Synchronise the calling thread with the device, then read and clear the
+ * batch's status word: MVD_ERR_TIMEOUT after an expired queue wait. */
+mvd_status mvd_batch_device_status(mvd_batch *b);
+
 mvd_status mvd_batch_destroy(mvd_batch *b);
 
 /* PSF calibration: the Poisson data fit of the deconvolved estimate and its

@@ -47,8 +47,8 @@ mvd_status cuda_fail(cudaError_t e, const char *what) {
 }
 
 // Tuning cache (MVD_TUNE_CACHE): lines "<key> <a> <b>".
-bool tune_cache_lookup(const std::string &key, int *a, int *b);
-void tune_cache_store(const std::string &key, int a, int b);
+bool tune_cache_lookup(const std::string &key, int *a, int *b, int *c);
+void tune_cache_store(const std::string &key, int a, int b, int c);
 
 struct DeviceGuard {
     int prev = -1, want;
@@ -917,7 +917,7 @@ mvd_status mvd_autotune(mvd_ctx *c, const void *data, mvd_dtype dt, int n_planes
                   static_cast<int>(c->boundary), static_cast<int>(c->order), c->ft.total_terms,
                   static_cast<int>(c->variant), c->weights ? 1 : 0);
     int cached = -1, unused = 0;
-    if (tune_cache_lookup(key, &cached, &unused) && cached >= 0) {
+    if (tune_cache_lookup(key, &cached, &unused, &unused) && cached >= 0) {
         c->algo = static_cast<mvd_algo>(cached);
         return MVD_OK;
     }
@@ -979,7 +979,7 @@ mvd_status mvd_autotune(mvd_ctx *c, const void *data, mvd_dtype dt, int n_planes
         return st;
     }
     c->algo = best_a;
-    tune_cache_store(key, static_cast<int>(best_a), 0);
+    tune_cache_store(key, static_cast<int>(best_a), 0, 0);
     return MVD_OK;
 }
 
@@ -1402,6 +1402,18 @@ struct mvd_batch {
     int max_ctas = 0;
     int graph_kernels = 0;
     std::string key;
+    // persistent queue schedule (MVD_BATCH_QUEUE): the fused-route volumes of
+    // each PSF-size class run as one launch over a device work queue
+    int schedule = MVD_BATCH_GRAPH;
+    long long wait_budget = mvd::kDefaultWaitBudget;
+    DevBuf status;                               // one int: the queue launches' status word
+    struct Queue {
+        std::vector<int> vols;                   // batch indices of the class's volumes
+        DevBuf qvols, segs, taps, done, ctl;     // ctl: head (u64) + abort (int)
+        mvd::bq::QParams qp{};
+        long long items = 0;
+    } q[mvd::bq::kClasses];
+    bool queue_ready = false;
 };
 
 namespace {
@@ -1414,6 +1426,115 @@ void batch_drop_graph(mvd_batch *b) {
     b->graph_kernels = 0;
 }
 
+// A volume runs on the queue when its context takes the fused separable
+// route with a PSF the fused kernels cover and at least one iteration.
+bool queue_volume(const mvd_ctx *c) {
+    return c->algo == MVD_ALGO_FUSED && mvd::fused_supported(c->K) && mvd::bq::size_class(c->K) >= 0 &&
+           c->iters > 0 && !c->weights && c->Ka == 0;
+}
+
+// Per-class tables of the queue schedule: volume descriptors with their
+// factors padded to the class size, phase-major segments, per-plane counters.
+mvd_status batch_queue_prepare(mvd_batch *b) {
+    for (int cls = 0; cls < mvd::bq::kClasses; ++cls) {
+        auto &Q = b->q[cls];
+        Q.vols.clear();
+        Q.items = 0;
+        const int KC = mvd::bq::class_k(cls);
+        std::vector<mvd::bq::QVol> qv;
+        std::vector<float> taps;
+        long long planes = 0;
+        int max_phases = 0;
+        for (size_t i = 0; i < b->vols.size(); ++i) {
+            mvd_ctx *c = b->ctx[i];
+            if (!queue_volume(c) || mvd::bq::size_class(c->K) != cls) continue;
+            const mvd_volume_desc &d = b->vols[i];
+            cudaError_t e = prepare_workspace(c, d.n_planes);
+            if (e != cudaSuccess) return fail(MVD_ERR_NOMEM, "volume %zu workspace: %s", i, cudaGetErrorString(e));
+            mvd::bq::QVol v{};
+            v.phi = d.stacks_dev ? b->planes[i].ptr : d.planes_dev;
+            v.u16 = b->dt == MVD_U16;
+            v.psi = d.estimate_dev;
+            v.ratio = c->ratio.as<float>();
+            v.means = c->means.as<float>();
+            v.H = c->H;
+            v.W = c->W;
+            v.P = d.n_planes;
+            v.V = c->V;
+            v.circular = c->boundary == MVD_BOUNDARY_CIRCULAR;
+            v.seq = c->order == MVD_ORDER_SEQUENTIAL;
+            v.phases = 2 * c->iters * (v.seq ? c->V : 1);
+            v.tiles_x = (c->W + 127) / 128;
+            v.tiles = v.tiles_x * ((c->H + 31) / 32);
+            v.eps = c->eps;
+            // factors [terms][4][K] -> [terms][4][KC], centred, zero taps around
+            const int pad = (KC - c->K) / 2;
+            const size_t base = taps.size() / (4 * KC);
+            for (int t = 0; t < c->ft.total_terms; ++t)
+                for (int kind = 0; kind < 4; ++kind) {
+                    std::vector<float> row(KC, 0.0f);
+                    for (int m = 0; m < c->K; ++m)
+                        row[pad + m] = c->taps_host[(static_cast<size_t>(t) * 4 + kind) * c->K + m];
+                    taps.insert(taps.end(), row.begin(), row.end());
+                }
+            for (int vv = 0; vv < c->V; ++vv) {
+                v.rank[vv] = c->ft.rank[vv];
+                v.tap_off[vv] = static_cast<int>(base) + c->ft.tap_off[vv];
+                v.crank[vv] = c->ft.crank[vv];
+                v.ctap_off[vv] = static_cast<int>(base) + c->ft.ctap_off[vv];
+                v.short_mask[vv] = c->ft.short_mask[vv];
+            }
+            // taps and done are device offsets until the buffers exist
+            v.taps = nullptr;
+            v.done = reinterpret_cast<int *>(planes * sizeof(int));
+            planes += d.n_planes;
+            max_phases = std::max(max_phases, v.phases);
+            qv.push_back(v);
+            Q.vols.push_back(static_cast<int>(i));
+        }
+        if (qv.empty()) continue;
+        std::vector<mvd::bq::QSeg> segs;
+        long long start = 0;
+        for (int ph = 0; ph < max_phases; ++ph)
+            for (size_t j = 0; j < qv.size(); ++j) {
+                if (ph >= qv[j].phases) continue;
+                segs.push_back({start, static_cast<int>(j), ph});
+                start += static_cast<long long>(qv[j].P) * qv[j].tiles;
+            }
+        Q.items = start;
+        cudaError_t e;
+        if ((e = Q.qvols.ensure(qv.size() * sizeof(mvd::bq::QVol))) != cudaSuccess ||
+            (e = Q.segs.ensure(segs.size() * sizeof(mvd::bq::QSeg))) != cudaSuccess ||
+            (e = Q.taps.ensure(taps.size() * sizeof(float))) != cudaSuccess ||
+            (e = Q.done.ensure(planes * sizeof(int))) != cudaSuccess ||
+            (e = Q.ctl.ensure(16)) != cudaSuccess)
+            return fail(MVD_ERR_NOMEM, "queue tables: %s", cudaGetErrorString(e));
+        for (auto &v : qv) {
+            v.taps = Q.taps.as<float>();
+            v.done = Q.done.as<int>() + reinterpret_cast<size_t>(v.done) / sizeof(int);
+        }
+        if ((e = cudaMemcpy(Q.qvols.ptr, qv.data(), qv.size() * sizeof(mvd::bq::QVol), cudaMemcpyHostToDevice)) !=
+                cudaSuccess ||
+            (e = cudaMemcpy(Q.segs.ptr, segs.data(), segs.size() * sizeof(mvd::bq::QSeg), cudaMemcpyHostToDevice)) !=
+                cudaSuccess ||
+            (e = cudaMemcpy(Q.taps.ptr, taps.data(), taps.size() * sizeof(float), cudaMemcpyHostToDevice)) !=
+                cudaSuccess)
+            return cuda_fail(e, "upload queue tables");
+        auto &qp = Q.qp;
+        qp.vols = Q.qvols.as<mvd::bq::QVol>();
+        qp.segs = Q.segs.as<mvd::bq::QSeg>();
+        qp.nseg = static_cast<int>(segs.size());
+        qp.total = Q.items;
+        qp.head = reinterpret_cast<unsigned long long *>(Q.ctl.ptr);
+        qp.abort = reinterpret_cast<int *>(static_cast<char *>(Q.ctl.ptr) + 8);
+    }
+    cudaError_t e = b->status.ensure(sizeof(int));
+    if (e != cudaSuccess) return fail(MVD_ERR_NOMEM, "batch status: %s", cudaGetErrorString(e));
+    if ((e = cudaMemset(b->status.ptr, 0, sizeof(int))) != cudaSuccess) return cuda_fail(e, "batch status");
+    b->queue_ready = true;
+    return MVD_OK;
+}
+
 mvd_status batch_capture(mvd_batch *b) {
     batch_drop_graph(b);
     for (auto *c : b->ctx) c->max_ctas = b->max_ctas;
@@ -1424,26 +1545,69 @@ mvd_status batch_capture(mvd_batch *b) {
         uint64_t before;
         ~Uncount() { mvd::g_launches.fetch_sub(mvd::g_launches.load() - before); }
     } uncount{counted_before};
+    // the queue's tables are allocated and uploaded before capturing
+    if (b->schedule == MVD_BATCH_QUEUE && !b->queue_ready) {
+        mvd_status qs = batch_queue_prepare(b);
+        if (qs != MVD_OK) return qs;
+    }
     cudaError_t e = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return cuda_fail(e, "begin capture");
     mvd_status st = MVD_OK;
+    const bool queue = b->schedule == MVD_BATCH_QUEUE;
+    std::vector<char> on_queue(b->vols.size(), 0);
+    if (queue)
+        for (auto &Q : b->q)
+            for (int i : Q.vols) on_queue[i] = 1;
     cudaEventRecord(b->fork, b->cap);
-    for (size_t i = 0; i < b->vols.size() && st == MVD_OK; ++i) {
-        const mvd_volume_desc &v = b->vols[i];
-        cudaStream_t s = b->concurrent ? b->streams[i] : b->cap;
-        if (b->concurrent) cudaStreamWaitEvent(s, b->fork, 0);
-        const void *data = v.planes_dev;
-        if (v.stacks_dev) {
-            st = mvd_reslice(b->ctx[i], v.stacks_dev, b->dt, v.views, v.plane_h, v.n_planes, v.plane_w,
-                             b->planes[i].ptr, s);
-            data = b->planes[i].ptr;
+    // queue volumes: reslice and plane means on their branches, joined before
+    // the queue launches; the others: their whole schedule, joined at the end
+    for (int pass = 0; pass < 2 && st == MVD_OK; ++pass) {
+        for (size_t i = 0; i < b->vols.size() && st == MVD_OK; ++i) {
+            if (on_queue[i] != (pass == 0)) continue;
+            const mvd_volume_desc &v = b->vols[i];
+            mvd_ctx *c = b->ctx[i];
+            cudaStream_t s = b->concurrent ? b->streams[i] : b->cap;
+            if (b->concurrent) cudaStreamWaitEvent(s, b->fork, 0);
+            const void *data = v.planes_dev;
+            if (v.stacks_dev) {
+                st = mvd_reslice(c, v.stacks_dev, b->dt, v.views, v.plane_h, v.n_planes, v.plane_w, b->planes[i].ptr,
+                                 s);
+                data = b->planes[i].ptr;
+            }
+            if (st == MVD_OK && on_queue[i]) {
+                cudaError_t e2 = mvd::launch_plane_means(data, b->dt == MVD_U16, c->V, v.n_planes, c->H, c->W,
+                                                          c->means.as<float>(), s);
+                if (e2 != cudaSuccess) st = cuda_fail(e2, "plane means kernel");
+            } else if (st == MVD_OK) {
+                st = mvd_deconvolve_planes(c, data, b->dt, v.estimate_dev, v.n_planes, 1, s);
+            }
+            if (b->concurrent && pass == 0) {
+                cudaEventRecord(b->done[i], s);
+                cudaStreamWaitEvent(b->cap, b->done[i], 0);
+            }
         }
-        if (st == MVD_OK) st = mvd_deconvolve_planes(b->ctx[i], data, b->dt, v.estimate_dev, v.n_planes, 1, s);
-        if (b->concurrent) {
-            cudaEventRecord(b->done[i], s);
-            cudaStreamWaitEvent(b->cap, b->done[i], 0);
+        if (pass == 0 && queue && st == MVD_OK) {
+            int sms = 0;
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device);
+            for (int cls = 0; cls < mvd::bq::kClasses && st == MVD_OK; ++cls) {
+                auto &Q = b->q[cls];
+                if (Q.items == 0) continue;
+                Q.qp.err = b->status.as<int>();
+                Q.qp.wait_budget = b->wait_budget;
+                cudaError_t e2 = cudaMemsetAsync(Q.done.ptr, 0, Q.done.bytes, b->cap);
+                if (e2 == cudaSuccess) e2 = cudaMemsetAsync(Q.ctl.ptr, 0, 16, b->cap);
+                if (e2 == cudaSuccess) e2 = mvd::bq::launch_queue(cls, Q.qp, sms, b->cap);
+                if (e2 != cudaSuccess) st = cuda_fail(e2, "queue launch");
+                else mvd::count_launch(1);
+            }
         }
     }
+    if (b->concurrent)
+        for (size_t i = 0; i < b->vols.size(); ++i)
+            if (!on_queue[i]) {
+                cudaEventRecord(b->done[i], b->streams[i]);
+                cudaStreamWaitEvent(b->cap, b->done[i], 0);
+            }
     cudaGraph_t g = nullptr;
     e = cudaStreamEndCapture(b->cap, &g);
     if (st != MVD_OK) {
@@ -1467,7 +1631,7 @@ mvd_status batch_capture(mvd_batch *b) {
     return MVD_OK;
 }
 
-bool tune_cache_lookup(const std::string &key, int *conc, int *ctas) {
+bool tune_cache_lookup(const std::string &key, int *conc, int *ctas, int *sched) {
     const char *path = std::getenv("MVD_TUNE_CACHE");
     if (!path || !*path) return false;
     FILE *f = std::fopen(path, "r");
@@ -1475,17 +1639,21 @@ bool tune_cache_lookup(const std::string &key, int *conc, int *ctas) {
     char line[4096];
     bool found = false;
     while (std::fgets(line, sizeof line, f)) {
-        // line: <key> <concurrent> <max_ctas>
-        char *sp = std::strrchr(line, ' ');
-        if (!sp) continue;
-        *sp = 0;
-        const int c2 = std::atoi(sp + 1);
-        char *sp2 = std::strrchr(line, ' ');
-        if (!sp2) continue;
-        *sp2 = 0;
-        if (key == line) {
-            *conc = std::atoi(sp2 + 1);
-            *ctas = c2;
+        // line: <key> <concurrent> <max_ctas> <schedule>
+        int v[3];
+        bool ok = true;
+        for (int k = 2; k >= 0 && ok; --k) {
+            char *sp = std::strrchr(line, ' ');
+            if (!sp) ok = false;
+            else {
+                v[k] = std::atoi(sp + 1);
+                *sp = 0;
+            }
+        }
+        if (ok && key == line) {
+            *conc = v[0];
+            *ctas = v[1];
+            *sched = v[2];
             found = true;
         }
     }
@@ -1493,12 +1661,12 @@ bool tune_cache_lookup(const std::string &key, int *conc, int *ctas) {
     return found;
 }
 
-void tune_cache_store(const std::string &key, int conc, int ctas) {
+void tune_cache_store(const std::string &key, int conc, int ctas, int sched) {
     const char *path = std::getenv("MVD_TUNE_CACHE");
     if (!path || !*path) return;
     FILE *f = std::fopen(path, "a");
     if (!f) return;
-    std::fprintf(f, "%s %d %d\n", key.c_str(), conc, ctas);
+    std::fprintf(f, "%s %d %d %d\n", key.c_str(), conc, ctas, sched);
     std::fclose(f);
 }
 
@@ -1524,7 +1692,7 @@ mvd_status mvd_batch_create(mvd_batch **out, const mvd_volume_desc *vols, int n,
     b->vols.assign(vols, vols + n);
     const size_t es = dt == MVD_U16 ? 2 : 4;
     char buf[128];
-    b->key = "v1";
+    b->key = "v2";
     for (int i = 0; i < n && true; ++i) {
         const mvd_volume_desc &v = vols[i];
         mvd_ctx *c = nullptr;
@@ -1604,17 +1772,26 @@ mvd_status mvd_batch_tune(mvd_batch *b, void *stream) {
         }
         batch_drop_graph(b);
     }
-    // 2. the launch shape
-    int conc = 1, ctas = 0;
-    if (tune_cache_lookup(b->key, &conc, &ctas)) {
+    // 2. the schedule and launch shape
+    b->queue_ready = false;
+    int conc = 1, ctas = 0, sched = MVD_BATCH_GRAPH;
+    if (tune_cache_lookup(b->key, &conc, &ctas, &sched)) {
         b->concurrent = conc;
         b->max_ctas = ctas;
+        b->schedule = sched;
         batch_drop_graph(b);
         return MVD_OK;
     }
     int sms = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device);
-    const int cand[][2] = {{1, 0}, {0, 0}, {1, sms > 0 ? sms : 1}};
+    bool any_queue = false;
+    for (auto *c : b->ctx) any_queue |= queue_volume(c);
+    // {concurrent branches, persistent-grid cap, schedule}
+    const int cand[][3] = {{1, 0, MVD_BATCH_GRAPH},
+                           {0, 0, MVD_BATCH_GRAPH},
+                           {1, sms > 0 ? sms : 1, MVD_BATCH_GRAPH},
+                           {1, 0, MVD_BATCH_QUEUE}};
+    const int n_cand = any_queue ? 4 : 3;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
@@ -1622,9 +1799,10 @@ mvd_status mvd_batch_tune(mvd_batch *b, void *stream) {
     float best = 1e30f;
     int best_i = 0;
     mvd_status st = MVD_OK;
-    for (int i = 0; i < 3 && st == MVD_OK; ++i) {
+    for (int i = 0; i < n_cand && st == MVD_OK; ++i) {
         b->concurrent = cand[i][0];
         b->max_ctas = cand[i][1];
+        b->schedule = cand[i][2];
         if ((st = batch_capture(b)) != MVD_OK) break;
         cudaGraphLaunch(b->exec, s);                  // warm
         cudaEventRecord(e0, s);
@@ -1644,10 +1822,12 @@ mvd_status mvd_batch_tune(mvd_batch *b, void *stream) {
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (st != MVD_OK) return st;
+    if ((st = mvd_batch_device_status(b)) != MVD_OK) return st;
     b->concurrent = cand[best_i][0];
     b->max_ctas = cand[best_i][1];
+    b->schedule = cand[best_i][2];
     batch_drop_graph(b);
-    tune_cache_store(b->key, b->concurrent, b->max_ctas);
+    tune_cache_store(b->key, b->concurrent, b->max_ctas, b->schedule);
     return MVD_OK;
 }
 
@@ -1659,6 +1839,55 @@ mvd_status mvd_batch_info(const mvd_batch *b, int *concurrent, int *max_ctas, in
     return MVD_OK;
 }
 
+mvd_status mvd_batch_set_schedule(mvd_batch *b, int schedule) {
+    t_last_error.clear();
+    if (!b) return fail(MVD_ERR_ARG, "batch is NULL");
+    if (schedule != MVD_BATCH_GRAPH && schedule != MVD_BATCH_QUEUE) return fail(MVD_ERR_ARG, "unknown schedule");
+    DeviceGuard g(b->device);
+    b->schedule = schedule;
+    batch_drop_graph(b);
+    return MVD_OK;
+}
+
+mvd_status mvd_batch_queue_info(const mvd_batch *b, int *schedule, int *queue_volumes, long long *queue_items) {
+    if (!b) return fail(MVD_ERR_ARG, "batch is NULL");
+    int nv = 0;
+    long long items = 0;
+    if (b->schedule == MVD_BATCH_QUEUE && b->queue_ready)
+        for (const auto &Q : b->q) {
+            nv += static_cast<int>(Q.vols.size());
+            items += Q.items;
+        }
+    if (schedule) *schedule = b->schedule;
+    if (queue_volumes) *queue_volumes = nv;
+    if (queue_items) *queue_items = items;
+    return MVD_OK;
+}
+
+mvd_status mvd_batch_set_wait_budget(mvd_batch *b, long long cycles) {
+    t_last_error.clear();
+    if (!b) return fail(MVD_ERR_ARG, "batch is NULL");
+    DeviceGuard g(b->device);
+    b->wait_budget = cycles == 0 ? mvd::kDefaultWaitBudget : cycles;
+    batch_drop_graph(b);
+    return MVD_OK;
+}
+
+mvd_status mvd_batch_device_status(mvd_batch *b) {
+    t_last_error.clear();
+    if (!b) return fail(MVD_ERR_ARG, "batch is NULL");
+    DeviceGuard g(b->device);
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return cuda_fail(e, "batch");
+    if (!b->status.ptr) return MVD_OK;
+    int w = 0;
+    if ((e = cudaMemcpy(&w, b->status.ptr, sizeof w, cudaMemcpyDeviceToHost)) != cudaSuccess)
+        return cuda_fail(e, "batch status");
+    if (w == 0) return MVD_OK;
+    cudaMemset(b->status.ptr, 0, sizeof(int));
+    return fail(MVD_ERR_TIMEOUT, "a queue wait of the batch ran out (status %d)", w);
+}
+
 mvd_status mvd_batch_destroy(mvd_batch *b) {
     if (!b) return MVD_OK;
     DeviceGuard g(b->device);
@@ -1667,6 +1896,14 @@ mvd_status mvd_batch_destroy(mvd_batch *b) {
     for (auto &p : b->planes) p.release();
     for (auto s : b->streams) cudaStreamDestroy(s);
     for (auto ev : b->done) cudaEventDestroy(ev);
+    for (auto &Q : b->q) {
+        Q.qvols.release();
+        Q.segs.release();
+        Q.taps.release();
+        Q.done.release();
+        Q.ctl.release();
+    }
+    b->status.release();
     if (b->fork) cudaEventDestroy(b->fork);
     if (b->cap) cudaStreamDestroy(b->cap);
     delete b;

@@ -149,6 +149,47 @@ void tf32_tile_shape(int K, int *tile_h, int *tile_w);
 cudaError_t launch_tf32_blur_ratio(const FusedArgs &a, cudaStream_t s);
 cudaError_t launch_tf32_correlate_update(const FusedArgs &a, cudaStream_t s);
 
+// Persistent batched launch of the fused path (batchq.cu).
+namespace bq {
+// One volume of the queue: its planes, estimate, ratio scratch, plane means,
+// factor taps padded to the launch's PSF-size class ([terms][4][KC], the
+// FactorTable layout) and one counter of finished tiles per plane.
+struct QVol {
+    const void *phi;          // [V][P][H][W]
+    int u16;
+    float *psi;               // [P][H][W]
+    float *ratio;             // [V][P][H][W]
+    const float *means;       // [P]
+    const float *taps;
+    int *done;                // [P]
+    int H, W, P, V, circular, seq, phases, tiles_x, tiles;
+    float eps;
+    int rank[kMaxViews], tap_off[kMaxViews], crank[kMaxViews], ctap_off[kMaxViews];
+    unsigned char short_mask[kMaxViews];
+};
+// Items [start, start + P * tiles) are phase `phase` of volume `vol`.
+struct QSeg {
+    long long start;
+    int vol, phase;
+};
+struct QParams {
+    const QVol *vols;
+    const QSeg *segs;
+    int nseg;
+    long long total;                  // items
+    unsigned long long *head;         // queue counter (zero before the launch)
+    int *abort;                       // set when a wait expires: every CTA leaves
+    int *err;                         // device status word
+    long long wait_budget;            // clock cycles per wait; < 0: report a timeout (test hook)
+};
+constexpr int kClasses = 3;
+// PSF-size class of K (0: 17, 1: 31, 2: 47), -1 beyond the fused kernels.
+int size_class(int K);
+int class_k(int cls);
+// Items, grid and shared memory of a class's launch.
+cudaError_t launch_queue(int cls, const QParams &qp, int sms, cudaStream_t s);
+}  // namespace bq
+
 // Fourier route (fft.cu, fft_rows.cu, fft_cols.cu).
 namespace fftr {
 constexpr int kMaxRadices = 16;

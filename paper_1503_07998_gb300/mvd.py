@@ -84,6 +84,10 @@ def lib() -> ctypes.CDLL:
     L.mvd_batch_run.argtypes = [vp, vp]
     L.mvd_batch_info.argtypes = [vp, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i)]
     L.mvd_batch_destroy.argtypes = [vp]
+    L.mvd_batch_set_schedule.argtypes = [vp, i]
+    L.mvd_batch_queue_info.argtypes = [vp, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(ctypes.c_longlong)]
+    L.mvd_batch_set_wait_budget.argtypes = [vp, ctypes.c_longlong]
+    L.mvd_batch_device_status.argtypes = [vp]
     L.mvd_deconvolve_planes_static.argtypes = [i, vp, i, i, i, i, i, f, vp, i, vp, i, i, vp]
     L.mvd_static_device_status.argtypes = [vp]
     L.mvd_static_set_wait_budget.argtypes = [ctypes.c_longlong]
@@ -110,6 +114,8 @@ def lib() -> ctypes.CDLL:
                  "mvd_deconvolve_planes_static", "mvd_static_device_status", "mvd_static_set_wait_budget",
                  "mvd_debug_fail_allocations", "mvd_psf_grad", "mvd_set_psfs", "mvd_autotune",
                  "mvd_batch_create", "mvd_batch_tune", "mvd_batch_run", "mvd_batch_info", "mvd_batch_destroy",
+                 "mvd_batch_set_schedule", "mvd_batch_queue_info", "mvd_batch_set_wait_budget",
+                 "mvd_batch_device_status",
                  "mvd_reslice", "mvd_deconvolve_planes", "mvd_run_host", "mvd_psf_factors",
                  "mvd_profile_enable", "mvd_profile_read"):
         getattr(L, name).restype = ctypes.c_int
@@ -622,6 +628,30 @@ def mvd_batch_info(batch: Batch) -> dict:
     c, m, k = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
     _check(lib().mvd_batch_info(batch.handle, ctypes.byref(c), ctypes.byref(m), ctypes.byref(k)), "mvd_batch_info")
     return {"concurrent": c.value, "max_ctas": m.value, "graph_kernels": k.value}
+
+
+BATCH_SCHEDULE = {"graph": 0, "queue": 1}
+
+
+def mvd_batch_set_schedule(batch: Batch, schedule: str) -> None:
+    _check(lib().mvd_batch_set_schedule(batch.handle, BATCH_SCHEDULE[schedule]), "mvd_batch_set_schedule")
+
+
+def mvd_batch_queue_info(batch: Batch) -> dict:
+    s, n, q = ctypes.c_int(), ctypes.c_int(), ctypes.c_longlong()
+    _check(lib().mvd_batch_queue_info(batch.handle, ctypes.byref(s), ctypes.byref(n), ctypes.byref(q)),
+           "mvd_batch_queue_info")
+    names = {v: k for k, v in BATCH_SCHEDULE.items()}
+    return {"schedule": names.get(s.value, s.value), "queue_volumes": n.value, "queue_items": q.value}
+
+
+def mvd_batch_set_wait_budget(batch: Batch, cycles: int) -> None:
+    _check(lib().mvd_batch_set_wait_budget(batch.handle, int(cycles)), "mvd_batch_set_wait_budget")
+
+
+def mvd_batch_device_status(batch: Batch) -> None:
+    """Raises MvdError (MVD_ERR_TIMEOUT) if a queue wait of the batch ran out."""
+    _check(lib().mvd_batch_device_status(batch.handle), "mvd_batch_device_status")
 
 
 def mvd_batch_destroy(batch: Batch) -> None:
