@@ -1467,6 +1467,13 @@ mvd_status batch_queue_prepare(mvd_batch *b) {
             v.tiles_x = (c->W + 127) / 128;
             v.tiles = v.tiles_x * ((c->H + 31) / 32);
             v.eps = c->eps;
+            // TMA tiles on the zero boundary (zero fill outside the plane)
+            int bw = 0, bh = 0;
+            mvd::bq::tile_box(cls, &bw, &bh);
+            v.use_tma = !v.circular &&
+                        mvd::fused::encode_plane_map(&v.psi_map, v.psi, v.W, v.H, v.P, bw, bh) &&
+                        mvd::fused::encode_plane_map(&v.ratio_map, v.ratio, v.W, v.H,
+                                                     static_cast<long long>(v.V) * v.P, bw, bh);
             // factors [terms][4][K] -> [terms][4][KC], centred, zero taps around
             const int pad = (KC - c->K) / 2;
             const size_t base = taps.size() / (4 * KC);
@@ -1479,13 +1486,14 @@ mvd_status batch_queue_prepare(mvd_batch *b) {
                 }
             for (int vv = 0; vv < c->V; ++vv) {
                 v.rank[vv] = c->ft.rank[vv];
-                v.tap_off[vv] = static_cast<int>(base) + c->ft.tap_off[vv];
+                v.tap_off[vv] = c->ft.tap_off[vv];
                 v.crank[vv] = c->ft.crank[vv];
-                v.ctap_off[vv] = static_cast<int>(base) + c->ft.ctap_off[vv];
+                v.ctap_off[vv] = c->ft.ctap_off[vv];
                 v.short_mask[vv] = c->ft.short_mask[vv];
             }
+            v.ntaps = c->ft.total_terms * 4 * KC;
             // taps and done are device offsets until the buffers exist
-            v.taps = nullptr;
+            v.taps = reinterpret_cast<const float *>(base * 4 * KC * sizeof(float));
             v.done = reinterpret_cast<int *>(planes * sizeof(int));
             planes += d.n_planes;
             max_phases = std::max(max_phases, v.phases);
@@ -1510,7 +1518,7 @@ mvd_status batch_queue_prepare(mvd_batch *b) {
             (e = Q.ctl.ensure(16)) != cudaSuccess)
             return fail(MVD_ERR_NOMEM, "queue tables: %s", cudaGetErrorString(e));
         for (auto &v : qv) {
-            v.taps = Q.taps.as<float>();
+            v.taps = Q.taps.as<float>() + reinterpret_cast<size_t>(v.taps) / sizeof(float);
             v.done = Q.done.as<int>() + reinterpret_cast<size_t>(v.done) / sizeof(int);
         }
         if ((e = cudaMemcpy(Q.qvols.ptr, qv.data(), qv.size() * sizeof(mvd::bq::QVol), cudaMemcpyHostToDevice)) !=

@@ -30,6 +30,7 @@
 
 #include "fused_common.cuh"
 #include "mvd_internal.h"
+#include "tma.cuh"
 
 namespace mvd {
 namespace bq {
@@ -40,7 +41,14 @@ using fused::Geo;
 using fused::kNC;
 using fused::kThreads;
 constexpr int kTyQ = 32;                 // output tile rows
-constexpr int kHeader = 128;             // item slot, flags
+constexpr int kHeader = 128;             // item slots, barrier, flags
+// The current volume's descriptor and (up to kTapCache floats of) factor
+// taps live in shared memory while the CTA works on its items.
+constexpr int kQvBytes = (static_cast<int>(sizeof(QVol)) + 127) / 128 * 128;
+constexpr int kTapCache = 4096;
+constexpr int kTileAt = kHeader + kQvBytes + kTapCache * 4;
+static_assert(kTileAt % 128 == 0, "TMA destination alignment");
+static_assert(sizeof(QVol) % 16 == 0, "descriptor copied as 16-byte words");
 constexpr long long kDrainBudget = 4000000000LL;
 
 __device__ __forceinline__ float load_data(const void *phi, int u16, long long i) {
@@ -48,27 +56,72 @@ __device__ __forceinline__ float load_data(const void *phi, int u16, long long i
                : __ldg(static_cast<const float *>(phi) + i);
 }
 
-// Tile [BOX_H][BOX_W] of a plane written inside this launch (L2 reads);
-// src == nullptr: the plane's constant first estimate `fill`.
+// Tile [BOX_H][BOX_W] of a plane written inside this launch, for volumes
+// without a TMA map (circular boundary, unaligned rows): L2 reads, eight in
+// flight per thread before their shared-memory stores.
 template <int KC>
-__device__ __forceinline__ void load_tile_l2(float *__restrict__ tile, const float *src, float fill, int y0, int x0,
-                                             int H, int W, int circular) {
+__device__ __forceinline__ void load_tile_l2(float *__restrict__ tile, const float *src, int y0, int x0, int H, int W,
+                                             int circular) {
     using G = Geo<KC, kTyQ>;
     constexpr int N = G::BOX_H * G::BOX_W;
-    for (int idx = threadIdx.x; idx < N; idx += kThreads) {
-        const int r = idx / G::BOX_W;
-        const int c = idx - r * G::BOX_W;
-        int gy = y0 - G::R + r, gx = x0 - G::R4 + c;
-        bool in = gy >= 0 && gy < H && gx >= 0 && gx < W;
-        if (circular) {
-            gy %= H;
-            if (gy < 0) gy += H;
-            gx %= W;
-            if (gx < 0) gx += W;
-            in = true;
+    constexpr int B = 8;
+    for (int i0 = threadIdx.x; i0 < N; i0 += B * kThreads) {
+        float r[B];
+#pragma unroll
+        for (int u = 0; u < B; ++u) {
+            const int idx = i0 + u * kThreads;
+            r[u] = 0.0f;
+            if (idx < N) {
+                const int row = idx / G::BOX_W;
+                int gy = y0 - G::R + row, gx = x0 - G::R4 + (idx - row * G::BOX_W);
+                bool in = gy >= 0 && gy < H && gx >= 0 && gx < W;
+                if (circular) {
+                    gy %= H;
+                    if (gy < 0) gy += H;
+                    gx %= W;
+                    if (gx < 0) gx += W;
+                    in = true;
+                }
+                if (in) r[u] = __ldcg(src + static_cast<long long>(gy) * W + gx);
+            }
         }
-        tile[idx] = in ? (src ? __ldcg(src + static_cast<long long>(gy) * W + gx) : fill) : 0.0f;
+#pragma unroll
+        for (int u = 0; u < B; ++u)
+            if (i0 + u * kThreads < N) tile[i0 + u * kThreads] = r[u];
     }
+}
+
+// The item's input tile into shared memory: the plane's constant first
+// estimate, a TMA copy from the volume's map (plane z), or L2 loads.  Every
+// thread waits on the copy's barrier; an expired wait flags the status word
+// and the batch's abort flag, drains the copy and returns false (uniform).
+template <int KC>
+__device__ __forceinline__ bool stage_tile(float *tile, uint64_t *bar, uint32_t &phase, volatile int *cta_abort,
+                                           const QVol &v, const QParams &qp, const CUtensorMap *map,
+                                           const float *src, bool constant, float fill, int z, int y0, int x0) {
+    using G = Geo<KC, kTyQ>;
+    if (constant) {
+        fused::fill_tile_const<KC, kTyQ>(tile, fill, y0, x0, v.H, v.W, v.circular);
+    } else if (v.use_tma) {
+        if (threadIdx.x == 0) {
+            tma::fence_proxy_async_global();
+            tma::fence_proxy_async_smem();
+            tma::mbar_arrive_expect_tx(bar, G::TILE_BYTES);
+            tma::load_3d(tile, map, bar, x0 - G::R4, y0 - G::R, z);
+        }
+        const long long budget = qp.wait_budget < 0 ? kDrainBudget : qp.wait_budget;
+        if (!tma::mbar_wait_bounded(bar, phase, budget)) {
+            atomicOr(qp.err, kDevTimeout);
+            atomicExch(qp.abort, 1);
+            tma::mbar_wait_bounded(bar, phase, kDrainBudget);
+            *cta_abort = 1;
+        }
+        phase ^= 1u;
+    } else {
+        load_tile_l2<KC>(tile, src, y0, x0, v.H, v.W, v.circular);
+    }
+    __syncthreads();
+    return *cta_abort == 0;
 }
 
 // Phase s of a volume: iteration, views [v0, v1) and kind (0 = A, 1 = B).
@@ -119,70 +172,150 @@ __device__ bool wait_counter(const int *counter, int need, const QParams &qp) {
 
 namespace {
 
+// Row-wise epilogue over the 32 x 128 results parked in the staging tile:
+// warp w takes rows w, w + 8, ...; lane l columns l, l + 32, l + 64, l + 96,
+// so every load and store of a warp is one contiguous 128-byte run.
+//   RATIO:  out = phi / max(result, eps)      (out, phi: the view's plane)
+//   UPDATE: psi = psi * result, or mean * result on the first update
+template <int KC, bool RATIO>
+__device__ __forceinline__ void row_out(const float *__restrict__ stage, const QVol &v, long long plane_off,
+                                        int y0, int x0, bool first, float mean) {
+    using G = Geo<KC, kTyQ>;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int r = warp; r < G::TY; r += kThreads / 32) {
+        const int y = y0 + r;
+        if (y >= v.H) break;
+        const long long row = plane_off + static_cast<long long>(y) * v.W;
+        float in[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const int x = x0 + lane + 32 * e;
+            in[e] = 0.0f;
+            if (x < v.W) {
+                if (RATIO) in[e] = load_data(v.phi, v.u16, row + x);
+                else in[e] = first ? mean : __ldcg(v.psi + row + x);
+            }
+        }
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const int x = x0 + lane + 32 * e;
+            if (x >= v.W) continue;
+            const float s = stage[r * G::VB_LD + lane + 32 * e];
+            if (RATIO) v.ratio[row + x] = __fdiv_rn(in[e], fmaxf(s, v.eps));
+            else v.psi[row + x] = in[e] * s;
+        }
+    }
+}
+
+}  // namespace
+
+namespace {
+
 template <int KC>
 __global__ void __launch_bounds__(kThreads, 2) queue_kernel(const __grid_constant__ QParams qp) {
     using G = Geo<KC, kTyQ>;
     static_assert(G::H_PER_THREAD == 1, "one horizontal item per thread");
-    static_assert(kHeader == fused::kTileOffset, "tile placement");
     extern __shared__ __align__(128) unsigned char smem[];
+    // header: the current item (q, segment, go), the tile barrier, the CTA's
+    // abort flag, and the next item taken ahead (q, segment, its plane's
+    // counter and the count it needs)
     long long *slot = reinterpret_cast<long long *>(smem);
     int *slot_seg = reinterpret_cast<int *>(smem + 8);
     int *slot_ok = reinterpret_cast<int *>(smem + 12);
-    float *tile = reinterpret_cast<float *>(smem + kHeader);
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem + 16);
+    volatile int *cta_abort = reinterpret_cast<volatile int *>(smem + 24);
+    long long *next_q = reinterpret_cast<long long *>(smem + 32);
+    int *next_seg = reinterpret_cast<int *>(smem + 40);
+    int *next_need = reinterpret_cast<int *>(smem + 44);
+    const int **next_done = reinterpret_cast<const int **>(smem + 48);
+    QVol *vs = reinterpret_cast<QVol *>(smem + kHeader);
+    float *taps_s = reinterpret_cast<float *>(smem + kHeader + kQvBytes);
+    float *tile = reinterpret_cast<float *>(smem + kTileAt);
     float *stage = tile + G::BOX_H * G::BOX_W;
     constexpr int KS = fused::short_taps<KC>();
+    uint32_t phase = 0;
+    // One thread of warp 1 takes the next item from the queue while the CTA
+    // works on the current one: items come in increasing order, so its
+    // segment search starts from the last segment found.
+    constexpr int kTaker = 32;
+    int sg_cache = 0;
+    int cached_vol = -1;
+    auto take_next = [&]() {
+        const long long q = static_cast<long long>(atomicAdd(qp.head, 1ull));
+        *next_q = q;
+        if (q >= qp.total) return;
+        if (sg_cache + 1 < qp.nseg && qp.segs[sg_cache + 1].start <= q) {
+            int lo = sg_cache + 1, hi = qp.nseg - 1;   // last segment starting at or before q
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (qp.segs[mid].start <= q) lo = mid;
+                else hi = mid - 1;
+            }
+            sg_cache = lo;
+        }
+        const QSeg &seg = qp.segs[sg_cache];
+        const QVol &v = qp.vols[seg.vol];
+        const int p = static_cast<int>((q - seg.start) / v.tiles);
+        *next_seg = sg_cache;
+        *next_need = seg.phase * v.tiles;
+        *next_done = v.done + p;
+    };
+    if (threadIdx.x == 0) {
+        *cta_abort = 0;
+        tma::mbar_init(bar, 1);
+        tma::fence_barrier_init();
+    }
+    if (threadIdx.x == kTaker) take_next();
+    __syncthreads();
 
     for (;;) {
         if (threadIdx.x == 0) {
-            const long long q = static_cast<long long>(atomicAdd(qp.head, 1ull));
+            const long long q = *next_q;
             int ok = *reinterpret_cast<volatile int *>(qp.abort) == 0;
-            int sg = 0;
-            if (q < qp.total && ok) {
-                int lo = 0, hi = qp.nseg - 1;   // last segment starting at or before q
-                while (lo < hi) {
-                    const int mid = (lo + hi + 1) >> 1;
-                    if (qp.segs[mid].start <= q) lo = mid;
-                    else hi = mid - 1;
-                }
-                sg = lo;
-                const QSeg &seg = qp.segs[sg];
-                const QVol &v = qp.vols[seg.vol];
-                const int p = static_cast<int>((q - seg.start) / v.tiles);
-                ok = wait_counter(v.done + p, seg.phase * v.tiles, qp);
-            }
+            if (q < qp.total && ok) ok = wait_counter(*next_done, *next_need, qp);
             *slot = q;
-            *slot_seg = sg;
+            *slot_seg = *next_seg;
             *slot_ok = ok;
         }
         __syncthreads();
         const long long q = *slot;
         if (q >= qp.total || !*slot_ok) break;
+        if (threadIdx.x == kTaker) take_next();
         const QSeg seg = qp.segs[*slot_seg];
-        const QVol &v = qp.vols[seg.vol];
+        if (seg.vol != cached_vol) {   // uniform: the descriptor and taps of a new volume
+            const QVol *g = qp.vols + seg.vol;
+            for (int i = threadIdx.x; i < static_cast<int>(sizeof(QVol) / 16); i += kThreads)
+                reinterpret_cast<int4 *>(vs)[i] = reinterpret_cast<const int4 *>(g)[i];
+            const int nt = g->ntaps;
+            if (nt <= kTapCache)
+                for (int i = threadIdx.x; i < nt; i += kThreads) taps_s[i] = __ldg(g->taps + i);
+            __syncthreads();
+            cached_vol = seg.vol;
+        }
+        const QVol &v = *vs;
+        const QVol *vg = qp.vols + seg.vol;
+        const float *taps = v.ntaps <= kTapCache ? taps_s : v.taps;
         const long long local = q - seg.start;
         const int p = static_cast<int>(local / v.tiles);
         const int k = static_cast<int>(local - static_cast<long long>(p) * v.tiles);
         const int ty = k / v.tiles_x;
         const int y0 = ty * G::TY, x0 = (k - ty * v.tiles_x) * G::TX;
-        const int H = v.H, W = v.W, P = v.P;
-        const long long plane = static_cast<long long>(H) * W;
+        const int P = v.P;
+        const long long plane = static_cast<long long>(v.H) * v.W;
         const PhaseInfo f = phase_info(v, seg.phase);
-        int y, x;
-        fused::item_origin<KC, kTyQ>(0, y0, x0, y, x);
-        const int n = (y < H && x < W) ? min(kNC, W - x) : 0;
 
         if (f.kind == 0) {   // A: ratio_v = phi_v / max(P_v * psi, eps)
             const bool first = seg.phase == 0;
-            load_tile_l2<KC>(tile, first ? nullptr : v.psi + p * plane, first ? __ldg(v.means + p) : 0.0f, y0,
-                             x0, H, W, v.circular);
-            __syncthreads();
+            if (!stage_tile<KC>(tile, bar, phase, cta_abort, v, qp, &vg->psi_map, v.psi + p * plane, first,
+                                first ? __ldg(v.means + p) : 0.0f, p, y0, x0))
+                break;
             for (int vv = f.v0; vv < f.v1; ++vv) {
                 float acc[1][kNC];
 #pragma unroll
                 for (int j = 0; j < kNC; ++j) acc[0][j] = 0.0f;
                 const unsigned sm = v.short_mask[vv];
                 for (int t = 0; t < v.rank[vv]; ++t) {
-                    const float *tq = v.taps + static_cast<long long>(v.tap_off[vv] + t) * 4 * KC;
+                    const float *tq = taps + static_cast<long long>(v.tap_off[vv] + t) * 4 * KC;
                     if (sm & 1u) fused::vertical_pass<KC, KS, kTyQ>(tile, stage, tq);
                     else fused::vertical_pass<KC, KC, kTyQ>(tile, stage, tq);
                     __syncthreads();
@@ -190,25 +323,26 @@ __global__ void __launch_bounds__(kThreads, 2) queue_kernel(const __grid_constan
                     else fused::horizontal_pass<KC, KC, kTyQ>(stage, tq + KC, acc);
                     __syncthreads();
                 }
-                const long long off = (static_cast<long long>(vv) * P + p) * plane + static_cast<long long>(y) * W + x;
-                float d[kNC];
-#pragma unroll
-                for (int e = 0; e < kNC; ++e) d[e] = e < n ? load_data(v.phi, v.u16, off + e) : 0.0f;
-#pragma unroll
-                for (int e = 0; e < kNC; ++e)
-                    if (e < n) v.ratio[off + e] = __fdiv_rn(d[e], fmaxf(acc[0][e], v.eps));
+                fused::park_items<KC, kTyQ>(stage, acc);
+                __syncthreads();
+                row_out<KC, true>(stage, v, (static_cast<long long>(vv) * P + p) * plane, y0, x0, false, 0.0f);
+                __syncthreads();   // the staging tile is rewritten by the next pass
             }
         } else {             // B: psi <- psi * prod_v (ratio_v correlated with P_v)
             float prod[1][kNC];
 #pragma unroll
             for (int j = 0; j < kNC; ++j) prod[0][j] = 1.0f;
+            bool dead = false;
             for (int vv = f.v0; vv < f.v1; ++vv) {
-                load_tile_l2<KC>(tile, v.ratio + (static_cast<long long>(vv) * P + p) * plane, 0.0f, y0, x0, H, W,
-                                 v.circular);
-                __syncthreads();
+                if (!stage_tile<KC>(tile, bar, phase, cta_abort, v, qp, &vg->ratio_map,
+                                    v.ratio + (static_cast<long long>(vv) * P + p) * plane, false, 0.0f, vv * P + p,
+                                    y0, x0)) {
+                    dead = true;
+                    break;
+                }
                 const unsigned sm = v.short_mask[vv];
                 if (v.crank[vv] == 1) {
-                    const float *tq = v.taps + static_cast<long long>(v.ctap_off[vv]) * 4 * KC + 2 * KC;
+                    const float *tq = taps + static_cast<long long>(v.ctap_off[vv]) * 4 * KC + 2 * KC;
                     if (sm & 4u) fused::vertical_pass<KC, KS, kTyQ>(tile, stage, tq);
                     else fused::vertical_pass<KC, KC, kTyQ>(tile, stage, tq);
                     __syncthreads();
@@ -220,7 +354,7 @@ __global__ void __launch_bounds__(kThreads, 2) queue_kernel(const __grid_constan
 #pragma unroll
                     for (int j = 0; j < kNC; ++j) c[0][j] = 0.0f;
                     for (int t = 0; t < v.crank[vv]; ++t) {
-                        const float *tq = v.taps + static_cast<long long>(v.ctap_off[vv] + t) * 4 * KC + 2 * KC;
+                        const float *tq = taps + static_cast<long long>(v.ctap_off[vv] + t) * 4 * KC + 2 * KC;
                         if (sm & 4u) fused::vertical_pass<KC, KS, kTyQ>(tile, stage, tq);
                         else fused::vertical_pass<KC, KC, kTyQ>(tile, stage, tq);
                         __syncthreads();
@@ -232,18 +366,16 @@ __global__ void __launch_bounds__(kThreads, 2) queue_kernel(const __grid_constan
                     for (int j = 0; j < kNC; ++j) prod[0][j] *= c[0][j];
                 }
             }
+            if (dead) break;
             // the first update starts from the plane's mean
             const bool first = seg.phase == 1;
-            const long long off = p * plane + static_cast<long long>(y) * W + x;
-            const float m = first ? __ldg(v.means + p) : 0.0f;
-            float b[kNC];
-#pragma unroll
-            for (int e = 0; e < kNC; ++e) b[e] = e < n ? (first ? m : __ldcg(v.psi + off + e)) : 0.0f;
-#pragma unroll
-            for (int e = 0; e < kNC; ++e)
-                if (e < n) v.psi[off + e] = b[e] * prod[0][e];
+            fused::park_items<KC, kTyQ>(stage, prod);
+            __syncthreads();
+            row_out<KC, false>(stage, v, p * plane, y0, x0, first, first ? __ldg(v.means + p) : 0.0f);
         }
-        // publish the tile: every thread's stores, then the plane's counter
+        // publish the tile: every thread's stores (to plain loads and to the
+        // TMA copies of later items), then the plane's counter
+        tma::fence_proxy_async_global();
         __threadfence();
         __syncthreads();
         if (threadIdx.x == 0) atomicAdd(v.done + p, 1);
@@ -253,7 +385,7 @@ __global__ void __launch_bounds__(kThreads, 2) queue_kernel(const __grid_constan
 template <int KC>
 cudaError_t launch_class(const QParams &qp, int sms, cudaStream_t s) {
     using G = Geo<KC, kTyQ>;
-    const size_t smem = G::SMEM_BYTES;
+    const size_t smem = kTileAt + (G::BOX_H * G::BOX_W + G::TY * G::VB_LD) * 4;
     cudaError_t e = cudaFuncSetAttribute(queue_kernel<KC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          static_cast<int>(smem));
     if (e != cudaSuccess) return e;
@@ -269,6 +401,18 @@ cudaError_t launch_class(const QParams &qp, int sms, cudaStream_t s) {
 }
 
 }  // namespace
+
+template <int KC>
+void box_of(int *w, int *h) {
+    *w = Geo<KC, kTyQ>::BOX_W;
+    *h = Geo<KC, kTyQ>::BOX_H;
+}
+
+void tile_box(int cls, int *box_w, int *box_h) {
+    if (cls == 0) box_of<17>(box_w, box_h);
+    else if (cls == 1) box_of<31>(box_w, box_h);
+    else box_of<47>(box_w, box_h);
+}
 
 int size_class(int K) { return K <= 17 ? 0 : (K <= 31 ? 1 : (K <= kFusedMaxK ? 2 : -1)); }
 int class_k(int cls) { return cls == 0 ? 17 : (cls == 1 ? 31 : 47); }

@@ -588,6 +588,13 @@ cudaError_t dispatch(const FusedArgs &a, int which, cudaStream_t s) {
 
 }  // namespace
 
+// Tile map of an FP32 [D][H][W] tensor for other translation units (the
+// batch queue): false if the encoder is missing or rejects the layout.
+bool encode_plane_map(CUtensorMap *m, const void *base, int W, int H, long long D, int box_w, int box_h) {
+    if (!aligned16(base) || (static_cast<long long>(W) * 4) % 16 != 0) return false;
+    return encode_3d(m, base, W, H, D, box_w, box_h);
+}
+
 }  // namespace fused
 
 bool fused_supported(int K) { return K >= 1 && K <= kFusedMaxK && (K % 2) == 1; }

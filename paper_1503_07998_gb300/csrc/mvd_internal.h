@@ -5,6 +5,7 @@
 #include <cstddef>
 #include <cstdint>
 #include <vector>
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 namespace mvd {
@@ -155,12 +156,16 @@ namespace bq {
 // factor taps padded to the launch's PSF-size class ([terms][4][KC], the
 // FactorTable layout) and one counter of finished tiles per plane.
 struct QVol {
+    CUtensorMap psi_map;      // TMA maps of the estimate [P][H][W] and the ratios [V*P][H][W]
+    CUtensorMap ratio_map;    // (boxes of the launch's tile), valid if use_tma
+    int use_tma;
     const void *phi;          // [V][P][H][W]
     int u16;
     float *psi;               // [P][H][W]
     float *ratio;             // [V][P][H][W]
     const float *means;       // [P]
-    const float *taps;
+    const float *taps;        // this volume's factors
+    int ntaps;                // their floats (terms * 4 * KC)
     int *done;                // [P]
     int H, W, P, V, circular, seq, phases, tiles_x, tiles;
     float eps;
@@ -188,7 +193,12 @@ int size_class(int K);
 int class_k(int cls);
 // Items, grid and shared memory of a class's launch.
 cudaError_t launch_queue(int cls, const QParams &qp, int sms, cudaStream_t s);
+// TMA box (width, height) of a class's tiles.
+void tile_box(int cls, int *box_w, int *box_h);
 }  // namespace bq
+namespace fused {
+bool encode_plane_map(CUtensorMap *m, const void *base, int W, int H, long long D, int box_w, int box_h);
+}  // namespace fused
 
 // Fourier route (fft.cu, fft_rows.cu, fft_cols.cu).
 namespace fftr {

@@ -26,10 +26,10 @@ def mvd():
     return m
 
 
-def make_batch(mvd, vols, order):
+def make_batch(mvd, vols, order, boundary="zero"):
     ests = [torch.full((v["P"], v["H"], v["W"]), -1.0, device="cuda") for v in vols]
     batch = mvd.mvd_batch_create([{"stacks": v["stacks"], "psfs": v["psfs"], "iters": v["iters"], "estimate": e}
-                                  for v, e in zip(vols, ests)], order=order)
+                                  for v, e in zip(vols, ests)], boundary=boundary, order=order)
     return batch, ests
 
 
@@ -38,13 +38,13 @@ def planes_of(v):
     return np.stack([oracle.reslice(s) for s in v["stacks"].cpu().numpy()])
 
 
-def check_against_oracle(vols, ests, order, sample):
+def check_against_oracle(vols, ests, order, sample, boundary="zero"):
     for v, e in zip(vols, ests):
         got = e.cpu().numpy()
         planes = planes_of(v)
         for p in sample(v["P"]):
             phi = planes[:, p][:, None]
-            ref = oracle.rl_planes(phi, v["psfs"], v["iters"], eps=1e-6, order=order, route="fft")
+            ref = oracle.rl_planes(phi, v["psfs"], v["iters"], eps=1e-6, order=order, boundary=boundary, route="fft")
             assert_parity(got[p][None], ref, what=f"volume {v['H']}^2 x {v['P']} V={v['views']} K={v['K']} plane {p}")
 
 
@@ -73,6 +73,22 @@ def test_queue_schedule_small_uneven_volumes(mvd, order):
         for q, g in zip(queued, ests):
             assert_parity(q.cpu().numpy(), g.cpu().numpy().astype(np.float64), what="queue vs graph schedule")
         check_against_oracle(vols, queued, order, lambda P: sorted({0, P // 2, P - 1}))
+    finally:
+        batch.close()
+
+
+def test_queue_schedule_circular_boundary(mvd):
+    """Circular boundary: the queue stages its tiles with plain L2 loads
+    (indices wrapped) instead of TMA copies."""
+    vols = synth.uneven_volumes(4, seed=310, side=(48, 130), planes=(2, 5), views=(2, 2), psf=(5, 35),
+                                iters=(2, 4), density=2e-3, device="cuda")
+    batch, ests = make_batch(mvd, vols, "sequential", boundary="circular")
+    try:
+        mvd.mvd_batch_set_schedule(batch, "queue")
+        mvd.mvd_batch_run(batch)
+        mvd.mvd_batch_device_status(batch)
+        assert mvd.mvd_batch_queue_info(batch)["queue_volumes"] == 4
+        check_against_oracle(vols, ests, "sequential", lambda P: [0, P - 1], boundary="circular")
     finally:
         batch.close()
 
