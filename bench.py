@@ -495,6 +495,25 @@ def run_mvd(args, wl):
         finally:
             mvd.mvd_set_algo(ctx, "fused")
 
+    # the plane-resident route on the same planes (planes up to 512 x 512)
+    resident = None
+    if leg("resident"):
+        try:
+            mvd.mvd_set_algo(ctx, "resident")
+            mvd.mvd_deconvolve_planes(ctx, planes, est)
+            torch.cuda.synchronize()
+            rms, _ = timed_call(stream, lambda: mvd.mvd_deconvolve_planes(ctx, planes, est), ctx)
+            keep("resident")
+            resident = {"value": units_per_step / (rms / 1e3), "unit": UNIT, "ms": rms,
+                        "note": "deconvolution only (no reslice); one thread-block cluster per plane keeps the "
+                                "estimate, ratio and product in shared memory for all iterations, phi read once "
+                                "per iteration and view",
+                        "hbm_bytes_per_vi_algorithmic": (es * iters * V + 4 + 4) / (iters * V)}
+        except mvd.MvdError as e:
+            resident = {"unavailable": str(e)}
+        finally:
+            mvd.mvd_set_algo(ctx, "fused")
+
     # the optional tensor-core routes (BF16x3 and TF32 tcgen05 passes) on the
     # same planes
     tc_routes = {}
@@ -663,7 +682,8 @@ def run_mvd(args, wl):
                 "roofline": roof, "kernels": kr, "cpu_baseline": cpu, "e2e": e2e,
                 "error_vs_oracle": errors,
                 "gpu_launches": int(launches), "clocks": clk, "sms": sms, "plain_per_plane": plain,
-                "fft_route": fft_route, "tensor_route": tensor_route, "tf32_route": tf32_route,
+                "fft_route": fft_route, "resident_route": resident, "tensor_route": tensor_route,
+                "tf32_route": tf32_route,
                 "weighted_padded": weighted, "vol3d": vol3d, "psf_grad": grad,
                 "paper_context": "GTX TITAN Black, 2 views, 1024^3 padded, 10 it: 21.1 s = 1.02e9 voxel-view-it/s "
                                  "(Supp. Table 1); another machine, not the target"}
@@ -685,7 +705,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-plain", action="store_true", help="none of the comparison legs")
     ap.add_argument("--legs", default="all",
-                    help="comparison legs to run: all, or a comma list of plain,fft,tensor,tf32,weighted,vol3d,grad")
+                    help="comparison legs to run: all, or a comma list of plain,fft,resident,tensor,tf32,weighted,vol3d,grad")
     args = ap.parse_args()
     if args.warmup < 3:
         print("note: at least 3 warm-up steps are used", file=sys.stderr)

@@ -103,7 +103,19 @@ typedef enum {
      * boundaries.  Its error against the exact result is larger than the
      * FP32 routes' and is reported, not bounded by their tolerance.  Never
      * chosen by default or by mvd_autotune. */
-    MVD_ALGO_TF32 = 5
+    MVD_ALGO_TF32 = 5,
+    /* Plane-resident route: one thread-block cluster of up to 16 CTAs keeps
+     * a plane's estimate, ratio and (simultaneous order) product of the
+     * views' corrections in shared memory for all iterations; the vertical
+     * passes read the rows next to a CTA's strip from its neighbours' shared
+     * memory (distributed shared memory), cluster barriers separate the
+     * phases of each iteration (Supp. Note 1 update).  Per iteration HBM is
+     * read only for the data phi_v.  Same separable factors and FP32
+     * arithmetic as MVD_ALGO_FUSED.  ZERO boundary, K <= 47, planes of up to
+     * 512 columns whose three (simultaneous) or two (sequential) strip
+     * buffers fit in shared memory: up to 512 x 512 (16 CTAs of 32 rows).
+     * Never chosen by default or by mvd_autotune. */
+    MVD_ALGO_RESIDENT = 6
 } mvd_algo;
 
 typedef enum {
@@ -193,6 +205,8 @@ mvd_status mvd_destroy(mvd_ctx *ctx);
  *   MVD_ALGO_FUSED        K <= 47 and the separable terms fit;
  *   MVD_ALGO_FFT          a padded grid of 2^a 3^b 5^c sides <= 2048 exists;
  *   MVD_ALGO_TENSOR/TF32  odd K <= 47;
+ *   MVD_ALGO_RESIDENT     ZERO boundary, K <= 47, no weights or axial
+ *                         profiles, a plane that fits on chip (see above);
  *   MVD_ALGO_PLAIN/DIRECT any K.
  * Weights, axial profiles, mvd_run_host and mvd_psf_grad add their own
  * restrictions (see there). */

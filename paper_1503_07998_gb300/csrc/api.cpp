@@ -196,6 +196,8 @@ struct mvd_ctx {
         mvd::fftr::FftPlan1 px{}, py{};
         DevBuf tw_x, tw_y, spec, cspec, S0, T;
     } fft;
+    DevBuf res_taps;                     // plane-resident route: factors padded to the size class
+    bool res_taps_ready = false;         // res_taps holds the current factors
 };
 
 namespace {
@@ -239,6 +241,7 @@ mvd_status upload_factors(mvd_ctx *c) {
     build_corr_psfs(c);
     c->psf_dev_fresh = false;
     c->fft.planned = false;   // the spectra follow the PSFs and the variant
+    c->res_taps_ready = false;
     if (!mvd::factorise_psfs(c->psfs.data(), c->V, c->K, c->rank_tol, c->ft, taps.data(), cap, msg, sizeof msg,
                              c->corr_psfs.empty() ? nullptr : c->corr_psfs.data()))
         return fail(MVD_ERR_ARG, "PSF factorisation failed: %s", msg);
@@ -507,6 +510,83 @@ mvd_status run_fft(mvd_ctx *c, const void *data, mvd_dtype dt, float *est, int P
             if ((e = mvd::fftr::launch_iteration(a, sms, s)) != cudaSuccess) return cuda_fail(e, "Fourier kernels");
         }
     }
+    c->prof.end(s);
+    return MVD_OK;
+}
+
+// The context's factors [terms][4][K] padded with zero taps to [terms][4][KC].
+std::vector<float> padded_taps(const mvd_ctx *c, int KC) {
+    const int pad = (KC - c->K) / 2;
+    std::vector<float> out(static_cast<size_t>(c->ft.total_terms) * 4 * KC, 0.0f);
+    for (int t = 0; t < c->ft.total_terms; ++t)
+        for (int kind = 0; kind < 4; ++kind)
+            for (int m = 0; m < c->K; ++m)
+                out[(static_cast<size_t>(t) * 4 + kind) * KC + pad + m] =
+                    c->taps_host[(static_cast<size_t>(t) * 4 + kind) * c->K + m];
+    return out;
+}
+
+// Whether the plane-resident route can take this context: its cluster size,
+// strip rows and shared memory.
+bool resident_plan(const mvd_ctx *c, int *C, int *strip, size_t *smem) {
+    const int cls = mvd::bq::size_class(c->K);
+    if (cls < 0 || c->boundary != MVD_BOUNDARY_ZERO || c->weights || c->Ka != 0) return false;
+    const int KC = mvd::bq::class_k(cls);
+    return mvd::res::plan(c->H, c->W, cls, c->order == MVD_ORDER_SEQUENTIAL, c->ft.total_terms * 4 * KC, C, strip,
+                          smem);
+}
+
+// The padded factors on the device, uploaded once per factorisation (from
+// mvd_set_algo, so that a captured run does no synchronous copy).
+mvd_status upload_resident_taps(mvd_ctx *c) {
+    if (c->res_taps_ready) return MVD_OK;
+    const std::vector<float> taps = padded_taps(c, mvd::bq::class_k(mvd::bq::size_class(c->K)));
+    cudaError_t e = c->res_taps.ensure(taps.size() * sizeof(float));
+    if (e != cudaSuccess) return fail(MVD_ERR_NOMEM, "resident taps: %s", cudaGetErrorString(e));
+    if ((e = cudaMemcpy(c->res_taps.ptr, taps.data(), taps.size() * sizeof(float), cudaMemcpyHostToDevice)) !=
+        cudaSuccess)
+        return cuda_fail(e, "upload resident taps");
+    c->res_taps_ready = true;
+    return MVD_OK;
+}
+
+mvd_status run_resident(mvd_ctx *c, const void *data, mvd_dtype dt, float *est, int P, int init_mean,
+                        cudaStream_t s) {
+    int C = 0, strip = 0;
+    size_t smem = 0;
+    if (!resident_plan(c, &C, &strip, &smem)) return fail(MVD_ERR_UNSUPPORTED, "plane does not fit on chip");
+    const int cls = mvd::bq::size_class(c->K);
+    const int KC = mvd::bq::class_k(cls);
+    mvd_status st = upload_resident_taps(c);
+    if (st != MVD_OK) return st;
+    cudaError_t e;
+    mvd::res::ResArgs a{};
+    a.phi = data;
+    a.u16 = dt == MVD_U16;
+    a.psi_in = init_mean ? nullptr : est;
+    a.means = c->means.as<float>();
+    a.psi_out = est;
+    a.taps = c->res_taps.as<float>();
+    a.ntaps = c->ft.total_terms * 4 * KC;
+    a.H = c->H;
+    a.W = c->W;
+    a.P = P;
+    a.V = c->V;
+    a.iters = c->iters;
+    a.seq = c->order == MVD_ORDER_SEQUENTIAL;
+    a.strip = strip;
+    a.C = C;
+    a.eps = c->eps;
+    for (int v = 0; v < c->V; ++v) {
+        a.rank[v] = c->ft.rank[v];
+        a.tap_off[v] = c->ft.tap_off[v];
+        a.crank[v] = c->ft.crank[v];
+        a.ctap_off[v] = c->ft.ctap_off[v];
+        a.short_mask[v] = c->ft.short_mask[v];
+    }
+    c->prof.mark(s, "resident");
+    if ((e = mvd::res::launch(a, cls, smem, s)) != cudaSuccess) return cuda_fail(e, "plane-resident kernel");
+    mvd::count_launch(1);
     c->prof.end(s);
     return MVD_OK;
 }
@@ -1004,6 +1084,7 @@ mvd_status mvd_destroy(mvd_ctx *c) {
     c->fft.spec.release();
     c->fft.S0.release();
     c->fft.T.release();
+    c->res_taps.release();
     if (c->copy_in) cudaStreamDestroy(c->copy_in);
     if (c->copy_out) cudaStreamDestroy(c->copy_out);
     delete c;
@@ -1013,8 +1094,17 @@ mvd_status mvd_destroy(mvd_ctx *c) {
 mvd_status mvd_set_algo(mvd_ctx *c, mvd_algo algo) {
     if (!c) return fail(MVD_ERR_ARG, "ctx is NULL");
     if (algo != MVD_ALGO_FUSED && algo != MVD_ALGO_PLAIN && algo != MVD_ALGO_DIRECT && algo != MVD_ALGO_FFT &&
-        !tensor_algo(algo))
+        !tensor_algo(algo) && algo != MVD_ALGO_RESIDENT)
         return fail(MVD_ERR_ARG, "unknown algo %d", static_cast<int>(algo));
+    if (algo == MVD_ALGO_RESIDENT) {
+        int C, strip;
+        size_t smem;
+        if (!resident_plan(c, &C, &strip, &smem))
+            return fail(MVD_ERR_UNSUPPORTED,
+                        "plane-resident route: ZERO boundary, K <= 47, no weights, planes that fit on chip");
+        mvd_status st = upload_resident_taps(c);
+        if (st != MVD_OK) return st;
+    }
     if (tensor_algo(algo) && !mvd::tc_supported(c->K))
         return fail(MVD_ERR_UNSUPPORTED, "tensor-core route takes odd K <= 47 (got %d)", c->K);
     if (algo == MVD_ALGO_FUSED && !(mvd::fused_supported(c->K) && mvd::fused_taps_fit(c->ft)))
@@ -1266,6 +1356,7 @@ mvd_status mvd_deconvolve_planes(mvd_ctx *c, const void *data, mvd_dtype dt, flo
     if ((c->algo == MVD_ALGO_FUSED && mvd::fused_taps_fit(c->ft)) || tensor_algo(c->algo))
         return run_fused(c, data, dt, est, n_planes, init_mean, s);
     if (c->algo == MVD_ALGO_FFT) return run_fft(c, data, dt, est, n_planes, init_mean, s);
+    if (c->algo == MVD_ALGO_RESIDENT) return run_resident(c, data, dt, est, n_planes, init_mean, s);
     return run_plain(c, data, dt, est, n_planes, init_mean, c->algo == MVD_ALGO_DIRECT, s);
 }
 

@@ -200,6 +200,28 @@ namespace fused {
 bool encode_plane_map(CUtensorMap *m, const void *base, int W, int H, long long D, int box_w, int box_h);
 }  // namespace fused
 
+// Plane-resident route (resident.cu): a cluster of CTAs keeps one plane's
+// estimate, ratio and running product in shared memory for all iterations.
+namespace res {
+struct ResArgs {
+    const void *phi;          // [V][P][H][W]
+    int u16;
+    const float *psi_in;      // [P][H][W], or nullptr: start from the plane means
+    const float *means;       // [P]
+    float *psi_out;           // [P][H][W]
+    const float *taps;        // [terms][4][KC] (factors padded to the size class)
+    int ntaps;
+    int H, W, P, V, iters, seq, strip, C;
+    float eps;
+    int rank[kMaxViews], tap_off[kMaxViews], crank[kMaxViews], ctap_off[kMaxViews];
+    unsigned char short_mask[kMaxViews];
+};
+// Cluster size C, strip rows and dynamic shared memory for planes H x W with
+// PSF-size class cls; false if a plane does not fit on chip.
+bool plan(int H, int W, int cls, int seq, int ntaps, int *C, int *strip, size_t *smem);
+cudaError_t launch(const ResArgs &a, int cls, size_t smem, cudaStream_t s);
+}  // namespace res
+
 // Fourier route (fft.cu, fft_rows.cu, fft_cols.cu).
 namespace fftr {
 constexpr int kMaxRadices = 16;

@@ -24,7 +24,7 @@ HEADER = os.path.join(os.path.dirname(HERE), "include", "mvd.h")
 MVD_OK, MVD_ERR_ARG, MVD_ERR_CUDA, MVD_ERR_NOMEM, MVD_ERR_TIMEOUT, MVD_ERR_STATE, MVD_ERR_UNSUPPORTED = range(7)
 BOUNDARY = {"zero": 0, "circular": 1}
 DTYPE = {"u16": 0, "f32": 1}
-ALGO = {"fused": 0, "plain": 1, "direct": 2, "fft": 3, "tensor": 4, "tf32": 5}
+ALGO = {"fused": 0, "plain": 1, "direct": 2, "fft": 3, "tensor": 4, "tf32": 5, "resident": 6}
 ORDER = {"simultaneous": 0, "sequential": 1}
 VARIANT = {"independent": 0, "efficient_bayesian": 1, "optimization_1": 2, "optimization_2": 3}
 
