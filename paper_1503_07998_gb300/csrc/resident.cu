@@ -54,6 +54,14 @@ __host__ __device__ constexpr int stage_pitch(int W, int KC) {
     return (w / 4) % 2 == 1 ? w : w + 4;
 }
 
+// Row pitch of the strip buffers: W rounded to whole quads, an odd number of
+// them, so that the 16-byte stores of the 8 rows of a quarter-warp's items
+// hit distinct bank groups.
+__host__ __device__ constexpr int strip_pitch(int W) {
+    const int w = rup(W, 4);
+    return (w / 4) % 2 == 1 ? w : w + 4;
+}
+
 struct Layout {
     size_t rows_psi, rows_ratio, taps, psi, prod, ratio, stage, total;
 };
@@ -67,7 +75,7 @@ __host__ __device__ inline Layout layout(int W, int strip, int KC, int seq, int 
     o += static_cast<size_t>(strip + 2 * R) * sizeof(void *);
     L.taps = o = rup(static_cast<int>(o), 16);
     o += static_cast<size_t>(ntaps) * 4;
-    const size_t plane = static_cast<size_t>(strip) * W * 4;
+    const size_t plane = static_cast<size_t>(strip) * strip_pitch(W) * 4;
     L.psi = o = rup(static_cast<int>(o), 16);
     o += plane;
     L.prod = o;
@@ -83,6 +91,39 @@ __host__ __device__ inline Layout layout(int W, int strip, int KC, int seq, int 
 __device__ __forceinline__ float data_at(const void *phi, int u16, long long i) {
     return u16 ? static_cast<float>(__ldg(static_cast<const uint16_t *>(phi) + i))
                : __ldg(static_cast<const float *>(phi) + i);
+}
+
+// Columns c0 .. c0+15 of a strip row (16-byte aligned): whole quads inside
+// the plane's W columns, single values for a partial last quad, zeros (load)
+// or nothing (store) beyond.
+__device__ __forceinline__ void store16(float *row, int c0, int W, const float (&v)[16]) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int c = c0 + 4 * q;
+        if (c + 3 < W) {
+            *reinterpret_cast<float4 *>(row + c) = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+        } else {
+#pragma unroll
+            for (int e = 0; e < 4; ++e)
+                if (c + e < W) row[c + e] = v[4 * q + e];
+        }
+    }
+}
+__device__ __forceinline__ void load16(const float *row, int c0, int W, float (&v)[16]) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int c = c0 + 4 * q;
+        if (c + 3 < W) {
+            const float4 x = *reinterpret_cast<const float4 *>(row + c);
+            v[4 * q] = x.x;
+            v[4 * q + 1] = x.y;
+            v[4 * q + 2] = x.z;
+            v[4 * q + 3] = x.w;
+        } else {
+#pragma unroll
+            for (int e = 0; e < 4; ++e) v[4 * q + e] = c + e < W ? row[c + e] : 0.0f;
+        }
+    }
 }
 
 // Vertical pass of chunk rows r0 .. r0+7 of the strip:
@@ -157,6 +198,7 @@ __global__ void __launch_bounds__(kThreads, 1) resident_kernel(const __grid_cons
     float *ratio = reinterpret_cast<float *>(smem + L.ratio);
     float *stage = reinterpret_cast<float *>(smem + L.stage);
     const long long plane = static_cast<long long>(H) * W;
+    const int WP = strip_pitch(W);
     const int g0 = me * S;                       // first plane row of this strip
 
     // row tables: strip row j (-R <= j < S + R) -> its CTA's buffer, or zero
@@ -166,8 +208,8 @@ __global__ void __launch_bounds__(kThreads, 1) resident_kernel(const __grid_cons
         if (gy >= 0 && gy < H) {
             const unsigned owner = static_cast<unsigned>(gy / S);
             const int local = gy - static_cast<int>(owner) * S;
-            rp = cl.map_shared_rank(psi, owner) + static_cast<long long>(local) * W;
-            rr = cl.map_shared_rank(ratio, owner) + static_cast<long long>(local) * W;
+            rp = cl.map_shared_rank(psi, owner) + static_cast<long long>(local) * WP;
+            rr = cl.map_shared_rank(ratio, owner) + static_cast<long long>(local) * WP;
         }
         rows_psi[j] = rp;
         rows_ratio[j] = rr;
@@ -181,7 +223,7 @@ __global__ void __launch_bounds__(kThreads, 1) resident_kernel(const __grid_cons
         const int gy = g0 + r;
         float v = 0.0f;
         if (gy < H) v = a.psi_in ? __ldg(a.psi_in + p * plane + static_cast<long long>(gy) * W + c) : m0;
-        psi[i] = v;
+        psi[r * WP + c] = v;
     }
     cl.sync();
 
@@ -219,11 +261,10 @@ __global__ void __launch_bounds__(kThreads, 1) resident_kernel(const __grid_cons
                             const int c = g * kNC + j;
                             d[j] = c < W ? data_at(a.phi, a.u16, off + c) : 0.0f;
                         }
+                        float r[kNC];
 #pragma unroll
-                        for (int j = 0; j < kNC; ++j) {
-                            const int c = g * kNC + j;
-                            if (c < W) ratio[lr * W + c] = __fdiv_rn(d[j], fmaxf(acc[j], a.eps));
-                        }
+                        for (int j = 0; j < kNC; ++j) r[j] = __fdiv_rn(d[j], fmaxf(acc[j], a.eps));
+                        store16(ratio + lr * WP, g * kNC, W, r);
                     }
                 }
                 cl.sync();   // every strip's ratio is complete (halos of B)
@@ -247,19 +288,20 @@ __global__ void __launch_bounds__(kThreads, 1) resident_kernel(const __grid_cons
                     }
                     const int lr = r0 + row;
                     if (mine && lr < S && g0 + lr < H) {
+                        float *row_buf = (a.seq ? psi : prod) + lr * WP;
+                        if (a.seq || v != v0) {
+                            float old[kNC];
+                            load16(row_buf, g * kNC, W, old);
 #pragma unroll
-                        for (int j = 0; j < kNC; ++j) {
-                            const int c = g * kNC + j;
-                            if (c >= W) continue;
-                            float &dst = a.seq ? psi[lr * W + c] : prod[lr * W + c];
-                            dst = (a.seq || v != v0) ? dst * acc[j] : acc[j];
+                            for (int j = 0; j < kNC; ++j) acc[j] *= old[j];
                         }
+                        store16(row_buf, g * kNC, W, acc);
                     }
                 }
                 cl.sync();   // halo reads of r_v (and, sequential, of psi) are done
             }
             if (!a.seq) {    // simultaneous: psi *= prod_v c_v
-                for (int i = threadIdx.x; i < S * W; i += kThreads) psi[i] *= prod[i];
+                for (int i = threadIdx.x; i < S * WP; i += kThreads) psi[i] *= prod[i];
                 cl.sync();
             }
         }
@@ -267,7 +309,7 @@ __global__ void __launch_bounds__(kThreads, 1) resident_kernel(const __grid_cons
     for (int i = threadIdx.x; i < S * W; i += kThreads) {
         const int r = i / W, c = i - r * W;
         const int gy = g0 + r;
-        if (gy < H) a.psi_out[p * plane + static_cast<long long>(gy) * W + c] = psi[i];
+        if (gy < H) a.psi_out[p * plane + static_cast<long long>(gy) * W + c] = psi[r * WP + c];
     }
     cl.sync();   // no CTA leaves while another may still read its shared memory
 }
