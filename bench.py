@@ -704,6 +704,10 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-plain", action="store_true", help="none of the comparison legs")
+    ap.add_argument("--batch-volumes", default="",
+                    help="batch64 only: comma list of the volumes (0-63) to run instead of all 64")
+    ap.add_argument("--batch-schedule", default="auto", choices=["auto", "graph", "queue"],
+                    help="batch64 only: the schedule (auto: mvd_batch_tune picks)")
     ap.add_argument("--legs", default="all",
                     help="comparison legs to run: all, or a comma list of plain,fft,resident,tensor,tf32,weighted,vol3d,grad")
     args = ap.parse_args()
@@ -729,14 +733,18 @@ def run_batch(args):
     dev = torch.device("cuda", torch.cuda.current_device())
     stream = torch.cuda.current_stream(dev)
     # the same 64 volumes on every world size; each rank takes its share
-    mine = shard.volumes_of_rank(64, rank, world)
-    allv = synth.uneven_volumes(64, seed=1000, shapes_only=True)
+    subset = [int(i) for i in args.batch_volumes.split(",")] if args.batch_volumes else list(range(64))
+    mine = [subset[i] for i in shard.volumes_of_rank(len(subset), rank, world)]
+    allv = [v for i, v in enumerate(synth.uneven_volumes(64, seed=1000, shapes_only=True)) if i in set(subset)]
     vols = synth.uneven_volumes(64, seed=1000, device=dev, only=mine)
     ests = [torch.empty((v["P"], v["H"], v["W"]), device=dev) for v in vols]
     batch = mvd.mvd_batch_create([{"stacks": v["stacks"], "psfs": v["psfs"], "iters": v["iters"], "estimate": e}
                                   for v, e in zip(vols, ests)], order="sequential")
     t0 = time.perf_counter()
-    mvd.mvd_batch_tune(batch)
+    if args.batch_schedule == "auto":
+        mvd.mvd_batch_tune(batch)
+    else:
+        mvd.mvd_batch_set_schedule(batch, args.batch_schedule)
     tune_s = time.perf_counter() - t0
     for _ in range(args.warmup):
         mvd.mvd_batch_run(batch)
@@ -778,8 +786,10 @@ def run_batch(args):
     line = {"metric": METRIC, "value": units / (ms / 1e3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "strong",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "64 uneven volumes per GPU, one captured CUDA graph, fused-route volumes on "
-                                   "the persistent queue when the tuner keeps it (see run_batch)",
+            "config": {"workload": ("64 uneven volumes per GPU, one captured CUDA graph, fused-route volumes on "
+                                    "the persistent queue when the tuner keeps it (see run_batch)")
+                       if len(subset) == 64 else f"volumes {subset} of the 64-volume batch (see run_batch)",
+                       "schedule": args.batch_schedule,
                        "voxels": int(sum(v["P"] * v["H"] * v["W"] for v in allv)),
                        "voxel_view_iterations": int(units), "order": "sequential",
                        "l2": "inputs larger than L2",

@@ -103,8 +103,11 @@ __global__ void __launch_bounds__(kThreads) fft_cols_kernel(const FftArgs a, int
             load(a.S0 + p * splane, b0, c0);
             __syncthreads();
             if (live) fft_warp<false>(b0 + warp * LD, b1 + warp * LD, *pl, tw, lane);
-            float2 *Psi = odd ? b1 : b0;                    // the other two do the inverse transforms
-            float2 *w0 = odd ? b0 : b1, *w1 = b2;
+            float2 *Psi = odd ? b1 : b0;
+            // several views: the other two buffers do the inverse transforms;
+            // one view: Psi . H_v in place, the other buffer as scratch
+            const bool three = a.view_hi - a.view_lo > 1;
+            float2 *w0 = three ? (odd ? b0 : b1) : Psi, *w1 = three ? b2 : (odd ? b0 : b1);
             float2 *res = odd ? w1 : w0;
             for (int v = a.view_lo; v < a.view_hi; ++v) {
                 if (live) {
@@ -141,19 +144,31 @@ __global__ void __launch_bounds__(kThreads) fft_cols_kernel(const FftArgs a, int
 
 cudaError_t launch_cols(int mode, const FftArgs &a, int sms, cudaStream_t s) {
     const int LD = col_pitch(a.Ly);
-    const int nbuf = mode == COL_BLUR ? 3 : 2;
+    // the blur keeps Psi for every view of the launch: a third buffer only
+    // when there is more than one
+    const int nbuf = mode == COL_BLUR && a.view_hi - a.view_lo > 1 ? 3 : 2;
     const size_t fixed = kPlanBytes + static_cast<size_t>((a.py.tw_len + 1) & ~1) * sizeof(float2);
     const size_t per_col = static_cast<size_t>(nbuf) * LD * sizeof(float2);
-    const int CB = static_cast<int>(std::min<size_t>(kWarps, (kSmemCap - fixed) / per_col));
-    if (CB < 1) return cudaErrorInvalidValue;
-    const size_t smem = fixed + CB * per_col;
+    const int max_cb = static_cast<int>(std::min<size_t>(kWarps, (kSmemCap - fixed) / per_col));
+    if (max_cb < 1) return cudaErrorInvalidValue;
     const void *fn = mode == COL_BLUR ? reinterpret_cast<const void *>(fft_cols_kernel<COL_BLUR>)
                                       : reinterpret_cast<const void *>(fft_cols_kernel<COL_CORR>);
-    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         static_cast<int>(fixed + max_cb * per_col));
     if (e != cudaSuccess) return e;
-    int per_sm = 0;
-    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, 32 * CB, smem)) != cudaSuccess) return e;
+    // columns (warps) per CTA: the count that keeps the most warps resident per SM
+    int CB = 0, per_sm = 0;
+    for (int w = max_cb; w >= 1; --w) {
+        int b = 0;
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, fn, 32 * w, fixed + w * per_col)) != cudaSuccess)
+            return e;
+        if (b * w > per_sm * CB) {
+            CB = w;
+            per_sm = b;
+        }
+    }
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    const size_t smem = fixed + CB * per_col;
     const int nblk = (a.Lc + CB - 1) / CB;
     const long long items = static_cast<long long>(a.P) * nblk;
     const int grid = static_cast<int>(std::min<long long>(items, static_cast<long long>(per_sm) * std::max(sms, 1)));

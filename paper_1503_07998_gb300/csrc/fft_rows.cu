@@ -229,17 +229,28 @@ cudaError_t launch_rows(int mode, const FftArgs &a, int sms, cudaStream_t s) {
     const int use_prod = mode == ROW_UPDATE && a.view_hi - a.view_lo > 1;
     const size_t fixed = kPlanBytes + static_cast<size_t>((a.px.tw_len + 1) & ~1) * sizeof(float2);
     const size_t per_warp = 2ull * buf_len(a.Lx) * sizeof(float2) + (use_prod ? 2ull * a.W * sizeof(float) : 0);
-    const int nw = static_cast<int>(std::min<size_t>(kWarps, (kSmemCap - fixed) / per_warp));
-    if (nw < 1) return cudaErrorInvalidValue;
-    const size_t smem = fixed + nw * per_warp;
+    const int max_nw = static_cast<int>(std::min<size_t>(kWarps, (kSmemCap - fixed) / per_warp));
+    if (max_nw < 1) return cudaErrorInvalidValue;
     const void *fn = mode == ROW_PSI     ? reinterpret_cast<const void *>(fft_rows_kernel<ROW_PSI>)
                      : mode == ROW_RATIO ? reinterpret_cast<const void *>(fft_rows_kernel<ROW_RATIO>)
                                          : reinterpret_cast<const void *>(fft_rows_kernel<ROW_UPDATE>);
-    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         static_cast<int>(fixed + max_nw * per_warp));
     if (e != cudaSuccess) return e;
-    int per_sm = 0;
-    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, 32 * nw, smem)) != cudaSuccess) return e;
+    // warps per CTA: the count that keeps the most warps resident per SM
+    // (registers and shared memory both limit the CTAs per SM)
+    int nw = 0, per_sm = 0;
+    for (int w = max_nw; w >= 1; --w) {
+        int b = 0;
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, fn, 32 * w, fixed + w * per_warp)) != cudaSuccess)
+            return e;
+        if (b * w > per_sm * nw) {
+            nw = w;
+            per_sm = b;
+        }
+    }
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    const size_t smem = fixed + nw * per_warp;
     const long long items = static_cast<long long>(a.P) * pairs;
     const long long need = (items + nw - 1) / nw;
     const int grid = static_cast<int>(std::min<long long>(need, static_cast<long long>(per_sm) * std::max(sms, 1)));
