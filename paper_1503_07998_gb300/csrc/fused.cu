@@ -169,7 +169,9 @@ __device__ __forceinline__ TileCoord tile_coord(int t, int tiles_x, int tiles_y)
     return {p, ty * G::TY, (r - ty * tiles_x) * G::TX};
 }
 
-// Tile height of kernel B (32 rows, three CTAs per SM where they fit).
+// Tile heights: kernel A 0 (Geo's choice: 64 rows while two CTAs fit on an
+// SM, else 32), kernel B 32 rows with three CTAs per SM where they fit.
+constexpr int kTyA = 0;
 constexpr int kTyB = 32;
 
 // Persistent: each CTA walks tiles blockIdx.x, blockIdx.x + gridDim.x, ...
@@ -177,9 +179,9 @@ constexpr int kTyB = 32;
 // vertical pass of the current tile (the input tile is free from then on),
 // so the copy overlaps the last horizontal pass and the epilogue.
 template <int K>
-__global__ void __launch_bounds__(kThreads, Geo<K>::MIN_BLOCKS)
+__global__ void __launch_bounds__(kThreads, Geo<K, kTyA>::MIN_BLOCKS)
 blur_ratio_kernel(const __grid_constant__ KParams kp) {
-    using G = Geo<K>;
+    using G = Geo<K, kTyA>;
     const FusedArgs &a = kp.a;
     extern __shared__ __align__(128) unsigned char smem[];
     uint64_t *bar = reinterpret_cast<uint64_t *>(smem);
@@ -211,22 +213,22 @@ blur_ratio_kernel(const __grid_constant__ KParams kp) {
     __syncthreads();
     int t = blockIdx.x;
     if (use_tma && threadIdx.x == 0 && t < n_tiles) {
-        const TileCoord c = tile_coord<K>(t, tiles_x, tiles_y);
+        const TileCoord c = tile_coord<K, kTyA>(t, tiles_x, tiles_y);
         tma::mbar_arrive_expect_tx(bar, G::TILE_BYTES);
         tma::load_3d(tile, &kp.map, bar, c.x0 - G::R4, c.y0 - G::R, c.p);
     }
     uint32_t phase = 0;
     for (; t < n_tiles; t += gridDim.x) {
-        const TileCoord tc = tile_coord<K>(t, tiles_x, tiles_y);
+        const TileCoord tc = tile_coord<K, kTyA>(t, tiles_x, tiles_y);
         const int p = tc.p, y0 = tc.y0, x0 = tc.x0;
         if (use_tma) {
             if (!wait_tile(bar, phase, a, abort_flag)) return;
             phase ^= 1u;
         } else {
             if (a.psi_in)
-                load_tile_sw<K>(tile, a.psi_in + p * plane_px, 0.0f, y0, x0, a.H, a.W, a.circular);
+                load_tile_sw<K, kTyA>(tile, a.psi_in + p * plane_px, 0.0f, y0, x0, a.H, a.W, a.circular);
             else
-                fill_tile_const<K>(tile, __ldg(a.means + p), y0, x0, a.H, a.W, a.circular);
+                fill_tile_const<K, kTyA>(tile, __ldg(a.means + p), y0, x0, a.H, a.W, a.circular);
             __syncthreads();
         }
         const int t_next = t + gridDim.x;
@@ -255,12 +257,12 @@ blur_ratio_kernel(const __grid_constant__ KParams kp) {
             for (int q = 0; q < a.ft.rank[lead]; ++q) {
                 const float *tq = kp.taps + (a.ft.tap_off[lead] + q) * 2 * K;
                 if (sm & 1u)
-                    vertical_pass<K, short_taps<K>()>(tile, stage, tq);
+                    vertical_pass<K, short_taps<K>(), kTyA>(tile, stage, tq);
                 else
-                    vertical_pass<K>(tile, stage, tq);
+                    vertical_pass<K, K, kTyA>(tile, stage, tq);
                 __syncthreads();
                 if (--left == 0 && use_tma && threadIdx.x == 0 && t_next < n_tiles) {
-                    const TileCoord c = tile_coord<K>(t_next, tiles_x, tiles_y);
+                    const TileCoord c = tile_coord<K, kTyA>(t_next, tiles_x, tiles_y);
                     tma::fence_proxy_async_smem();
                     tma::mbar_arrive_expect_tx(bar, G::TILE_BYTES);
                     tma::load_3d(tile, &kp.map, bar, c.x0 - G::R4, c.y0 - G::R, c.p);
@@ -270,7 +272,7 @@ blur_ratio_kernel(const __grid_constant__ KParams kp) {
 #pragma unroll
                     for (int h = 0; h < G::H_PER_THREAD; ++h) {
                         int y, x;
-                        item_origin<K>(h, y0, x0, y, x);
+                        item_origin<K, kTyA>(h, y0, x0, y, x);
                         if (y < a.H && x < a.W) {
                             const uint4 *src = reinterpret_cast<const uint4 *>(
                                 static_cast<const uint16_t *>(a.phi) + vplane + static_cast<long long>(y) * a.W + x);
@@ -280,9 +282,9 @@ blur_ratio_kernel(const __grid_constant__ KParams kp) {
                     }
                 }
                 if (sm & 2u)
-                    horizontal_pass<K, short_taps<K>()>(stage, tq + K, acc);
+                    horizontal_pass<K, short_taps<K>(), kTyA>(stage, tq + K, acc);
                 else
-                    horizontal_pass<K>(stage, tq + K, acc);
+                    horizontal_pass<K, K, kTyA>(stage, tq + K, acc);
                 __syncthreads();
             }
             // ratio epilogue per item (16 consecutive pixels of one row)
@@ -292,7 +294,7 @@ blur_ratio_kernel(const __grid_constant__ KParams kp) {
 #pragma unroll
                 for (int h = 0; h < G::H_PER_THREAD; ++h) {
                     int y, x;
-                    item_origin<K>(h, y0, x0, y, x);
+                    item_origin<K, kTyA>(h, y0, x0, y, x);
                     if (y >= a.H || x >= a.W) continue;
                     const int n = min(kNC, a.W - x);
                     const long long off = vplane + static_cast<long long>(y) * a.W + x;
@@ -512,19 +514,19 @@ inline bool aligned16(const void *p) { return reinterpret_cast<uintptr_t>(p) % 1
 template <int K, int TYF>
 cudaError_t launch_one(const FusedArgs &a, int which, cudaStream_t s) {
     using G = Geo<K, TYF>;
-    // the shared-memory opt-in is per function and device
-    static unsigned long long attr_set = 0;
+    // the shared-memory opt-in is per function (kernel A or B) and device
+    static unsigned long long attr_set[2] = {0, 0};
     int dev = 0;
     cudaGetDevice(&dev);
     const unsigned long long bit = 1ull << (dev & 63);
-    if (!(attr_set & bit)) {
+    if (!(attr_set[which] & bit)) {
         const cudaError_t e =
             which == 0 ? cudaFuncSetAttribute(blur_ratio_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                               G::SMEM_BYTES)
                        : cudaFuncSetAttribute(correlate_update_kernel<K>,
                                               cudaFuncAttributeMaxDynamicSharedMemorySize, G::SMEM_BYTES);
         if (e != cudaSuccess) return e;
-        attr_set |= bit;
+        attr_set[which] |= bit;
     }
     // persistent grid: as many CTAs as fit on the device at once, at most one per tile
     static int resident[64][2] = {};
@@ -578,7 +580,7 @@ cudaError_t dispatch(const FusedArgs &a, int which, cudaStream_t s) {
     switch (a.ft.K) {
 #define MVD_CASE(k) \
     case k:         \
-        return which == 0 ? launch_one<k, 0>(a, 0, s) : launch_one<k, kTyB>(a, 1, s);
+        return which == 0 ? launch_one<k, kTyA>(a, 0, s) : launch_one<k, kTyB>(a, 1, s);
         MVD_FUSED_CASES(MVD_CASE)
 #undef MVD_CASE
         default:
