@@ -495,6 +495,8 @@ mvd_status run_fft(mvd_ctx *c, const void *data, mvd_dtype dt, float *est, int P
     a.u16 = dt == MVD_U16;
     a.S0 = f.S0.as<float2>();
     a.T = f.T.as<float2>();
+    a.err = c->status.as<int>();
+    a.wait_budget = c->wait_budget;
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);

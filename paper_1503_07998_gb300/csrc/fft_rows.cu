@@ -12,6 +12,7 @@
 
 #include "fft_engine.cuh"
 #include "mvd_internal.h"
+#include "tma.cuh"
 
 namespace mvd {
 namespace fftr {
@@ -222,10 +223,188 @@ __global__ void __launch_bounds__(kThreads) fft_rows_kernel(const FftArgs a, int
     }
 }
 
+// The ratio pass with every job's inputs prefetched.  A job is (row pair,
+// view): its two stored half-spectrum rows and its two data rows.  Lane 0 of
+// each warp copies the next job's rows into the warp's staging buffers with
+// bulk async copies (one per row pair) as soon as the current job has
+// consumed them, so they land while the warp transforms; each buffer has its
+// own mbarrier.  Waits are bounded: an expired wait sets the status word,
+// and the warp drains its copies in flight and stops.  Taken when the data
+// rows are whole 16-byte units (W * element size a multiple of 16).
+constexpr int kBarBytes = kWarps * 16;
+constexpr long long kDrainBudget = 4000000000LL;
+
+__host__ __device__ inline int rup16(int b) { return (b + 15) & ~15; }
+
+__global__ void __launch_bounds__(kThreads) fft_rows_ratio_pf_kernel(const FftArgs a, int pairs, int es) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    FftPlan1 *pl = reinterpret_cast<FftPlan1 *>(smem);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + kPlanBytes);
+    float2 *tw = reinterpret_cast<float2 *>(smem + kPlanBytes + kBarBytes);
+    const int twl = (a.px.tw_len + 1) & ~1;
+    const int Lx = a.Lx, W = a.W, Lc = a.Lc;
+    const int BL = buf_len(Lx), SL = 2 * a.LcP, PB = rup16(2 * W * es);
+    const size_t per_warp = static_cast<size_t>(2 * BL + SL) * sizeof(float2) + PB;
+    const int nw = blockDim.x >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    unsigned char *wb = reinterpret_cast<unsigned char *>(tw + twl) + warp * per_warp;
+    float2 *x = reinterpret_cast<float2 *>(wb);
+    float2 *y = x + BL;
+    float2 *st = y + BL;                                           // staged half spectra, 2 rows of LcP
+    unsigned char *ph = reinterpret_cast<unsigned char *>(st + SL);   // staged data, 2 rows of W
+    uint64_t *barT = bars + 2 * warp, *barP = barT + 1;
+    if (threadIdx.x == 0) *pl = a.px;
+    for (int i = threadIdx.x; i < a.px.tw_len; i += blockDim.x) tw[i] = a.tw_x[i];
+    if (lane == 0) {
+        tma::mbar_init(barT, 1);
+        tma::mbar_init(barP, 1);
+        tma::fence_barrier_init();
+    }
+    __syncthreads();
+
+    const long long plane = static_cast<long long>(a.H) * W;
+    const long long splane = static_cast<long long>(a.H) * a.LcP;
+    const long long items = static_cast<long long>(a.P) * pairs;
+    const long long stride = static_cast<long long>(gridDim.x) * nw;
+    const long long first = static_cast<long long>(blockIdx.x) * nw + warp;
+    // lane 0: copy job (it, v)'s half-spectrum rows (T) and/or data rows (P)
+    auto issue = [&](long long it, int v, bool rows_T, bool rows_P) {
+        if (lane != 0) return;
+        const int p = static_cast<int>(it / pairs);
+        const int y0 = 2 * static_cast<int>(it - static_cast<long long>(p) * pairs);
+        const int nr = y0 + 1 < a.H ? 2 : 1;
+        const long long vp = static_cast<long long>(v) * a.P + p;
+        if (rows_T) {
+            const uint32_t bytes = static_cast<uint32_t>(nr * a.LcP * sizeof(float2));
+            tma::fence_proxy_async_smem();
+            tma::mbar_arrive_expect_tx(barT, bytes);
+            tma::bulk_g2s(st, a.T + vp * splane + static_cast<long long>(y0) * a.LcP, bytes, barT);
+        }
+        if (rows_P) {
+            const uint32_t bytes = static_cast<uint32_t>(nr * W * es);
+            tma::fence_proxy_async_smem();
+            tma::mbar_arrive_expect_tx(barP, bytes);
+            tma::bulk_g2s(ph, static_cast<const unsigned char *>(a.phi) + (vp * plane + static_cast<long long>(y0) * W) * es,
+                          bytes, barP);
+        }
+    };
+    const long long budget = a.wait_budget < 0 ? kDrainBudget : a.wait_budget;
+    uint32_t phT = 0, phP = 0;
+    bool pendT = false, pendP = false;
+    // every lane waits; false after an expired (or injected) timeout, with the
+    // warp's copies in flight drained
+    auto wait = [&](uint64_t *bar, uint32_t &ph, bool &pend) -> bool {
+        const bool ok = tma::mbar_wait_bounded(bar, ph, budget) && a.wait_budget >= 0;
+        if (__all_sync(0xffffffffu, ok)) {
+            pend = false;
+            ph ^= 1u;
+            return true;
+        }
+        if (lane == 0) atomicOr(a.err, kDevTimeout);
+        if (pendT) tma::mbar_wait_bounded(barT, phT, kDrainBudget);
+        if (pendP) tma::mbar_wait_bounded(barP, phP, kDrainBudget);
+        return false;
+    };
+    if (first < items) {
+        issue(first, a.view_lo, true, true);
+        pendT = pendP = true;
+    }
+    for (long long it = first; it < items; it += stride) {
+        const int p = static_cast<int>(it / pairs);
+        const int y0 = 2 * static_cast<int>(it - static_cast<long long>(p) * pairs);
+        const bool have1 = y0 + 1 < a.H;
+        for (int v = a.view_lo; v < a.view_hi; ++v) {
+            long long nit = it;
+            int nv = v + 1;
+            if (nv >= a.view_hi) {
+                nit = it + stride;
+                nv = a.view_lo;
+            }
+            const bool next = nit < items;
+            float2 *T = a.T + (static_cast<long long>(v) * a.P + p) * splane;
+            // half spectra -> full spectrum of the packed pair
+            if (!wait(barT, phT, pendT)) return;
+            for (int k = lane; k < Lx; k += 32) {
+                const int kk = k < Lc ? k : Lx - k;
+                float2 A = st[kk], B = have1 ? st[a.LcP + kk] : make_float2(0.f, 0.f);
+                if (k >= Lc) {
+                    A.y = -A.y;
+                    B.y = -B.y;
+                }
+                x[k] = make_float2(A.x - B.y, A.y + B.x);
+            }
+            __syncwarp();
+            if (next) {
+                issue(nit, nv, true, false);
+                pendT = true;
+            }
+            float2 *z = fft_warp<true>(x, y, *pl, tw, lane);
+            float2 *zo = (z == x) ? y : x;
+            if (!wait(barP, phP, pendP)) return;
+            for (int i = lane; i < Lx; i += 32) {
+                float r0 = 0.f, r1 = 0.f;
+                if (i < W) {
+                    const float2 b = z[i];
+                    const float d0 = es == 2 ? static_cast<float>(reinterpret_cast<const uint16_t *>(ph)[i])
+                                             : reinterpret_cast<const float *>(ph)[i];
+                    r0 = __fdiv_rn(d0, fmaxf(b.x, a.eps));
+                    if (have1) {
+                        const float d1 = es == 2 ? static_cast<float>(reinterpret_cast<const uint16_t *>(ph)[W + i])
+                                                 : reinterpret_cast<const float *>(ph)[W + i];
+                        r1 = __fdiv_rn(d1, fmaxf(b.y, a.eps));
+                    }
+                }
+                zo[i] = make_float2(r0, r1);
+            }
+            __syncwarp();
+            if (next) {
+                issue(nit, nv, false, true);
+                pendP = true;
+            }
+            const float2 *Z = fft_warp<false>(zo, z, *pl, tw, lane);
+            store_pair_spectrum(a, Z, T, y0, have1, lane);
+            __syncwarp();
+        }
+    }
+}
+
 }  // namespace
+
+// The prefetching ratio pass (data rows in whole 16-byte units).
+cudaError_t launch_ratio_pf(const FftArgs &a, int sms, cudaStream_t s) {
+    const int pairs = (a.H + 1) / 2;
+    const int es = a.u16 ? 2 : 4;
+    const size_t fixed = kPlanBytes + kBarBytes + static_cast<size_t>((a.px.tw_len + 1) & ~1) * sizeof(float2);
+    const size_t per_warp = static_cast<size_t>(2 * buf_len(a.Lx) + 2 * a.LcP) * sizeof(float2) + rup16(2 * a.W * es);
+    const int max_nw = static_cast<int>(std::min<size_t>(kWarps, (kSmemCap - fixed) / per_warp));
+    if (max_nw < 1) return cudaErrorInvalidValue;
+    const void *fn = reinterpret_cast<const void *>(fft_rows_ratio_pf_kernel);
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         static_cast<int>(fixed + max_nw * per_warp));
+    if (e != cudaSuccess) return e;
+    int nw = 0, per_sm = 0;
+    for (int w = max_nw; w >= 1; --w) {
+        int b = 0;
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, fn, 32 * w, fixed + w * per_warp)) != cudaSuccess)
+            return e;
+        if (b * w > per_sm * nw) {
+            nw = w;
+            per_sm = b;
+        }
+    }
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    const long long items = static_cast<long long>(a.P) * pairs;
+    const long long need = (items + nw - 1) / nw;
+    const int grid = static_cast<int>(std::min<long long>(need, static_cast<long long>(per_sm) * std::max(sms, 1)));
+    if (grid < 1) return cudaSuccess;
+    fft_rows_ratio_pf_kernel<<<grid, 32 * nw, fixed + nw * per_warp, s>>>(a, pairs, es);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_rows(int mode, const FftArgs &a, int sms, cudaStream_t s) {
     const int pairs = (a.H + 1) / 2;
+    if (mode == ROW_RATIO && a.err && (static_cast<long long>(a.W) * (a.u16 ? 2 : 4)) % 16 == 0 &&
+        reinterpret_cast<uintptr_t>(a.phi) % 16 == 0)
+        return launch_ratio_pf(a, sms, s);
     const int use_prod = mode == ROW_UPDATE && a.view_hi - a.view_lo > 1;
     const size_t fixed = kPlanBytes + static_cast<size_t>((a.px.tw_len + 1) & ~1) * sizeof(float2);
     const size_t per_warp = 2ull * buf_len(a.Lx) * sizeof(float2) + (use_prod ? 2ull * a.W * sizeof(float) : 0);

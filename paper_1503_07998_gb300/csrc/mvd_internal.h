@@ -254,6 +254,8 @@ struct FftArgs {
     int u16;
     float2 *S0;                        // [P][H][LcP]
     float2 *T;                         // [V][P][H][LcP]
+    int *err;                          // device status word (kDevTimeout on an expired copy wait)
+    long long wait_budget;             // clock cycles a copy wait may spin
 };
 bool smooth_size(int n, int *out);
 bool radix_list(int n, int *rad, int *nrad);

@@ -60,6 +60,16 @@ __device__ __forceinline__ void load_3d(void *dst, const CUtensorMap *map, uint6
         : "memory");
 }
 
+// Untiled bulk copy of `bytes` (a multiple of 16) from global to shared
+// memory, both 16-byte aligned, completing on `bar` (expect the bytes first).
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(src)), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
 __device__ __forceinline__ void load_4d(void *dst, const CUtensorMap *map, uint64_t *bar, int c0, int c1, int c2,
                                         int c3) {
     asm volatile(

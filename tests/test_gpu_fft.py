@@ -108,3 +108,31 @@ def test_autotune_picks_a_route_and_keeps_parity(mvd, tmp_path, monkeypatch):
         ctx.close()
     ref = oracle.rl_planes(c.phi, c.psfs, 4, eps=1e-6, route="fft")
     assert_parity(est.cpu().numpy(), ref, what=f"autotuned ({route})")
+
+
+def test_injected_copy_timeout_is_reported_and_context_recovers(mvd):
+    """The ratio pass prefetches each job's rows with bulk async copies on
+    bounded mbarrier waits: a negative wait budget makes them report a
+    timeout (MVD_ERR_TIMEOUT) once the copies land; with the default budget
+    the same context is correct."""
+    c = synth.plane_case(seed=12, H=96, W=128, n_planes=2, n_blobs=40, K=21, sigma_axial=5.0,
+                         sigma_lateral=1.4, dtype=np.uint16)
+    V, P, H, W = c.phi.shape
+    ctx = mvd.mvd_create(V, c.psfs, 21, H, W, 3, "zero", 1e-6)
+    try:
+        mvd.mvd_set_algo(ctx, "fft")
+        d = torch.from_numpy(c.phi).cuda()
+        est = torch.empty((P, H, W), device="cuda")
+        mvd.mvd_set_wait_budget(ctx, -1)
+        mvd.mvd_deconvolve_planes(ctx, d, est)
+        with pytest.raises(mvd.MvdError) as ei:
+            mvd.mvd_device_status(ctx)
+        assert ei.value.status == mvd.MVD_ERR_TIMEOUT
+        mvd.mvd_set_wait_budget(ctx, 0)
+        mvd.mvd_deconvolve_planes(ctx, d, est)
+        mvd.mvd_device_status(ctx)
+        got = est.cpu().numpy()
+    finally:
+        ctx.close()
+    ref = oracle.rl_planes(c.phi, c.psfs, 3, eps=1e-6, route="fft")
+    assert_parity(got, ref, what="fft after an injected timeout")
