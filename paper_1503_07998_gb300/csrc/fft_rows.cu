@@ -223,34 +223,39 @@ __global__ void __launch_bounds__(kThreads) fft_rows_kernel(const FftArgs a, int
     }
 }
 
-// The ratio pass with every job's inputs prefetched.  A job is (row pair,
-// view): its two stored half-spectrum rows and its two data rows.  Lane 0 of
-// each warp copies the next job's rows into the warp's staging buffers with
-// bulk async copies (one per row pair) as soon as the current job has
-// consumed them, so they land while the warp transforms; each buffer has its
-// own mbarrier.  Waits are bounded: an expired wait sets the status word,
-// and the warp drains its copies in flight and stops.  Taken when the data
-// rows are whole 16-byte units (W * element size a multiple of 16).
+// Row passes with every job's inputs prefetched.  A job is (row pair,
+// view) for the ratio pass and a row pair for the others; its inputs are the
+// two stored half-spectrum rows (ratio, update) and two rows of the data
+// (ratio) or of the estimate (update, estimate; none on the first
+// iteration, which starts from the plane means).  Lane 0 of each warp copies
+// the next job's rows into the warp's staging buffers with bulk async copies
+// (one per row pair) as soon as the current job has consumed them, so they
+// land while the warp transforms; each buffer has its own mbarrier.  Waits
+// are bounded: an expired wait sets the status word, and the warp drains its
+// copies in flight and stops.  Taken when those rows are whole 16-byte units
+// and, for the update, when a launch has one view (no product buffer).
 constexpr int kBarBytes = kWarps * 16;
 constexpr long long kDrainBudget = 4000000000LL;
 
 __host__ __device__ inline int rup16(int b) { return (b + 15) & ~15; }
 
-__global__ void __launch_bounds__(kThreads) fft_rows_ratio_pf_kernel(const FftArgs a, int pairs, int es) {
+template <int MODE>
+__global__ void __launch_bounds__(kThreads) fft_rows_pf_kernel(const FftArgs a, int pairs, int es) {
+    constexpr bool kUsesT = MODE != ROW_PSI;
     extern __shared__ __align__(16) unsigned char smem[];
     FftPlan1 *pl = reinterpret_cast<FftPlan1 *>(smem);
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem + kPlanBytes);
     float2 *tw = reinterpret_cast<float2 *>(smem + kPlanBytes + kBarBytes);
     const int twl = (a.px.tw_len + 1) & ~1;
     const int Lx = a.Lx, W = a.W, Lc = a.Lc;
-    const int BL = buf_len(Lx), SL = 2 * a.LcP, PB = rup16(2 * W * es);
+    const int BL = buf_len(Lx), SL = kUsesT ? 2 * a.LcP : 0, PB = rup16(2 * W * es);
     const size_t per_warp = static_cast<size_t>(2 * BL + SL) * sizeof(float2) + PB;
     const int nw = blockDim.x >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     unsigned char *wb = reinterpret_cast<unsigned char *>(tw + twl) + warp * per_warp;
     float2 *x = reinterpret_cast<float2 *>(wb);
     float2 *y = x + BL;
-    float2 *st = y + BL;                                           // staged half spectra, 2 rows of LcP
-    unsigned char *ph = reinterpret_cast<unsigned char *>(st + SL);   // staged data, 2 rows of W
+    float2 *st = y + BL;                                              // staged half spectra, 2 rows of LcP
+    unsigned char *ph = reinterpret_cast<unsigned char *>(st + SL);   // staged data / estimate, 2 rows of W
     uint64_t *barT = bars + 2 * warp, *barP = barT + 1;
     if (threadIdx.x == 0) *pl = a.px;
     for (int i = threadIdx.x; i < a.px.tw_len; i += blockDim.x) tw[i] = a.tw_x[i];
@@ -266,7 +271,9 @@ __global__ void __launch_bounds__(kThreads) fft_rows_ratio_pf_kernel(const FftAr
     const long long items = static_cast<long long>(a.P) * pairs;
     const long long stride = static_cast<long long>(gridDim.x) * nw;
     const long long first = static_cast<long long>(blockIdx.x) * nw + warp;
-    // lane 0: copy job (it, v)'s half-spectrum rows (T) and/or data rows (P)
+    const int v_hi = MODE == ROW_RATIO ? a.view_hi : a.view_lo + 1;   // one job per row pair otherwise
+    const bool usesP = MODE == ROW_RATIO || a.psi_in != nullptr;
+    // lane 0: copy job (it, v)'s half-spectrum rows and/or its other rows
     auto issue = [&](long long it, int v, bool rows_T, bool rows_P) {
         if (lane != 0) return;
         const int p = static_cast<int>(it / pairs);
@@ -281,10 +288,13 @@ __global__ void __launch_bounds__(kThreads) fft_rows_ratio_pf_kernel(const FftAr
         }
         if (rows_P) {
             const uint32_t bytes = static_cast<uint32_t>(nr * W * es);
+            const unsigned char *src =
+                MODE == ROW_RATIO
+                    ? static_cast<const unsigned char *>(a.phi) + (vp * plane + static_cast<long long>(y0) * W) * es
+                    : reinterpret_cast<const unsigned char *>(a.psi_in + p * plane + static_cast<long long>(y0) * W);
             tma::fence_proxy_async_smem();
             tma::mbar_arrive_expect_tx(barP, bytes);
-            tma::bulk_g2s(ph, static_cast<const unsigned char *>(a.phi) + (vp * plane + static_cast<long long>(y0) * W) * es,
-                          bytes, barP);
+            tma::bulk_g2s(ph, src, bytes, barP);
         }
     };
     const long long budget = a.wait_budget < 0 ? kDrainBudget : a.wait_budget;
@@ -292,11 +302,11 @@ __global__ void __launch_bounds__(kThreads) fft_rows_ratio_pf_kernel(const FftAr
     bool pendT = false, pendP = false;
     // every lane waits; false after an expired (or injected) timeout, with the
     // warp's copies in flight drained
-    auto wait = [&](uint64_t *bar, uint32_t &ph, bool &pend) -> bool {
-        const bool ok = tma::mbar_wait_bounded(bar, ph, budget) && a.wait_budget >= 0;
+    auto wait = [&](uint64_t *bar, uint32_t &pha, bool &pend) -> bool {
+        const bool ok = tma::mbar_wait_bounded(bar, pha, budget) && a.wait_budget >= 0;
         if (__all_sync(0xffffffffu, ok)) {
             pend = false;
-            ph ^= 1u;
+            pha ^= 1u;
             return true;
         }
         if (lane == 0) atomicOr(a.err, kDevTimeout);
@@ -304,64 +314,98 @@ __global__ void __launch_bounds__(kThreads) fft_rows_ratio_pf_kernel(const FftAr
         if (pendP) tma::mbar_wait_bounded(barP, phP, kDrainBudget);
         return false;
     };
+    auto staged = [&](int i) -> float {   // element i of the staged data / estimate rows
+        return es == 2 ? static_cast<float>(reinterpret_cast<const uint16_t *>(ph)[i])
+                       : reinterpret_cast<const float *>(ph)[i];
+    };
     if (first < items) {
-        issue(first, a.view_lo, true, true);
-        pendT = pendP = true;
+        issue(first, a.view_lo, kUsesT, usesP);
+        pendT = kUsesT;
+        pendP = usesP;
     }
     for (long long it = first; it < items; it += stride) {
         const int p = static_cast<int>(it / pairs);
         const int y0 = 2 * static_cast<int>(it - static_cast<long long>(p) * pairs);
         const bool have1 = y0 + 1 < a.H;
-        for (int v = a.view_lo; v < a.view_hi; ++v) {
+        const float m = a.psi_in ? 0.0f : __ldg(a.means + p);
+        for (int v = a.view_lo; v < v_hi; ++v) {
             long long nit = it;
             int nv = v + 1;
-            if (nv >= a.view_hi) {
+            if (nv >= v_hi) {
                 nit = it + stride;
                 nv = a.view_lo;
             }
             const bool next = nit < items;
-            float2 *T = a.T + (static_cast<long long>(v) * a.P + p) * splane;
-            // half spectra -> full spectrum of the packed pair
-            if (!wait(barT, phT, pendT)) return;
-            for (int k = lane; k < Lx; k += 32) {
-                const int kk = k < Lc ? k : Lx - k;
-                float2 A = st[kk], B = have1 ? st[a.LcP + kk] : make_float2(0.f, 0.f);
-                if (k >= Lc) {
-                    A.y = -A.y;
-                    B.y = -B.y;
+            if constexpr (MODE == ROW_PSI) {
+                // the two estimate rows -> forward row FFT -> half spectra S0
+                if (usesP && !wait(barP, phP, pendP)) return;
+                for (int i = lane; i < Lx; i += 32) {
+                    float r0 = 0.f, r1 = 0.f;
+                    if (i < W) {
+                        r0 = usesP ? staged(i) : m;
+                        if (have1) r1 = usesP ? staged(W + i) : m;
+                    }
+                    x[i] = make_float2(r0, r1);
                 }
-                x[k] = make_float2(A.x - B.y, A.y + B.x);
-            }
-            __syncwarp();
-            if (next) {
-                issue(nit, nv, true, false);
-                pendT = true;
-            }
-            float2 *z = fft_warp<true>(x, y, *pl, tw, lane);
-            float2 *zo = (z == x) ? y : x;
-            if (!wait(barP, phP, pendP)) return;
-            for (int i = lane; i < Lx; i += 32) {
-                float r0 = 0.f, r1 = 0.f;
-                if (i < W) {
-                    const float2 b = z[i];
-                    const float d0 = es == 2 ? static_cast<float>(reinterpret_cast<const uint16_t *>(ph)[i])
-                                             : reinterpret_cast<const float *>(ph)[i];
-                    r0 = __fdiv_rn(d0, fmaxf(b.x, a.eps));
-                    if (have1) {
-                        const float d1 = es == 2 ? static_cast<float>(reinterpret_cast<const uint16_t *>(ph)[W + i])
-                                                 : reinterpret_cast<const float *>(ph)[W + i];
-                        r1 = __fdiv_rn(d1, fmaxf(b.y, a.eps));
+                __syncwarp();
+                if (next && usesP) {
+                    issue(nit, nv, false, true);
+                    pendP = true;
+                }
+                const float2 *Z = fft_warp<false>(x, y, *pl, tw, lane);
+                store_pair_spectrum(a, Z, a.S0 + p * splane, y0, have1, lane);
+            } else {
+                float2 *T = a.T + (static_cast<long long>(v) * a.P + p) * splane;
+                // half spectra -> full spectrum of the packed pair
+                if (!wait(barT, phT, pendT)) return;
+                for (int k = lane; k < Lx; k += 32) {
+                    const int kk = k < Lc ? k : Lx - k;
+                    float2 A = st[kk], B = have1 ? st[a.LcP + kk] : make_float2(0.f, 0.f);
+                    if (k >= Lc) {
+                        A.y = -A.y;
+                        B.y = -B.y;
+                    }
+                    x[k] = make_float2(A.x - B.y, A.y + B.x);
+                }
+                __syncwarp();
+                if (next) {
+                    issue(nit, nv, true, false);
+                    pendT = true;
+                }
+                float2 *z = fft_warp<true>(x, y, *pl, tw, lane);
+                if (usesP && !wait(barP, phP, pendP)) return;   // the data (ratio) or estimate (update) rows
+                if constexpr (MODE == ROW_RATIO) {
+                    float2 *zo = (z == x) ? y : x;
+                    for (int i = lane; i < Lx; i += 32) {
+                        float r0 = 0.f, r1 = 0.f;
+                        if (i < W) {
+                            const float2 b = z[i];
+                            r0 = __fdiv_rn(staged(i), fmaxf(b.x, a.eps));
+                            if (have1) r1 = __fdiv_rn(staged(W + i), fmaxf(b.y, a.eps));
+                        }
+                        zo[i] = make_float2(r0, r1);
+                    }
+                    __syncwarp();
+                    if (next) {
+                        issue(nit, nv, false, true);
+                        pendP = true;
+                    }
+                    const float2 *Z = fft_warp<false>(zo, z, *pl, tw, lane);
+                    store_pair_spectrum(a, Z, T, y0, have1, lane);
+                } else {   // ROW_UPDATE, one view: psi <- psi * c_v
+                    const long long o0 = p * plane + static_cast<long long>(y0) * W;
+                    for (int i = lane; i < W; i += 32) {
+                        const float2 c = z[i];
+                        a.psi_out[o0 + i] = (usesP ? staged(i) : m) * c.x;
+                        if (have1) a.psi_out[o0 + W + i] = (usesP ? staged(W + i) : m) * c.y;
+                    }
+                    __syncwarp();
+                    if (next && usesP) {   // the next row pair's estimate rows
+                        issue(nit, nv, false, true);
+                        pendP = true;
                     }
                 }
-                zo[i] = make_float2(r0, r1);
             }
-            __syncwarp();
-            if (next) {
-                issue(nit, nv, false, true);
-                pendP = true;
-            }
-            const float2 *Z = fft_warp<false>(zo, z, *pl, tw, lane);
-            store_pair_spectrum(a, Z, T, y0, have1, lane);
             __syncwarp();
         }
     }
@@ -369,15 +413,18 @@ __global__ void __launch_bounds__(kThreads) fft_rows_ratio_pf_kernel(const FftAr
 
 }  // namespace
 
-// The prefetching ratio pass (data rows in whole 16-byte units).
-cudaError_t launch_ratio_pf(const FftArgs &a, int sms, cudaStream_t s) {
+// The prefetching row passes (rows in whole 16-byte units).
+cudaError_t launch_rows_pf(int mode, const FftArgs &a, int sms, cudaStream_t s) {
     const int pairs = (a.H + 1) / 2;
-    const int es = a.u16 ? 2 : 4;
+    const int es = mode == ROW_RATIO ? (a.u16 ? 2 : 4) : 4;
+    const int SL = mode == ROW_PSI ? 0 : 2 * a.LcP;
     const size_t fixed = kPlanBytes + kBarBytes + static_cast<size_t>((a.px.tw_len + 1) & ~1) * sizeof(float2);
-    const size_t per_warp = static_cast<size_t>(2 * buf_len(a.Lx) + 2 * a.LcP) * sizeof(float2) + rup16(2 * a.W * es);
+    const size_t per_warp = static_cast<size_t>(2 * buf_len(a.Lx) + SL) * sizeof(float2) + rup16(2 * a.W * es);
     const int max_nw = static_cast<int>(std::min<size_t>(kWarps, (kSmemCap - fixed) / per_warp));
     if (max_nw < 1) return cudaErrorInvalidValue;
-    const void *fn = reinterpret_cast<const void *>(fft_rows_ratio_pf_kernel);
+    const void *fn = mode == ROW_PSI     ? reinterpret_cast<const void *>(fft_rows_pf_kernel<ROW_PSI>)
+                     : mode == ROW_RATIO ? reinterpret_cast<const void *>(fft_rows_pf_kernel<ROW_RATIO>)
+                                         : reinterpret_cast<const void *>(fft_rows_pf_kernel<ROW_UPDATE>);
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          static_cast<int>(fixed + max_nw * per_warp));
     if (e != cudaSuccess) return e;
@@ -396,15 +443,25 @@ cudaError_t launch_ratio_pf(const FftArgs &a, int sms, cudaStream_t s) {
     const long long need = (items + nw - 1) / nw;
     const int grid = static_cast<int>(std::min<long long>(need, static_cast<long long>(per_sm) * std::max(sms, 1)));
     if (grid < 1) return cudaSuccess;
-    fft_rows_ratio_pf_kernel<<<grid, 32 * nw, fixed + nw * per_warp, s>>>(a, pairs, es);
+    const size_t smem = fixed + nw * per_warp;
+    switch (mode) {
+        case ROW_PSI: fft_rows_pf_kernel<ROW_PSI><<<grid, 32 * nw, smem, s>>>(a, pairs, es); break;
+        case ROW_RATIO: fft_rows_pf_kernel<ROW_RATIO><<<grid, 32 * nw, smem, s>>>(a, pairs, es); break;
+        default: fft_rows_pf_kernel<ROW_UPDATE><<<grid, 32 * nw, smem, s>>>(a, pairs, es); break;
+    }
     return cudaGetLastError();
 }
 
 cudaError_t launch_rows(int mode, const FftArgs &a, int sms, cudaStream_t s) {
     const int pairs = (a.H + 1) / 2;
-    if (mode == ROW_RATIO && a.err && (static_cast<long long>(a.W) * (a.u16 ? 2 : 4)) % 16 == 0 &&
-        reinterpret_cast<uintptr_t>(a.phi) % 16 == 0)
-        return launch_ratio_pf(a, sms, s);
+    // prefetching passes where every staged row is a whole number of 16-byte units
+    const bool psi_ok = a.psi_in == nullptr || (a.W % 4 == 0 && reinterpret_cast<uintptr_t>(a.psi_in) % 16 == 0);
+    const bool pf = a.err != nullptr &&
+                    (mode == ROW_RATIO ? (static_cast<long long>(a.W) * (a.u16 ? 2 : 4)) % 16 == 0 &&
+                                             reinterpret_cast<uintptr_t>(a.phi) % 16 == 0
+                     : mode == ROW_UPDATE ? psi_ok && a.view_hi - a.view_lo == 1
+                                          : psi_ok);
+    if (pf) return launch_rows_pf(mode, a, sms, s);
     const int use_prod = mode == ROW_UPDATE && a.view_hi - a.view_lo > 1;
     const size_t fixed = kPlanBytes + static_cast<size_t>((a.px.tw_len + 1) & ~1) * sizeof(float2);
     const size_t per_warp = 2ull * buf_len(a.Lx) * sizeof(float2) + (use_prod ? 2ull * a.W * sizeof(float) : 0);
