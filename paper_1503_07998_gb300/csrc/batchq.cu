@@ -316,8 +316,7 @@ __global__ void __launch_bounds__(kThreads, 2) queue_kernel(const __grid_constan
                 const unsigned sm = v.short_mask[vv];
                 for (int t = 0; t < v.rank[vv]; ++t) {
                     const float *tq = taps + static_cast<long long>(v.tap_off[vv] + t) * 4 * KC;
-                    if (sm & 1u) fused::vertical_pass<KC, KS, kTyQ>(tile, stage, tq);
-                    else fused::vertical_pass<KC, KC, kTyQ>(tile, stage, tq);
+                    fused::vertical_pass_sel<KC, kTyQ>(sm & 1u, sm & 2u, tile, stage, tq);
                     __syncthreads();
                     if (sm & 2u) fused::horizontal_pass<KC, KS, kTyQ>(stage, tq + KC, acc);
                     else fused::horizontal_pass<KC, KC, kTyQ>(stage, tq + KC, acc);
@@ -343,8 +342,7 @@ __global__ void __launch_bounds__(kThreads, 2) queue_kernel(const __grid_constan
                 const unsigned sm = v.short_mask[vv];
                 if (v.crank[vv] == 1) {
                     const float *tq = taps + static_cast<long long>(v.ctap_off[vv]) * 4 * KC + 2 * KC;
-                    if (sm & 4u) fused::vertical_pass<KC, KS, kTyQ>(tile, stage, tq);
-                    else fused::vertical_pass<KC, KC, kTyQ>(tile, stage, tq);
+                    fused::vertical_pass_sel<KC, kTyQ>(sm & 4u, sm & 8u, tile, stage, tq);
                     __syncthreads();
                     if (sm & 8u) fused::horizontal_pass_mul<KC, KS, kTyQ>(stage, tq + KC, prod);
                     else fused::horizontal_pass_mul<KC, KC, kTyQ>(stage, tq + KC, prod);
@@ -355,8 +353,7 @@ __global__ void __launch_bounds__(kThreads, 2) queue_kernel(const __grid_constan
                     for (int j = 0; j < kNC; ++j) c[0][j] = 0.0f;
                     for (int t = 0; t < v.crank[vv]; ++t) {
                         const float *tq = taps + static_cast<long long>(v.ctap_off[vv] + t) * 4 * KC + 2 * KC;
-                        if (sm & 4u) fused::vertical_pass<KC, KS, kTyQ>(tile, stage, tq);
-                        else fused::vertical_pass<KC, KC, kTyQ>(tile, stage, tq);
+                        fused::vertical_pass_sel<KC, kTyQ>(sm & 4u, sm & 8u, tile, stage, tq);
                         __syncthreads();
                         if (sm & 8u) fused::horizontal_pass<KC, KS, kTyQ>(stage, tq + KC, c);
                         else fused::horizontal_pass<KC, KC, kTyQ>(stage, tq + KC, c);

@@ -256,10 +256,7 @@ blur_ratio_kernel(const __grid_constant__ KParams kp) {
             uint4 pf[G::H_PER_THREAD][2];
             for (int q = 0; q < a.ft.rank[lead]; ++q) {
                 const float *tq = kp.taps + (a.ft.tap_off[lead] + q) * 2 * K;
-                if (sm & 1u)
-                    vertical_pass<K, short_taps<K>(), kTyA>(tile, stage, tq);
-                else
-                    vertical_pass<K, K, kTyA>(tile, stage, tq);
+                vertical_pass_sel<K, kTyA>(sm & 1u, sm & 2u, tile, stage, tq);
                 __syncthreads();
                 if (--left == 0 && use_tma && threadIdx.x == 0 && t_next < n_tiles) {
                     const TileCoord c = tile_coord<K, kTyA>(t_next, tiles_x, tiles_y);
@@ -412,10 +409,7 @@ correlate_update_kernel(const __grid_constant__ KParams kp) {
             const unsigned sm = a.weights ? 0u : a.ft.short_mask[v];
             if (a.ft.crank[v] == 1 && !a.wnorm) {
                 const float *tq = kp.taps + a.ft.ctap_off[v] * 2 * K;
-                if (sm & 4u)
-                    vertical_pass<K, short_taps<K>(), kTyB>(tile, stage, tq);
-                else
-                    vertical_pass<K, K, kTyB>(tile, stage, tq);
+                vertical_pass_sel<K, kTyB>(sm & 4u, sm & 8u, tile, stage, tq);
                 __syncthreads();
                 prefetch_next();
                 if (sm & 8u)
@@ -431,10 +425,7 @@ correlate_update_kernel(const __grid_constant__ KParams kp) {
                     for (int j = 0; j < kNC; ++j) c[h][j] = 0.0f;
                 for (int q = 0; q < a.ft.crank[v]; ++q) {
                     const float *tq = kp.taps + (a.ft.ctap_off[v] + q) * 2 * K;
-                    if (sm & 4u)
-                        vertical_pass<K, short_taps<K>(), kTyB>(tile, stage, tq);
-                    else
-                        vertical_pass<K, K, kTyB>(tile, stage, tq);
+                    vertical_pass_sel<K, kTyB>(sm & 4u, sm & 8u, tile, stage, tq);
                     __syncthreads();
                     if (q == a.ft.crank[v] - 1) prefetch_next();
                     if (sm & 8u)

@@ -155,29 +155,50 @@ __device__ __forceinline__ void vertical_item(const float *__restrict__ tile, fl
 }
 
 // Vertical pass: stage[i][c] = sum_m t[m] * tile[i + m][COL0 + c] for the TY
-// output rows and IN_W columns.  The TX columns under the output tile run as
-// 16-row items (TX*TY/16 = a whole number of rounds of the CTA), the 2R halo
-// columns as 8-row items (one more round), so that no warp idles for long
-// at the barrier that follows.
-template <int K, int KP = K, int TYF = 0>
+// output rows and the columns that a horizontal pass of KH central taps
+// reads: c = OFFH .. OFFH + TX + KH - 2 with OFFH = (K - KH) / 2 (all IN_W
+// columns when KH = K).  The TX columns from OFFH on run as 16-row items
+// (TX*TY/16 = a whole number of rounds of the CTA), the KH - 1 halo columns
+// after them as 8-row items (one more round at most), so that no warp idles
+// for long at the barrier that follows.  Staging columns outside that range
+// keep stale values; the horizontal pass loads some of them as parts of
+// quads but multiplies none of them.
+template <int K, int KP = K, int TYF = 0, int KH = K>
 __device__ __forceinline__ void vertical_pass(const float *__restrict__ tile, float *__restrict__ stage,
                                               const float *__restrict__ taps_s) {
     using G = Geo<K, TYF>;
     static_assert((G::TX * (G::TY / kNR)) % kThreads == 0, "main vertical items must tile the CTA");
+    static_assert(KH >= 1 && KH <= K && (K - KH) % 2 == 0, "horizontal taps are central");
     constexpr int OFF = (K - KP) / 2;
+    constexpr int OFFH = (K - KH) / 2;
     float t[KP];
 #pragma unroll
     for (int m = 0; m < KP; ++m) t[m] = taps_s[OFF + m];
     for (int it = threadIdx.x; it < G::TX * (G::TY / kNR); it += kThreads) {
         const int rb = it / G::TX;
-        vertical_item<K, kNR, KP, TYF>(tile, stage, t, it - rb * G::TX, rb * kNR);
+        vertical_item<K, kNR, KP, TYF>(tile, stage, t, OFFH + it - rb * G::TX, rb * kNR);
     }
-    if (G::R > 0) {
-        constexpr int HC = G::R > 0 ? 2 * G::R : 1;   // halo columns TX .. TX+2R-1
+    if (KH > 1) {
+        constexpr int HC = KH > 1 ? KH - 1 : 1;   // halo columns OFFH+TX .. OFFH+TX+KH-2
         for (int it = threadIdx.x; it < HC * (G::TY / 8); it += kThreads) {
             const int r8 = it / HC;
-            vertical_item<K, 8, KP, TYF>(tile, stage, t, G::TX + (it - r8 * HC), r8 * 8);
+            vertical_item<K, 8, KP, TYF>(tile, stage, t, OFFH + G::TX + (it - r8 * HC), r8 * 8);
         }
+    }
+}
+
+// The vertical pass for a factor pair whose vertical (vs) and horizontal
+// (hs) factors run their short_taps<K>() central taps (true) or all K.
+template <int K, int TYF = 0>
+__device__ __forceinline__ void vertical_pass_sel(bool vs, bool hs, const float *__restrict__ tile,
+                                                  float *__restrict__ stage, const float *__restrict__ taps_s) {
+    constexpr int S = short_taps<K>();
+    if (vs) {
+        if (hs) vertical_pass<K, S, TYF, S>(tile, stage, taps_s);
+        else vertical_pass<K, S, TYF, K>(tile, stage, taps_s);
+    } else {
+        if (hs) vertical_pass<K, K, TYF, S>(tile, stage, taps_s);
+        else vertical_pass<K, K, TYF, K>(tile, stage, taps_s);
     }
 }
 
