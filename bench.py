@@ -624,12 +624,29 @@ def run_mvd(args, wl):
         try:
             mvd.mvd_reslice(gctx, gs, gplanes)
             mvd.mvd_psf_grad(gctx, gplanes, 2)
-            g0 = time.perf_counter()
-            loss, _ = mvd.mvd_psf_grad(gctx, gplanes, 2)
-            gt = time.perf_counter() - g0
-            grad = {"ms_per_gradient": gt * 1e3, "loss": loss,
+            reps = 3
+            ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            ev0.record()
+            for _ in range(reps):
+                loss, _ = mvd.mvd_psf_grad(gctx, gplanes, 2)
+            ev1.record()
+            torch.cuda.synchronize()
+            gms = ev0.elapsed_time(ev1) / reps
+            # algorithmic FLOPs of one gradient: every K x K stencil and every
+            # K^2-lag sum is 2 K^2 flop per pixel; forward 2TV stencils,
+            # terminal fit 2V stencils + V lag sums, recomputed segments 2TV
+            # stencils, reverse sweep 2TV stencils + 2TV lag sums
+            T_, V_, K_, n_ = 10, 2, 31, 64 * 256 * 256
+            n_stencil, n_lag = 6 * T_ * V_ + 2 * V_, 2 * T_ * V_ + V_
+            gflop = (n_stencil + n_lag) * 2 * K_ * K_ * n_
+            tfl = gflop / (gms * 1e-3) / 1e12
+            grad = {"ms_per_gradient": gms, "loss": loss,
                     "config": "2 views, 64 planes 256x256, K=31 free PSFs, 10 iterations, checkpoint every 2",
-                    "unrolled_voxel_view_iterations_per_s": 64 * 256 * 256 * 10 * 2 / gt}
+                    "unrolled_voxel_view_iterations_per_s": n_ * T_ * V_ / (gms * 1e-3),
+                    "roofline": {"bound": "alu", "achieved": tfl, "peak": alu_peak, "unit": "TFLOP/s",
+                                 "frac": tfl / alu_peak, "peak_source": alu_src,
+                                 "flops_per_gradient": gflop,
+                                 "count": f"{n_stencil} K x K stencils + {n_lag} K^2-lag sums, 2 K^2 flop per pixel each"}}
         finally:
             gctx.close()
             del gs, gplanes

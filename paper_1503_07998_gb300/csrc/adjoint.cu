@@ -23,6 +23,7 @@
 // lag sums reduce tiles in FP32 and combine across tiles in FP64.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdint>
 
 #include "mvd_internal.h"
@@ -32,103 +33,174 @@ namespace adj {
 
 namespace {
 
-constexpr int kT = 32;          // output tile side
-constexpr int kThreads = 256;   // 8 x 32: each thread 4 rows of one column
+constexpr int kThreads = 256;
+// Register-blocked stencils and lag sums: output tiles of kTY x kTX pixels;
+// taps and lag rows in chunks of kNB, so every shared-memory value a thread
+// loads feeds kNB FMAs whatever K is (the last chunk's taps past K are zero).
+constexpr int kTY = 64;
+constexpr int kTX = 64;
+constexpr int kNB = 16;
 
 __device__ __forceinline__ int wrap(int i, int n) {
     i %= n;
     return i < 0 ? i + n : i;
 }
 
-// Input tile of side kT + 2R around output tile (y0, x0) of plane `src`.
-__device__ __forceinline__ void load_halo(float *tile, const float *__restrict__ src, int y0, int x0, int R, int H,
+__host__ __device__ constexpr int n_chunks(int K) { return (K + kNB - 1) / kNB; }
+// Halo tile rows: kTY + K - 1 input rows, then zero rows up to the chunked
+// reach kTY + kNB * chunks - 1 (read only against zero taps or dropped lags).
+__host__ __device__ constexpr int halo_rows(int K) { return kTY + kNB * n_chunks(K) - 1; }
+__host__ __device__ constexpr int halo_cols(int K) { return kTX + K - 1; }
+// Floats of the halo tile, rounded up to whole 16-byte quads so that the
+// region after it starts 16-byte aligned.
+__host__ __device__ constexpr int halo_floats(int K) { return (halo_rows(K) * halo_cols(K) + 3) / 4 * 4; }
+
+// Halo tile around output tile (y0, x0) of plane `src`: tile[r][c] =
+// src(y0 - R + r, x0 - R + c), zero (ZERO boundary) or wrapped (CIRCULAR)
+// outside the plane, zero in the rows past kTY + K - 1.
+__device__ __forceinline__ void load_halo(float *tile, const float *__restrict__ src, int y0, int x0, int K, int H,
                                           int W, int circular) {
-    const int S = kT + 2 * R;
-    for (int i = threadIdx.x; i < S * S; i += kThreads) {
-        const int r = i / S, c = i - r * S;
-        int y = y0 - R + r, x = x0 - R + c;
+    const int R = (K - 1) / 2, NC = halo_cols(K), NR = halo_rows(K), valid = kTY + K - 1;
+    for (int i = threadIdx.x; i < NR * NC; i += kThreads) {
+        const int r = i / NC, c = i - r * NC;
+        const int y = y0 - R + r, x = x0 - R + c;
         float v = 0.0f;
-        if (circular) {
-            v = src[static_cast<long long>(wrap(y, H)) * W + wrap(x, W)];
-        } else if (y >= 0 && y < H && x >= 0 && x < W) {
-            v = src[static_cast<long long>(y) * W + x];
+        if (r < valid) {
+            if (circular) {
+                v = src[static_cast<long long>(wrap(y, H)) * W + wrap(x, W)];
+            } else if (y >= 0 && y < H && x >= 0 && x < W) {
+                v = src[static_cast<long long>(y) * W + x];
+            }
         }
         tile[i] = v;
     }
 }
 
-// out (=|+=) conv or corr of `in` with one K x K PSF, for every plane.
-//   conv: out(y,x) = sum_ij P[i][j] in(y-i+R, x-j+R)
+// out (=|+=) conv or corr of `in` with one K x K PSF, for every plane:
 //   corr: out(y,x) = sum_ij P[i][j] in(y+i-R, x+j-R)
+//   conv: out(y,x) = sum_ij P[i][j] in(y-i+R, x-j+R) = corr with P turned by 180 degrees.
+// Thread: one column and kNB consecutive output rows.  For every tap column
+// j and chunk of kNB tap rows it walks the 2 kNB - 1 input rows in reach,
+// each loaded once and multiplied into every output row it touches.
 __global__ void __launch_bounds__(kThreads)
 stencil_kernel(const float *__restrict__ in, float *__restrict__ out, const float *__restrict__ psf, int K, int H,
                int W, int circular, int correlate, int accumulate) {
-    extern __shared__ float sm[];
-    const int R = (K - 1) / 2;
-    const int S = kT + 2 * R;
+    static_assert(kTX * (kTY / kNB) == kThreads, "one item per thread");
+    extern __shared__ __align__(16) float sm[];
+    const int nch = n_chunks(K), KP = kNB * nch, NC = halo_cols(K);
     float *tile = sm;
-    float *p = sm + S * S;
+    float *taps = sm + halo_floats(K);   // [j][KP]: w(i, j), zero for i >= K (16-byte aligned rows)
     const long long plane = static_cast<long long>(H) * W;
     const float *src = in + blockIdx.z * plane;
     float *dst = out + blockIdx.z * plane;
-    const int y0 = blockIdx.y * kT, x0 = blockIdx.x * kT;
-    for (int i = threadIdx.x; i < K * K; i += kThreads) p[i] = psf[i];
-    load_halo(tile, src, y0, x0, R, H, W, circular);
+    const int y0 = blockIdx.y * kTY, x0 = blockIdx.x * kTX;
+    for (int k = threadIdx.x; k < K * KP; k += kThreads) {
+        const int j = k / KP, i = k - j * KP;
+        taps[k] = i < K ? (correlate ? psf[i * K + j] : psf[(K - 1 - i) * K + (K - 1 - j)]) : 0.0f;
+    }
+    load_halo(tile, src, y0, x0, K, H, W, circular);
     __syncthreads();
-    const int tx = threadIdx.x & 31, ty0 = threadIdx.x >> 5;   // rows ty0, ty0+8, ty0+16, ty0+24
-    float acc[4] = {0.f, 0.f, 0.f, 0.f};
-    for (int i = 0; i < K; ++i) {
-        for (int j = 0; j < K; ++j) {
-            // tile coordinate of the input tap for output row ty: conv -> ty+2R-i, corr -> ty+i
-            const float w = correlate ? p[i * K + j] : p[(K - 1 - i) * K + (K - 1 - j)];
-            const float *col = tile + i * S + j + tx;
+    const int c = threadIdx.x % kTX, r0 = kNB * (threadIdx.x / kTX);
+    float acc[kNB];
 #pragma unroll
-            for (int k = 0; k < 4; ++k) acc[k] = fmaf(w, col[(ty0 + 8 * k) * S], acc[k]);
+    for (int r = 0; r < kNB; ++r) acc[r] = 0.0f;
+    for (int j = 0; j < K; ++j) {
+        for (int ch = 0; ch < nch; ++ch) {
+            float t[kNB];
+            const float4 *tq = reinterpret_cast<const float4 *>(taps + j * KP + kNB * ch);
+#pragma unroll
+            for (int q = 0; q < kNB / 4; ++q) {
+                const float4 v = tq[q];
+                t[4 * q] = v.x;
+                t[4 * q + 1] = v.y;
+                t[4 * q + 2] = v.z;
+                t[4 * q + 3] = v.w;
+            }
+            const float *col = tile + (r0 + kNB * ch) * NC + c + j;
+#pragma unroll
+            for (int m = 0; m < 2 * kNB - 1; ++m) {
+                const float x = col[m * NC];
+#pragma unroll
+                for (int r = 0; r < kNB; ++r) {
+                    const int i = m - r;
+                    if (i >= 0 && i < kNB) acc[r] = fmaf(t[i], x, acc[r]);
+                }
+            }
         }
     }
+    const int x = x0 + c;
+    if (x >= W) return;
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        const int y = y0 + ty0 + 8 * k, x = x0 + tx;
-        if (y < H && x < W) {
+    for (int r = 0; r < kNB; ++r) {
+        const int y = y0 + r0 + r;
+        if (y < H) {
             const long long o = static_cast<long long>(y) * W + x;
-            dst[o] = accumulate ? dst[o] + acc[k] : acc[k];
+            dst[o] = accumulate ? dst[o] + acc[r] : acc[r];
         }
     }
 }
 
-// G[i][j] += sum_planes sum_x g(x) img(x + s*d_ij), s = +1 (corr form) or -1
-// (conv form), img zero or wrapped outside the plane.  One CTA per (tile,
-// plane); every thread owns taps k = tid, tid + 256, ...; FP32 per tile,
-// FP64 across tiles.
+// G[i][j] += sum_planes sum_x g(x) img(x + s*d_ij), d_ij = (i-R, j-R),
+// s = +1 (corr form) or -1 (conv form), img zero or wrapped outside the
+// plane.  One CTA per (tile, plane) computes the tile's lag sums
+//   Hs[i][j] = sum_{y,x in tile} g(y,x) img(y+i-R, x+j-R)
+// (s = -1 takes Hs[K-1-i][K-1-j]).  Work unit: one lag column j, a chunk of
+// kNB lag rows and a group of the tile's pixel columns; walking a pixel
+// column down, each img value feeds kNB lags against a sliding window of
+// kNB g values held in registers.  FP32 within a unit, FP64 across units
+// and tiles.
 __global__ void __launch_bounds__(kThreads)
 lag_sum_kernel(const float *__restrict__ g, const float *__restrict__ img, double *__restrict__ G, int K, int H, int W,
                int circular, int sign) {
-    extern __shared__ float sm[];
-    const int R = (K - 1) / 2;
-    const int S = kT + 2 * R;
-    float *tile = sm;               // img with halo
-    float *gt = sm + S * S;         // g over the tile (zero outside the plane)
+    extern __shared__ __align__(16) float sm[];
+    const int nch = n_chunks(K), KP = kNB * nch, NC = halo_cols(K);
+    const int items = K * nch;
+    const int groups = min(kTX, max(1, kThreads / items));
+    const int cpg = (kTX + groups - 1) / groups;
+    float *tile = sm;                          // img with halo
+    float *gt = tile + halo_floats(K);         // g over the tile [kTY][kTX], zero outside the plane
+    float *red = gt + kTY * kTX;               // [groups][KP][K] partial sums
     const long long plane = static_cast<long long>(H) * W;
-    const int y0 = blockIdx.y * kT, x0 = blockIdx.x * kT;
-    load_halo(tile, img + blockIdx.z * plane, y0, x0, R, H, W, circular);
-    for (int i = threadIdx.x; i < kT * kT; i += kThreads) {
-        const int r = i / kT, c = i - r * kT;
+    const int y0 = blockIdx.y * kTY, x0 = blockIdx.x * kTX;
+    load_halo(tile, img + blockIdx.z * plane, y0, x0, K, H, W, circular);
+    for (int i = threadIdx.x; i < kTY * kTX; i += kThreads) {
+        const int r = i / kTX, c = i - r * kTX;
         const int y = y0 + r, x = x0 + c;
         gt[i] = (y < H && x < W) ? g[blockIdx.z * plane + static_cast<long long>(y) * W + x] : 0.0f;
     }
     __syncthreads();
-    for (int k = threadIdx.x; k < K * K; k += kThreads) {
-        const int i = k / K, j = k - i * K;
-        const int dy = sign * (i - R), dx = sign * (j - R);
-        const float *base = tile + (R + dy) * S + (R + dx);
-        float acc = 0.0f;
-        for (int r = 0; r < kT; ++r) {
-            const float *gr = gt + r * kT;
-            const float *ir = base + r * S;
-#pragma unroll 8
-            for (int c = 0; c < kT; ++c) acc = fmaf(gr[c], ir[c], acc);
+    const int u = threadIdx.x;
+    const int gq = u / items, item = u - gq * items;
+    const int ch = item / K, j = item - ch * K;
+    if (gq < groups) {
+        float acc[kNB];
+#pragma unroll
+        for (int r = 0; r < kNB; ++r) acc[r] = 0.0f;
+        const int xb = gq * cpg, xe = min(kTX, xb + cpg);
+        for (int x = xb; x < xe; ++x) {
+            const float *tc = tile + kNB * ch * NC + x + j;   // rows 16ch + m, column x + j
+            const float *gc = gt + x;
+            float gv[kTY];
+#pragma unroll
+            for (int m = 0; m < kTY + kNB - 1; ++m) {
+                if (m < kTY) gv[m] = gc[m * kTX];
+                const float t = tc[m * NC];
+#pragma unroll
+                for (int r = 0; r < kNB; ++r) {
+                    const int y = m - r;   // lag row 16ch + r pairs pixel row y with img row y + 16ch + r
+                    if (y >= 0 && y < kTY) acc[r] = fmaf(gv[y], t, acc[r]);
+                }
+            }
         }
-        atomicAdd(G + k, static_cast<double>(acc));
+#pragma unroll
+        for (int r = 0; r < kNB; ++r) red[(gq * KP + kNB * ch + r) * K + j] = acc[r];
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < K * K; k += kThreads) {
+        double s = 0.0;
+        for (int q = 0; q < groups; ++q) s += static_cast<double>(red[q * KP * K + k]);
+        const int i = k / K, jj = k - i * K;
+        atomicAdd(G + (sign > 0 ? k : (K - 1 - i) * K + (K - 1 - jj)), s);
     }
 }
 
@@ -212,14 +284,12 @@ inline unsigned blocks(long long n) { return static_cast<unsigned>((n + kThreads
 
 }  // namespace
 
-int stencil_smem_bytes(int K) {
-    const int S = kT + 2 * ((K - 1) / 2);
-    return (S * S + K * K) * 4;
-}
+int stencil_smem_bytes(int K) { return (halo_floats(K) + K * kNB * n_chunks(K)) * 4; }
 
 int lag_smem_bytes(int K) {
-    const int S = kT + 2 * ((K - 1) / 2);
-    return (S * S + kT * kT) * 4;
+    const int items = K * n_chunks(K);
+    const int groups = std::min(kTX, std::max(1, kThreads / items));
+    return (halo_floats(K) + kTY * kTX + groups * kNB * n_chunks(K) * K) * 4;
 }
 
 cudaError_t stencil(const float *in, float *out, const float *psf, int K, int H, int W, int P, int circular,
@@ -227,7 +297,7 @@ cudaError_t stencil(const float *in, float *out, const float *psf, int K, int H,
     const int smem = stencil_smem_bytes(K);
     cudaError_t e = cudaFuncSetAttribute(stencil_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
-    const dim3 grid((W + kT - 1) / kT, (H + kT - 1) / kT, P);
+    const dim3 grid((W + kTX - 1) / kTX, (H + kTY - 1) / kTY, P);
     stencil_kernel<<<grid, kThreads, smem, s>>>(in, out, psf, K, H, W, circular, correlate, accumulate);
     count_launch();
     return cudaGetLastError();
@@ -238,7 +308,7 @@ cudaError_t lag_sum(const float *g, const float *img, double *G, int K, int H, i
     const int smem = lag_smem_bytes(K);
     cudaError_t e = cudaFuncSetAttribute(lag_sum_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
-    const dim3 grid((W + kT - 1) / kT, (H + kT - 1) / kT, P);
+    const dim3 grid((W + kTX - 1) / kTX, (H + kTY - 1) / kTY, P);
     lag_sum_kernel<<<grid, kThreads, smem, s>>>(g, img, G, K, H, W, circular, sign);
     count_launch();
     return cudaGetLastError();
