@@ -273,12 +273,16 @@ mvd_status mvd_run_host(mvd_ctx *ctx, const void *stacks_host, mvd_dtype dt,
 /* The chunks of planes mvd_run_host uses for ny planes of plane_bytes input
  * bytes each (all views).  With chunk_planes > 0 the chunks hold chunk_planes
  * planes (the last one the rest).  With chunk_planes = 0 they are chosen
- * automatically: about 128 MiB of input per chunk, except that the first and
- * the last chunk hold a quarter of that.  The iterations then start after a
- * short first copy, the last copy back is short, and every other copy
- * overlaps the iterations of a neighbouring chunk.  Small volumes get four
- * equal chunks instead.  Writes chunk i as planes y0[i] .. y0[i] + n[i] - 1,
- * in order and covering 0 .. ny - 1, for at most `cap` chunks.  Returns the
+ * automatically around base = 1 GiB of input per chunk (at most ny/4
+ * planes): chunks of base/8, base/4 and base/2 planes first, then equal
+ * chunks of at most base planes, and a last chunk of base/4.  The iterations
+ * then start after a short first copy, the last copy back is short, every
+ * other copy overlaps the iterations of a neighbouring chunk, and each
+ * chunk's launches run long enough that their start-up and last partial
+ * wave of tiles cost little.  Volumes under 256 MiB of input (or with base
+ * below 8 planes) get four equal chunks instead.  Writes chunk i as planes
+ * y0[i] .. y0[i] + n[i] - 1, in order and covering 0 .. ny - 1, for at most
+ * `cap` chunks.  Returns the
  * number of chunks, or -1 if an argument is invalid (ny < 1,
  * plane_bytes < 1, chunk_planes < 0, NULL arrays) or cap is too small.
  * Host only: no device work. */

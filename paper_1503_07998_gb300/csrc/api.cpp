@@ -1368,15 +1368,22 @@ int mvd_host_chunks(int ny, long long plane_bytes, int chunk_planes, int *y0, in
     if (chunk_planes > 0) {
         for (int y = 0; y < ny; y += chunk_planes) sizes.push_back(std::min(chunk_planes, ny - y));
     } else {
-        const long long base = std::max(1LL, std::min<long long>(ny, (128LL << 20) / plane_bytes));
-        const int edge = static_cast<int>(std::max(1LL, base / 4));
-        if (ny >= 2 * edge + base && base >= 4) {
-            // short first and last chunks, the middle in equal parts of at most `base`
-            const int mid = ny - 2 * edge;
+        // about 1 GiB of input per chunk (at most a quarter of the volume):
+        // every chunk's launches run long enough that their start-up and last
+        // partial wave stay small
+        const long long base = std::max(1LL, std::min<long long>(ny / 4, (1LL << 30) / plane_bytes));
+        std::vector<int> ramp;   // base/8, base/4, base/2: the iterations start after a short copy
+        for (long long d : {8LL, 4LL, 2LL})
+            if (base / d >= 1) ramp.push_back(static_cast<int>(base / d));
+        long long ramp_sum = 0;
+        for (int r : ramp) ramp_sum += r;
+        const int last = static_cast<int>(std::max(1LL, base / 4));   // short copy back at the end
+        if (base >= 8 && ny >= ramp_sum + last + base && static_cast<long long>(ny) * plane_bytes >= (256LL << 20)) {
+            const long long mid = ny - ramp_sum - last;
             const int parts = static_cast<int>((mid + base - 1) / base);
-            sizes.push_back(edge);
-            for (int i = 0; i < parts; ++i) sizes.push_back(mid / parts + (i < mid % parts ? 1 : 0));
-            sizes.push_back(edge);
+            sizes = ramp;
+            for (int i = 0; i < parts; ++i) sizes.push_back(static_cast<int>(mid / parts + (i < mid % parts ? 1 : 0)));
+            sizes.push_back(last);
         } else {
             const int cp = std::max(1, (ny + 3) / 4);
             for (int y = 0; y < ny; y += cp) sizes.push_back(std::min(cp, ny - y));

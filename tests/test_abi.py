@@ -154,13 +154,23 @@ def test_host_chunks_uniform_and_small_volumes():
 
 
 def test_host_chunks_ramp_for_large_volumes():
-    # 512 planes of 1 MiB (2 views of 512 x 512 uint16): 128-plane chunks,
-    # the first and the last a quarter of that
-    assert mvd.mvd_host_chunks(512, 1 << 20, 0) == [(0, 32), (32, 112), (144, 112), (256, 112), (368, 112),
-                                                    (480, 32)]
-    # 1024 planes of 4 MiB (4 views of 1024 x 1024 uint16): 32-plane chunks, edges of 8
-    ch = mvd.mvd_host_chunks(1024, 4 << 20, 0)
-    assert ch[0] == (0, 8) and ch[-1] == (1016, 8) and max(n for _, n in ch) <= 32
+    # 1024 planes of 8 MiB (4 views of 1024 x 1024 uint16): base 128 planes
+    # (1 GiB); ramp 16, 32, 64; 880 planes in 7 middle chunks; last 32
+    ch = mvd.mvd_host_chunks(1024, 8 << 20, 0)
+    sizes = [n for _, n in ch]
+    assert sizes[:3] == [16, 32, 64] and sizes[-1] == 32
+    assert len(sizes) == 11 and all(125 <= n <= 128 for n in sizes[3:-1]) and sum(sizes) == 1024
+    # 2048 planes of 1 MiB: base 512 (a quarter of the volume); ramp 64, 128,
+    # 256; 1472 planes in 3 middle chunks; last 128
+    assert [n for _, n in mvd.mvd_host_chunks(2048, 1 << 20, 0)] == [64, 128, 256, 491, 491, 490, 128]
+    # 512 planes of 1 MiB (2 views of 512 x 512 uint16): base 128
+    assert [n for _, n in mvd.mvd_host_chunks(512, 1 << 20, 0)] == [16, 32, 64, 123, 123, 122, 32]
+    # 4096 planes of 1 MiB: ramp 128, 256, 512; 2944 planes in 3 middle chunks; last 256
+    assert [n for _, n in mvd.mvd_host_chunks(4096, 1 << 20, 0)] == [128, 256, 512, 982, 981, 981, 256]
+    # planes above 128 MiB (base under 8 planes): four equal chunks
+    assert mvd.mvd_host_chunks(40, 256 << 20, 0) == [(0, 10), (10, 10), (20, 10), (30, 10)]
+    # under 256 MiB of input: four equal chunks
+    assert mvd.mvd_host_chunks(200, 1 << 20, 0) == [(0, 50), (50, 50), (100, 50), (150, 50)]
 
 
 def test_host_chunks_cover_every_plane_once():

@@ -225,13 +225,14 @@ def test_host_pipeline_equals_device_path(mvd):
 
 
 def test_host_pipeline_automatic_chunks_equal_device_path(mvd):
-    """200 MiB of input (2 views, 800 planes of 128 x 512): the automatic
-    schedule ramps (short first and last chunks); the result equals the
-    device path bit for bit."""
-    stacks, psfs = synth.volume_stacks(128, 800, 512, 9, 4.0, 1.5, (0, 90), 1e-4, seed=12, device=DEV)
+    """300 MiB of input (2 views, 1200 planes of 128 x 512): the automatic
+    schedule ramps (chunks of 37, 75 and 150 planes, three of about 288, a
+    last one of 75); the result equals the device path bit for bit."""
+    stacks, psfs = synth.volume_stacks(128, 1200, 512, 9, 4.0, 1.5, (0, 90), 1e-4, seed=12, device=DEV)
     V, Z, Y, X = stacks.shape
     chunks = mvd.mvd_host_chunks(Y, V * Z * X * 2)
-    assert len(chunks) >= 3 and chunks[0][1] < max(n for _, n in chunks) and chunks[-1][1] == chunks[0][1]
+    sizes = [n for _, n in chunks]
+    assert sizes[:3] == [37, 75, 150] and sizes[-1] == 75 and max(sizes) == 288 and sum(sizes) == Y
     ctx = mvd.mvd_create(V, psfs, 9, Z, X, 3, "zero", 1e-6)
     try:
         planes = torch.empty((V, Y, Z, X), dtype=stacks.dtype, device=DEV)
