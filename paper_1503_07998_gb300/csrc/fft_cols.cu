@@ -48,6 +48,10 @@ __global__ void __launch_bounds__(kThreads) fft_cols_kernel(const FftArgs a, int
     const long long srow = a.LcP, splane = static_cast<long long>(a.H) * srow;
     const long long items = static_cast<long long>(a.P) * nblk;
     const int nthr = blockDim.x;
+    // idx / CB as a multiply-high by ceil(2^32 / CB): exact for CB <= 8 and
+    // idx < 2^32 / 7 (a block holds at most Ly * CB elements)
+    const unsigned cb_magic = CB > 1 ? static_cast<unsigned>((0x100000000ull + CB - 1) / CB) : 0u;
+    auto row_of = [&](int idx) -> int { return CB > 1 ? static_cast<int>(__umulhi(static_cast<unsigned>(idx), cb_magic)) : idx; };
 
     // rows < H of the block's columns into dst (column c at dst + c LD), zero beyond
     auto load = [&](const float2 *src, float2 *dst, int c0) {
@@ -55,20 +59,20 @@ __global__ void __launch_bounds__(kThreads) fft_cols_kernel(const FftArgs a, int
             float2 v[kBatch];
 #pragma unroll
             for (int u = 0; u < kBatch; ++u) {
-                const int idx = idx0 + u * nthr, r = idx / CB, c = idx - r * CB;
+                const int idx = idx0 + u * nthr, r = row_of(idx), c = idx - r * CB;
                 v[u] = make_float2(0.f, 0.f);
                 if (idx < Ly * CB && r < a.H && c0 + c < a.Lc) v[u] = src[r * srow + c0 + c];
             }
 #pragma unroll
             for (int u = 0; u < kBatch; ++u) {
-                const int idx = idx0 + u * nthr, r = idx / CB, c = idx - r * CB;
+                const int idx = idx0 + u * nthr, r = row_of(idx), c = idx - r * CB;
                 if (idx < Ly * CB) dst[c * LD + r] = v[u];
             }
         }
     };
     auto store = [&](const float2 *src, float2 *dst, int c0) {   // rows < H
         for (int idx = threadIdx.x; idx < a.H * CB; idx += nthr) {
-            const int r = idx / CB, c = idx - r * CB;
+            const int r = row_of(idx), c = idx - r * CB;
             if (c0 + c < a.Lc) dst[r * srow + c0 + c] = src[c * LD + r];
         }
     };
