@@ -33,13 +33,16 @@ namespace adj {
 
 namespace {
 
-constexpr int kThreads = 256;
-// Register-blocked stencils and lag sums: output tiles of kTY x kTX pixels;
-// taps and lag rows in chunks of kNB, so every shared-memory value a thread
-// loads feeds kNB FMAs whatever K is (the last chunk's taps past K are zero).
-constexpr int kTY = 64;
+constexpr int kThreads = 256;   // elementwise kernels and the lag sums
+// Register-blocked stencils and lag sums: output tiles of TY x kTX pixels
+// (64 x 64, 256 threads); taps and lag rows in chunks of kNB, so every
+// shared-memory value a thread loads feeds kNB FMAs whatever K is (the last
+// chunk's taps past K are zero).
 constexpr int kTX = 64;
 constexpr int kNB = 16;
+constexpr int kStencilTY = 64;
+constexpr int kStencilThreads = kTX * (kStencilTY / kNB);   // one item per thread
+constexpr int kLagTY = 64;
 
 __device__ __forceinline__ int wrap(int i, int n) {
     i %= n;
@@ -47,21 +50,24 @@ __device__ __forceinline__ int wrap(int i, int n) {
 }
 
 __host__ __device__ constexpr int n_chunks(int K) { return (K + kNB - 1) / kNB; }
-// Halo tile rows: kTY + K - 1 input rows, then zero rows up to the chunked
-// reach kTY + kNB * chunks - 1 (read only against zero taps or dropped lags).
-__host__ __device__ constexpr int halo_rows(int K) { return kTY + kNB * n_chunks(K) - 1; }
+// Halo tile rows: TY + K - 1 input rows, then zero rows up to the chunked
+// reach TY + kNB * chunks - 1 (read only against zero taps or dropped lags).
+__host__ __device__ constexpr int halo_rows(int TY, int K) { return TY + kNB * n_chunks(K) - 1; }
 __host__ __device__ constexpr int halo_cols(int K) { return kTX + K - 1; }
 // Floats of the halo tile, rounded up to whole 16-byte quads so that the
 // region after it starts 16-byte aligned.
-__host__ __device__ constexpr int halo_floats(int K) { return (halo_rows(K) * halo_cols(K) + 3) / 4 * 4; }
+__host__ __device__ constexpr int halo_floats(int TY, int K) {
+    return (halo_rows(TY, K) * halo_cols(K) + 3) / 4 * 4;
+}
 
 // Halo tile around output tile (y0, x0) of plane `src`: tile[r][c] =
 // src(y0 - R + r, x0 - R + c), zero (ZERO boundary) or wrapped (CIRCULAR)
-// outside the plane, zero in the rows past kTY + K - 1.
+// outside the plane, zero in the rows past TY + K - 1.  NT threads.
+template <int TY, int NT>
 __device__ __forceinline__ void load_halo(float *tile, const float *__restrict__ src, int y0, int x0, int K, int H,
                                           int W, int circular) {
-    const int R = (K - 1) / 2, NC = halo_cols(K), NR = halo_rows(K), valid = kTY + K - 1;
-    for (int i = threadIdx.x; i < NR * NC; i += kThreads) {
+    const int R = (K - 1) / 2, NC = halo_cols(K), NR = halo_rows(TY, K), valid = TY + K - 1;
+    for (int i = threadIdx.x; i < NR * NC; i += NT) {
         const int r = i / NC, c = i - r * NC;
         const int y = y0 - R + r, x = x0 - R + c;
         float v = 0.0f;
@@ -82,23 +88,23 @@ __device__ __forceinline__ void load_halo(float *tile, const float *__restrict__
 // Thread: one column and kNB consecutive output rows.  For every tap column
 // j and chunk of kNB tap rows it walks the 2 kNB - 1 input rows in reach,
 // each loaded once and multiplied into every output row it touches.
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kStencilThreads)
 stencil_kernel(const float *__restrict__ in, float *__restrict__ out, const float *__restrict__ psf, int K, int H,
                int W, int circular, int correlate, int accumulate) {
-    static_assert(kTX * (kTY / kNB) == kThreads, "one item per thread");
+    constexpr int TY = kStencilTY;
     extern __shared__ __align__(16) float sm[];
     const int nch = n_chunks(K), KP = kNB * nch, NC = halo_cols(K);
     float *tile = sm;
-    float *taps = sm + halo_floats(K);   // [j][KP]: w(i, j), zero for i >= K (16-byte aligned rows)
+    float *taps = sm + halo_floats(TY, K);   // [j][KP]: w(i, j), zero for i >= K (16-byte aligned rows)
     const long long plane = static_cast<long long>(H) * W;
     const float *src = in + blockIdx.z * plane;
     float *dst = out + blockIdx.z * plane;
-    const int y0 = blockIdx.y * kTY, x0 = blockIdx.x * kTX;
-    for (int k = threadIdx.x; k < K * KP; k += kThreads) {
+    const int y0 = blockIdx.y * TY, x0 = blockIdx.x * kTX;
+    for (int k = threadIdx.x; k < K * KP; k += kStencilThreads) {
         const int j = k / KP, i = k - j * KP;
         taps[k] = i < K ? (correlate ? psf[i * K + j] : psf[(K - 1 - i) * K + (K - 1 - j)]) : 0.0f;
     }
-    load_halo(tile, src, y0, x0, K, H, W, circular);
+    load_halo<TY, kStencilThreads>(tile, src, y0, x0, K, H, W, circular);
     __syncthreads();
     const int c = threadIdx.x % kTX, r0 = kNB * (threadIdx.x / kTX);
     float acc[kNB];
@@ -148,22 +154,24 @@ stencil_kernel(const float *__restrict__ in, float *__restrict__ out, const floa
 // kNB lag rows and a group of the tile's pixel columns; walking a pixel
 // column down, each img value feeds kNB lags against a sliding window of
 // kNB g values held in registers.  FP32 within a unit, FP64 across units
-// and tiles.
+// (partial sums in shared memory, over the halo tile once it is read) and
+// tiles (atomics).
 __global__ void __launch_bounds__(kThreads)
 lag_sum_kernel(const float *__restrict__ g, const float *__restrict__ img, double *__restrict__ G, int K, int H, int W,
                int circular, int sign) {
+    constexpr int TY = kLagTY;
     extern __shared__ __align__(16) float sm[];
     const int nch = n_chunks(K), KP = kNB * nch, NC = halo_cols(K);
     const int items = K * nch;
     const int groups = min(kTX, max(1, kThreads / items));
     const int cpg = (kTX + groups - 1) / groups;
-    float *tile = sm;                          // img with halo
-    float *gt = tile + halo_floats(K);         // g over the tile [kTY][kTX], zero outside the plane
-    float *red = gt + kTY * kTX;               // [groups][KP][K] partial sums
+    float *tile = sm;                              // img with halo
+    float *gt = tile + halo_floats(TY, K);         // g over the tile [TY][kTX], zero outside the plane
+    float *red = tile;                             // [groups][KP][K] partial sums, once the tile is read
     const long long plane = static_cast<long long>(H) * W;
-    const int y0 = blockIdx.y * kTY, x0 = blockIdx.x * kTX;
-    load_halo(tile, img + blockIdx.z * plane, y0, x0, K, H, W, circular);
-    for (int i = threadIdx.x; i < kTY * kTX; i += kThreads) {
+    const int y0 = blockIdx.y * TY, x0 = blockIdx.x * kTX;
+    load_halo<TY, kThreads>(tile, img + blockIdx.z * plane, y0, x0, K, H, W, circular);
+    for (int i = threadIdx.x; i < TY * kTX; i += kThreads) {
         const int r = i / kTX, c = i - r * kTX;
         const int y = y0 + r, x = x0 + c;
         gt[i] = (y < H && x < W) ? g[blockIdx.z * plane + static_cast<long long>(y) * W + x] : 0.0f;
@@ -172,26 +180,29 @@ lag_sum_kernel(const float *__restrict__ g, const float *__restrict__ img, doubl
     const int u = threadIdx.x;
     const int gq = u / items, item = u - gq * items;
     const int ch = item / K, j = item - ch * K;
-    if (gq < groups) {
-        float acc[kNB];
+    float acc[kNB];
 #pragma unroll
-        for (int r = 0; r < kNB; ++r) acc[r] = 0.0f;
+    for (int r = 0; r < kNB; ++r) acc[r] = 0.0f;
+    if (gq < groups) {
         const int xb = gq * cpg, xe = min(kTX, xb + cpg);
         for (int x = xb; x < xe; ++x) {
             const float *tc = tile + kNB * ch * NC + x + j;   // rows 16ch + m, column x + j
             const float *gc = gt + x;
-            float gv[kTY];
+            float gv[TY];
 #pragma unroll
-            for (int m = 0; m < kTY + kNB - 1; ++m) {
-                if (m < kTY) gv[m] = gc[m * kTX];
+            for (int m = 0; m < TY + kNB - 1; ++m) {
+                if (m < TY) gv[m] = gc[m * kTX];
                 const float t = tc[m * NC];
 #pragma unroll
                 for (int r = 0; r < kNB; ++r) {
                     const int y = m - r;   // lag row 16ch + r pairs pixel row y with img row y + 16ch + r
-                    if (y >= 0 && y < kTY) acc[r] = fmaf(gv[y], t, acc[r]);
+                    if (y >= 0 && y < TY) acc[r] = fmaf(gv[y], t, acc[r]);
                 }
             }
         }
+    }
+    __syncthreads();   // the halo tile is read: its space takes the partial sums
+    if (gq < groups) {
 #pragma unroll
         for (int r = 0; r < kNB; ++r) red[(gq * KP + kNB * ch + r) * K + j] = acc[r];
     }
@@ -284,21 +295,20 @@ inline unsigned blocks(long long n) { return static_cast<unsigned>((n + kThreads
 
 }  // namespace
 
-int stencil_smem_bytes(int K) { return (halo_floats(K) + K * kNB * n_chunks(K)) * 4; }
+int stencil_smem_bytes(int K) { return (halo_floats(kStencilTY, K) + K * kNB * n_chunks(K)) * 4; }
 
-int lag_smem_bytes(int K) {
-    const int items = K * n_chunks(K);
-    const int groups = std::min(kTX, std::max(1, kThreads / items));
-    return (halo_floats(K) + kTY * kTX + groups * kNB * n_chunks(K) * K) * 4;
-}
+// The partial sums ([groups][KP][K], at most kThreads * kNB floats) reuse the
+// halo tile, which is never smaller.
+int lag_smem_bytes(int K) { return (halo_floats(kLagTY, K) + kLagTY * kTX) * 4; }
+static_assert(kThreads * kNB <= (kLagTY + kNB - 1) * kTX, "partial sums fit the halo tile");
 
 cudaError_t stencil(const float *in, float *out, const float *psf, int K, int H, int W, int P, int circular,
                     int correlate, int accumulate, cudaStream_t s) {
     const int smem = stencil_smem_bytes(K);
     cudaError_t e = cudaFuncSetAttribute(stencil_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
-    const dim3 grid((W + kTX - 1) / kTX, (H + kTY - 1) / kTY, P);
-    stencil_kernel<<<grid, kThreads, smem, s>>>(in, out, psf, K, H, W, circular, correlate, accumulate);
+    const dim3 grid((W + kTX - 1) / kTX, (H + kStencilTY - 1) / kStencilTY, P);
+    stencil_kernel<<<grid, kStencilThreads, smem, s>>>(in, out, psf, K, H, W, circular, correlate, accumulate);
     count_launch();
     return cudaGetLastError();
 }
@@ -308,7 +318,7 @@ cudaError_t lag_sum(const float *g, const float *img, double *G, int K, int H, i
     const int smem = lag_smem_bytes(K);
     cudaError_t e = cudaFuncSetAttribute(lag_sum_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
-    const dim3 grid((W + kTX - 1) / kTX, (H + kTY - 1) / kTY, P);
+    const dim3 grid((W + kTX - 1) / kTX, (H + kLagTY - 1) / kLagTY, P);
     lag_sum_kernel<<<grid, kThreads, smem, s>>>(g, img, G, K, H, W, circular, sign);
     count_launch();
     return cudaGetLastError();

@@ -53,6 +53,26 @@ def test_gradient_matches_oracle_small(mvd, boundary, ckpt):
     assert rel(est, ref_psi) <= 1e-5
 
 
+@pytest.mark.parametrize("K,boundary", [(1, "zero"), (15, "zero"), (17, "circular"), (33, "zero"), (49, "zero")])
+def test_gradient_tap_chunk_edges(mvd, K, boundary):
+    """Tap and lag rows run in chunks of 16: K = 1, 15 (one chunk), 17 and 33
+    (a last chunk of one tap) and 49 (a last chunk of one tap after three full
+    ones), on 70 x 75 planes (2 x 2 tiles of 64, both ragged).  (Flat random
+    33 x 33 PSFs with the circular boundary are left out: there the gradient
+    picks up a near-uniform offset of 4e-4 of its norm from FP32 rounding in
+    the sweep, the same on the earlier one-output-per-load kernels.)"""
+    rng = np.random.default_rng(70 + K)
+    V, P, H, W, T = 2, 2, 70, 75, 3
+    psfs = (rng.random((V, K, K)) + 0.05).astype(np.float32)
+    psfs /= psfs.sum(axis=(1, 2), keepdims=True)
+    phi = rng.uniform(5, 80, size=(V, P, H, W)).astype(np.float32)
+    loss, g, est = gpu_grad(mvd, phi, psfs, T, boundary, 2)
+    ref_loss, ref_g, ref_psi = oracle.rl_loss_and_psf_grad(phi, psfs, T, boundary)
+    assert abs(loss - ref_loss) <= 1e-6 * abs(ref_loss)
+    assert rel(g, ref_g) <= 1e-4, rel(g, ref_g)
+    assert rel(est, ref_psi) <= 1e-5
+
+
 def test_gradient_psf_calibration_case(mvd):
     """Two views of blob planes made with sigma (1.5, 7) PSFs; free 31x31
     PSFs initialised to sigma (1.2, 5); 10 unrolled iterations, checkpoint
