@@ -376,6 +376,15 @@ correlate_update_kernel(const __grid_constant__ KParams kp) {
         const TileCoord tc = tile_coord<K, kTyB>(t, tiles_x, tiles_y);
         const int p = tc.p, y0 = tc.y0, x0 = tc.x0;
         const int t_next = t + gridDim.x;
+        // the tile's estimate rows, read by the update epilogue after every
+        // view's passes, are requested into L2 now: one 128-byte line per
+        // thread (TY rows x TX columns = TY * 4 lines)
+        if (a.psi_in && threadIdx.x < G::TY * (G::TX / 32)) {
+            const int row = threadIdx.x / (G::TX / 32), seg = threadIdx.x % (G::TX / 32);
+            const int y = y0 + row, x = x0 + 32 * seg;
+            if (y < a.H && x < a.W)
+                asm volatile("prefetch.global.L2 [%0];" ::"l"(a.psi_in + p * plane_px + static_cast<long long>(y) * a.W + x));
+        }
         float prod[G::H_PER_THREAD][kNC];
 #pragma unroll
         for (int h = 0; h < G::H_PER_THREAD; ++h)
