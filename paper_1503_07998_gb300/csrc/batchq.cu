@@ -177,6 +177,22 @@ namespace {
 // so every load and store of a warp is one contiguous 128-byte run.
 //   RATIO:  out = phi / max(result, eps)      (out, phi: the view's plane)
 //   UPDATE: psi = psi * result, or mean * result on the first update
+// The tile's rows of one plane of `base` (es-byte elements) into L2, one
+// 128-byte line per thread and step: the item's epilogue reads them after
+// its passes.
+template <int KC>
+__device__ __forceinline__ void prefetch_rows(const void *base, int es, long long plane_off, int y0, int x0, int H,
+                                              int W) {
+    using G = Geo<KC, kTyQ>;
+    const int lpr = (G::TX * es + 127) / 128;   // lines per tile row
+    for (int i = threadIdx.x; i < G::TY * lpr; i += kThreads) {
+        const int row = i / lpr, x = x0 + (i - row * lpr) * (128 / es), y = y0 + row;
+        if (y < H && x < W)
+            asm volatile("prefetch.global.L2 [%0];" ::"l"(static_cast<const char *>(base) +
+                                                          (plane_off + static_cast<long long>(y) * W + x) * es));
+    }
+}
+
 template <int KC, bool RATIO>
 __device__ __forceinline__ void row_out(const float *__restrict__ stage, const QVol &v, long long plane_off,
                                         int y0, int x0, bool first, float mean) {
@@ -303,6 +319,12 @@ __global__ void __launch_bounds__(kThreads, 2) queue_kernel(const __grid_constan
         const int P = v.P;
         const long long plane = static_cast<long long>(v.H) * v.W;
         const PhaseInfo f = phase_info(v, seg.phase);
+        if (f.kind == 0) {
+            for (int vv = f.v0; vv < f.v1; ++vv)
+                prefetch_rows<KC>(v.phi, v.u16 ? 2 : 4, (static_cast<long long>(vv) * P + p) * plane, y0, x0, v.H, v.W);
+        } else if (seg.phase != 1) {
+            prefetch_rows<KC>(v.psi, 4, p * plane, y0, x0, v.H, v.W);
+        }
 
         if (f.kind == 0) {   // A: ratio_v = phi_v / max(P_v * psi, eps)
             const bool first = seg.phase == 0;
