@@ -25,6 +25,11 @@ def test_reference_arm_json_line():
     assert d["n_gpus"] == 1 and d["steps"] == 1 and d["warmup"] == 3
     assert d["higher_is_better"] is True and d["vs_baseline"] is None
     assert "workload" in d["config"]
+    # the same config object as the GPU arm's line (bench.workload_config),
+    # so that the two arms' lines describe one workload key for key
+    sys.path.insert(0, ROOT)
+    import bench
+    assert d["config"] == bench.workload_config(bench.WORKLOADS["volume128"], 1)
     cpu = d["cpu_baseline"]
     assert cpu["kind"] == "oracle" and cpu["cores"] >= 1 and cpu["value"] == d["value"] and cpu["sample"]
     e2e = d["e2e"]
