@@ -70,11 +70,34 @@ SM_MAX_MHZ = 2070.0
 # launch by the planes processed (traffic is proportional to the planes);
 # None where no capture of the current kernels exists.  The captures are
 # summarised under profiles/ (fused_kernels_volume1024x4.md); the 512^3
-# workload's kernels have changed since its capture.
+# workload has no capture of the current kernels.
 NCU_TRAFFIC_PER_LAUNCH = {
     "volume1024x4": {"blur_ratio": 1.0073e10, "correlate_update": 1.2251e10},
     "volume512": {"blur_ratio": None, "correlate_update": None},
 }
+# The fused kernels' source files and the first 16 hex digits of the SHA-256
+# of their concatenation when those counters were taken: once any of them
+# changes, the line reports traffic null until a new capture is recorded.
+FUSED_KERNEL_SOURCES = ("fused.cu", "fused_common.cuh", "tma.cuh", "mvd_internal.h")
+NCU_TRAFFIC_SOURCE_SHA16 = "e61f00f827214c9e"
+
+
+def fused_sources_sha16():
+    import hashlib
+    h = hashlib.sha256()
+    for f in FUSED_KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_1503_07998_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(workload, kernel):
+    """Captured DRAM bytes per launch of `kernel`, or None when there is no
+    capture of the kernels as they are now."""
+    t = NCU_TRAFFIC_PER_LAUNCH.get(workload, {}).get(kernel)
+    if t is None or fused_sources_sha16() != NCU_TRAFFIC_SOURCE_SHA16:
+        return None
+    return t
 
 
 def _measured_peaks():
@@ -449,7 +472,7 @@ def run_mvd(args, wl):
     else:
         roof = {"bound": "hbm", "achieved": d["hbm_gbs"], "peak": hbm_peak, "unit": "GB/s",
                 "frac": d["hbm_frac"], "peak_source": hbm_src}
-    roof.update({"kernel": dom, "traffic": NCU_TRAFFIC_PER_LAUNCH.get(args.workload, {}).get(dom),
+    roof.update({"kernel": dom, "traffic": ncu_traffic(args.workload, dom),
                  "algorithmic_bytes_per_launch": px * d["bytes_per_unit"],
                  "algorithmic_flops_per_launch": px * d["flops_per_unit"],
                  "hbm_gbs": d["hbm_gbs"], "hbm_frac": d["hbm_frac"], "hbm_peak": hbm_peak,
